@@ -1,0 +1,329 @@
+/*
+ * dass.h -- C ABI of libdass, the GB300 (sm_103a) hot path of
+ * "Dynamics-Aware Gaussian Splatting Streaming" (DASS, arXiv 2411.14847).
+ *
+ * Problem statement (Sec. 3.1): at timestep t the method starts from the Gaussians
+ * G_{t-1} and derives G_t from the C synchronised views of timestep t, in three stages:
+ * selective inheritance (Sec. 3.2), dynamics-aware shift (Sec. 3.3) and error-guided
+ * densification (Sec. 3.4). Every stage optimises Gaussians through the differentiable
+ * 3D Gaussian-splatting renderer of App. A.1 (projection, depth-ordered alpha blending).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: DASS_OK (0) or a negative dass_status. Argument errors are detected on
+ *    the host before anything is launched; DASS_ERR_CUDA reports a failed launch or CUDA
+ *    call (see dass_last_error()).
+ *  - Memory: every array argument is a DEVICE pointer owned by the caller, except where a
+ *    parameter says "host". The library never allocates device memory. Scratch memory is
+ *    a caller-provided `workspace` whose size the matching *_workspace() query returns.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls only
+ *    enqueue work; none synchronises the host except dass_step and dass_timestep where
+ *    documented. Results are valid once the stream reaches them.
+ *  - Layout: float32, structure of arrays, N-major, contiguous. Gaussians:
+ *      means[N][3], log_scales[N][3], quats[N][4] (w,x,y,z; need not be unit),
+ *      opacity_logit[N], sh[N][K][3] with K = (sh_degree+1)^2 real-SH coefficients
+ *      (index k = l*l + l + m, basis without Condon-Shortley phase), sh_degree <= 3.
+ *  - Cameras (host arrays of dass_camera): viewmat is the row-major world->camera 4x4
+ *    (OpenCV axes: x right, y down, z forward); pixel centres sit at integer coordinates.
+ *    At most DASS_MAX_CAMERAS cameras per call.
+ *  - Projected records: one dass_splat per (camera, Gaussian), record index
+ *    c * rec_stride + g (rec_stride = N for one scene seen by all cameras).
+ *  - Images are planar per camera, cameras concatenated: camera c occupies
+ *    3*H_c*W_c floats starting at 3 * sum_{c'<c} H_c' W_c', channel-major then row-major.
+ *  - Tiles: B x B pixel tiles (B in {8,16,32}); camera c owns the global tile ids
+ *    [tile_base_c, tile_base_c + ceil(W/B)*ceil(H/B)), row-major, cameras in order.
+ */
+#ifndef DASS_H
+#define DASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DASS_MAX_CAMERAS 64
+#define DASS_VERSION 1
+
+typedef enum dass_status {
+    DASS_OK = 0,
+    DASS_ERR_INVALID_ARG = -1,  /* bad size, NULL pointer, unsupported tile/batch/degree */
+    DASS_ERR_CUDA = -2,         /* a CUDA launch or call failed; dass_last_error() has text */
+    DASS_ERR_OOM = -3,          /* workspace smaller than the matching *_workspace() size */
+    DASS_ERR_CAPACITY = -4,     /* pair or Gaussian capacity exceeded; grow and retry */
+    DASS_ERR_TIMEOUT = -5,      /* a bounded wait gave up */
+    DASS_ERR_UNSUPPORTED = -6
+} dass_status;
+
+/* Camera of App. A.1's projection: world->camera viewmat, pinhole intrinsics. 88 bytes. */
+typedef struct dass_camera {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} dass_camera;
+
+/* Screen-space record of one Gaussian in one camera (App. A.1), written by dass_preprocess.
+ * radius == 0 marks a Gaussian that contributes to no pixel of that camera (behind the
+ * near plane z <= 0.2, opacity <= 1/255, or footprint outside every tile). 48 bytes. */
+typedef struct dass_splat {
+    float mean2d[2];   /* pixel coordinates (u, v) */
+    float conic[3];    /* inverse 2D covariance (a, b, c): power = -(a dx^2 + 2 b dx dy + c dy^2)/2 */
+    float opacity;     /* sigmoid(logit), times the inheritance mask (Eq. 1) */
+    float rgb[3];      /* view-dependent colour max(SH(d) + 0.5, 0) */
+    float depth;       /* camera-space z */
+    int32_t radius;    /* opacity-aware pixel radius of the alpha >= 1/255 footprint */
+    int32_t tiles;     /* tiles covered by [u-r,u+r] x [v-r,v+r] at the tile size of the call */
+} dass_splat;
+
+/* Gradient of the loss w.r.t. the fields of one dass_splat (accumulated by dass_render_bwd). */
+typedef struct dass_splat_grad {
+    float mean2d[2];
+    float conic[3];
+    float opacity;
+    float rgb[3];
+    float pad[3];
+} dass_splat_grad;
+
+/* grad_flags of dass_preprocess_bwd: which parameter gradients to produce. */
+#define DASS_GRAD_MEANS   1u
+#define DASS_GRAD_SCALES  2u
+#define DASS_GRAD_QUATS   4u
+#define DASS_GRAD_OPACITY 8u
+#define DASS_GRAD_SH      16u
+#define DASS_GRAD_ALL     31u
+
+/* ------------------------------------------------------------------ utilities */
+
+int dass_version(void);
+const char* dass_status_string(int status);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* dass_last_error(void);
+
+/* Host helper: total tiles and pixels of a camera set at tile size B. */
+int dass_tile_layout(const dass_camera* cams, int n_cams, int tile, int32_t* tiles_total,
+                     int64_t* pixels_total);
+
+/* ------------------------------------------------------------------ rasteriser (App. A.1) */
+
+/* Projection of every Gaussian into every camera (App. A.1: Sigma = R S S^T R^T,
+ * Sigma_2D = J W Sigma W^T J^T, plus 0.3 I low-pass; SH colour), one record per
+ * (camera, Gaussian) at splats[c * n + g]. `keep` (optional, N bytes, NULL = all 1) is the
+ * quantised inheritance mask of Eq. 1, multiplying the activated opacity and scale.
+ * `tile` only fills dass_splat.tiles. One launch for all cameras. */
+int dass_preprocess(int64_t n, int sh_degree, const float* means, const float* log_scales,
+                    const float* quats, const float* opacity_logit, const float* sh,
+                    const uint8_t* keep, const dass_camera* cams /* host */, int n_cams,
+                    int tile, dass_splat* splats, void* stream);
+
+/* Bytes of scratch that dass_bin_sort needs for n_records = n_cams * rec_stride records,
+ * `pair_capacity` (tile, Gaussian) pairs and `tiles_total` tiles. */
+int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total,
+                            size_t* bytes);
+
+/* Tile binning and device radix sort (tile-based rasterisation, Sec. 1 / Sec. 4.2).
+ * Each visible record emits one (tile, record) pair per covered tile; pairs are ordered by
+ * the 64-bit key (global tile id << 32 | depth bits), stable in record order: an LSD radix
+ * sort whose 32 depth-bit passes run on the records before duplication and whose tile-bit
+ * passes run on the pairs. Outputs: pair_rec[M] (record id per sorted pair),
+ * tile_ranges[2*tiles_total] ([start, end) per tile, 0,0 when empty) and
+ * counters[0] = M, counters[1] = 1 if M > pair_capacity (pairs beyond the capacity are
+ * dropped: the render is then incomplete and the caller must grow and rerun).
+ * Returns DASS_ERR_OOM if workspace_bytes < dass_bin_sort_workspace(). */
+int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camera* cams /* host */,
+                  int n_cams, int tile, uint32_t* pair_rec, int64_t pair_capacity,
+                  uint32_t* tile_ranges, int64_t* counters, void* workspace,
+                  size_t workspace_bytes, void* stream);
+
+/* Forward compositing of every tile of every camera in one launch (App. A.1 blending):
+ * per pixel, front to back over its tile's list, alpha = min(0.99, o exp(power)); alpha
+ * < 1/255 is skipped; before adding a Gaussian, T (1 - alpha) < 1e-4 stops the pixel and
+ * the Gaussian is not added. Writes image (planar), T_final[pixels] and n_last[pixels]
+ * (sorted-pair position of the last added Gaussian, -1 if none). bg: host float[3] or NULL
+ * (black). batch in {64,128,256}: Gaussians staged in shared memory per round. */
+int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                    const dass_camera* cams /* host */, int n_cams, int tile, int batch,
+                    const float* bg /* host, 3 */, float* image, float* T_final, int32_t* n_last,
+                    void* stream);
+
+/* Reverse-order backward of dass_render_fwd. Recomputes alpha from the saved T_final and
+ * n_last (T_j = T_{j+1} / (1 - alpha_j)); per Gaussian the 9 gradients are reduced across the
+ * warp with shuffles, then per block in shared memory, then added to splat_grads[record]
+ * with global atomics. splat_grads (n_records entries) is zeroed by this call first. */
+int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
+                    const uint32_t* tile_ranges, const dass_camera* cams /* host */, int n_cams,
+                    int tile, int batch, const float* bg /* host, 3 */, const float* T_final,
+                    const int32_t* n_last, const float* dL_dimage, dass_splat_grad* splat_grads,
+                    void* stream);
+
+/* Chain rule from splat gradients to parameter gradients (App. A.1 projection, SH colour,
+ * sigmoid/exp activations, Eq. 1 mask), summed over cameras. rows (optional, n_rows
+ * Gaussian indices) restricts the work to those Gaussians and makes the outputs compact
+ * ([n_rows][...]); rows == NULL means all n Gaussians. Only the outputs selected by
+ * grad_flags are written (others may be NULL). accumulate != 0 adds to the outputs. */
+int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, const float* log_scales,
+                        const float* quats, const float* opacity_logit, const float* sh,
+                        const uint8_t* keep, const dass_camera* cams /* host */, int n_cams,
+                        const dass_splat* splats, const dass_splat_grad* splat_grads,
+                        const int32_t* rows, int64_t n_rows, uint32_t grad_flags, int accumulate,
+                        float* d_means, float* d_log_scales, float* d_quats,
+                        float* d_opacity_logit, float* d_sh, void* stream);
+
+/* ------------------------------------------------------------------ DASS stages */
+
+/* Dynamics-aware shift (Sec. 3.3), dynamic rows only: for d < n_dyn with n = dyn_idx[d],
+ * out_means[n] = means[n] + dmu_d and out_quats[n] = norm(quats[n]) x norm(sigma_d)
+ * (Hamilton product). offsets[n_dyn][7] = (dmu[3], sigma[4]). Static rows of out_* are not
+ * touched (the caller keeps them equal to the inputs). n_dyn == 0 is a no-op. */
+int dass_shift(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* means,
+               const float* quats, float* out_means, float* out_quats, void* stream);
+
+/* Backward of dass_shift: from compact d_out_means[n_dyn][3], d_out_quats[n_dyn][4] (the
+ * gradients of the shifted rows, e.g. from dass_preprocess_bwd with rows = dyn_idx) to
+ * d_offsets[n_dyn][7]. Only dynamic Gaussians receive gradients (Sec. 3.3). */
+int dass_shift_bwd(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* quats,
+                   const float* d_out_means, const float* d_out_quats, float* d_offsets,
+                   void* stream);
+
+/* Masked Adam step (optimiser not named by the paper; the 3DGS family uses Adam):
+ * for each selected row r (rows == NULL: all n_rows rows) and k < row_width:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr_k m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps),
+ * with t = *step_dev + 1 read on the device (so one captured launch serves every step) and
+ * lr_k = lr[k] (host array of row_width learning rates). Unselected rows are untouched.
+ * If increment_step != 0 the call also does *step_dev += 1 after the update. */
+int dass_adam(int64_t n_rows, int row_width, const int32_t* rows, int64_t n_sel, float* param,
+              const float* grad, float* adam_m, float* adam_v, int32_t* step_dev,
+              const float* lr /* host, row_width */, float beta1, float beta2, float eps,
+              int increment_step, void* stream);
+
+/* Bytes of scratch for dass_loss over a camera set (3 SSIM partial maps per pixel/channel). */
+int dass_loss_workspace(const dass_camera* cams, int n_cams, size_t* bytes);
+
+/* Fidelity loss of Eq. 3: L = mean_c[(1-lambda) L1_c + lambda (1 - SSIM_c)], SSIM with an
+ * 11x11 Gaussian window (sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2). Writes
+ * dL_dimage (planar, like image) and adds L to *loss (device double; the caller zeroes it).
+ * lambda == 0 skips SSIM. */
+int dass_loss(const float* image, const float* target, const dass_camera* cams /* host */,
+              int n_cams, float lambda, float* dL_dimage, double* loss, void* workspace,
+              size_t workspace_bytes, void* stream);
+
+/* Per-iteration statistics of error-guided densification (Sec. 3.4): for every Gaussian g
+ * and camera c with a visible record (radius > 0 and the square of half-side radius around
+ * mean2d overlapping the image), accum[g] += |(dL/du W/2, dL/dv H/2)| (the view-space
+ * positional gradient in NDC units) and count[g] += 1. */
+int dass_densify_stats(int64_t n, const dass_splat* splats, const dass_splat_grad* splat_grads,
+                       const dass_camera* cams /* host */, int n_cams, float* accum,
+                       int32_t* count, void* stream);
+
+/* Selective inheritance copy (Sec. 3.2, Eq. 1, App. B.2): output = every base row
+ * (is_var == 0) in order, then every var row with Quant(sigmoid(m)) = 1, i.e. m > 0, in order;
+ * erase != 0 (every 20th timestep) drops all var rows. Writes the compacted parameters,
+ * is_var_out, remap[n] (old -> new row, -1 if dropped) and *n_out (device). The output
+ * arrays must not alias the inputs. */
+int dass_inherit_workspace(int64_t n, size_t* bytes);
+int dass_inherit(int64_t n, int sh_degree, const float* means, const float* log_scales,
+                 const float* quats, const float* opacity_logit, const float* sh,
+                 const uint8_t* is_var, const float* m, int erase, float* out_means,
+                 float* out_log_scales, float* out_quats, float* out_opacity_logit, float* out_sh,
+                 uint8_t* is_var_out, int32_t* remap, int64_t* n_out, void* workspace,
+                 size_t workspace_bytes, void* stream);
+
+/* Error pass of Sec. 3.4: per camera E^c = mean_RGB |image - target| (float32, order
+ * ((|dr|+|dg|)+|db|)/3), gamma^c = the element floor(q (P-1)) of the ascending sort of E^c
+ * (radix select), D^c = [E^c > gamma^c]; each base Gaussian (is_var == 0 or is_var == NULL)
+ * is projected with Alg. 1 (x_n = floor(0.5((x_norm+1)W - 1) + 0.5), y likewise with H) and
+ * s_err[g] = 1 if D^c(y_n, x_n) = 1 for some camera (p_hom <= 0 or outside: no hit).
+ * error_map (optional, [pixels]) receives E; gamma (device, [n_cams]) the thresholds. */
+int dass_error_pass_workspace(const dass_camera* cams, int n_cams, size_t* bytes);
+int dass_error_pass(const float* image, const float* target, const dass_camera* cams /* host */,
+                    int n_cams, float quantile, int64_t n, const float* means, const uint8_t* is_var,
+                    float* error_map, float* gamma, uint8_t* s_err, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Eq. 4 selection: g_n = accum/count (float32 division; 0 if count = 0);
+ * S = {base n : g_n > tau_pos} U (S_err n {base n : g_n > tau_err}); of S the at most k_max
+ * members with the largest g_n (ties: smaller index) are written to selected[] in ascending
+ * index order and their number to *n_selected (device). */
+int dass_densify_select_workspace(int64_t n, size_t* bytes);
+int dass_densify_select(int64_t n, const float* accum, const int32_t* count, const uint8_t* s_err,
+                        const uint8_t* is_var, float tau_pos, float tau_err, int32_t k_max,
+                        int32_t* selected, int32_t* n_selected, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/* Spawn densification (Sec. 3.4; the mechanism is not described, reading): for i <
+ * *n_selected with source s = selected[i], row n + i of every parameter array becomes a new
+ * var Gaussian: mean = mu_s + R_s diag(s_s) z_s, log-scale = log(s_s / 1.6), rotation,
+ * opacity logit and SH copied; is_var[n + i] = 1. z[n][3] holds the caller's N(0,1) draws
+ * indexed by source. Arrays must have room for n + k_max rows. *n_total (device) = n + count. */
+int dass_spawn(int64_t n, int sh_degree, float* means, float* log_scales, float* quats,
+               float* opacity_logit, float* sh, uint8_t* is_var, const int32_t* selected,
+               const int32_t* n_selected, int32_t k_max, const float* z, int64_t* n_total,
+               void* stream);
+
+/* ------------------------------------------------------------------ per-timestep driver */
+
+/* All buffers of one shift-stage optimisation (Sec. 3.3 with the fidelity loss of Eq. 3).
+ * Every pointer is a device pointer owned by the caller unless noted. */
+typedef struct dass_step_desc {
+    /* scene: n Gaussians (read-only during the stage) */
+    int64_t n;
+    int32_t sh_degree;
+    int32_t n_cams;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logit;
+    const float* sh;
+    const dass_camera* cams;          /* host [n_cams] */
+    const float* targets;             /* ground-truth images, planar like image */
+    /* dynamic group and its learned offsets */
+    int64_t n_dyn;
+    const int32_t* dyn_idx;           /* [n_dyn] */
+    float* offsets;                   /* [n_dyn][7] (dmu, sigma), updated in place */
+    float* offset_grad;               /* [n_dyn][7] */
+    float* adam_m;                    /* [n_dyn][7] */
+    float* adam_v;                    /* [n_dyn][7] */
+    int32_t* adam_step;               /* device int, incremented once per iteration */
+    float lr_mu, lr_sigma, beta1, beta2, eps, lambda_dssim;
+    /* rendering buffers */
+    int32_t tile, batch;
+    float* render_means;              /* [n][3]: means with the dynamic rows shifted */
+    float* render_quats;              /* [n][4] */
+    float* d_means_dyn;               /* [n_dyn][3] scratch */
+    float* d_quats_dyn;               /* [n_dyn][4] scratch */
+    dass_splat* splats;               /* [n_cams * n] */
+    dass_splat_grad* splat_grads;     /* [n_cams * n] */
+    uint32_t* pair_rec;               /* [pair_capacity] */
+    int64_t pair_capacity;
+    uint32_t* tile_ranges;            /* [2 * tiles_total] */
+    int64_t* counters;                /* [4] */
+    float* image;                     /* [pixels * 3] */
+    float* T_final;                   /* [pixels] */
+    int32_t* n_last;                  /* [pixels] */
+    float* dL_dimage;                 /* [pixels * 3] */
+    double* loss;                     /* [1], loss of the last iteration */
+    float* stat_accum;                /* [n] or NULL: densification statistics */
+    int32_t* stat_count;              /* [n] or NULL */
+    void* workspace;                  /* >= dass_step_workspace() bytes */
+    size_t workspace_bytes;
+} dass_step_desc;
+
+#define DASS_STEP_BATCHED 0   /* all cameras per launch, CUDA-graph replay of one iteration */
+#define DASS_STEP_PLAIN 1     /* one launch per camera per kernel, no graph */
+
+int dass_step_workspace(const dass_step_desc* d, size_t* bytes);
+
+/* Runs n_iters optimisation iterations of the shift stage: shift -> preprocess -> bin/sort
+ * -> forward -> loss -> backward -> preprocess backward (dynamic rows) -> shift backward ->
+ * [statistics] -> masked Adam on the offsets. mode DASS_STEP_BATCHED captures one iteration
+ * into a CUDA graph on `stream` (which must not be the legacy default stream) and replays it
+ * n_iters times; DASS_STEP_PLAIN launches per camera without a graph. render_means/quats
+ * must hold a copy of means/quats before the first call. The call ends with one stream
+ * synchronisation and a read of the pair-overflow flag: it returns DASS_ERR_CAPACITY if any
+ * iteration overflowed pair_capacity (results of the stage are then unreliable). */
+int dass_step(const dass_step_desc* d, int n_iters, int mode, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DASS_H */

@@ -177,14 +177,14 @@ def mean_grad_f32(accum, count):
 def densify_select(grad_mean, s_err, is_base, tau_pos, tau_err, k_max):
     """Eq. 4: S = {n in base : g_n > tau_pos} U (S_err n {n in base : g_n > tau_err}),
     then the at most k_max members with the largest g_n (ties by smaller index).
-    Returns sorted-by-(g desc, index asc) selected indices."""
+    Returns the selected indices in ascending index order (the order new rows are appended)."""
     g = np.asarray(grad_mean, dtype=np.float32)
     base = np.asarray(is_base, bool)
     s1 = base & (g > np.float32(tau_pos))
     s2 = np.asarray(s_err, bool) & base & (g > np.float32(tau_err))
     cand = np.nonzero(s1 | s2)[0]
     order = sorted(cand.tolist(), key=lambda n: (-float(g[n]), n))
-    return np.asarray(order[:k_max], dtype=np.int64)
+    return np.asarray(sorted(order[:k_max]), dtype=np.int64)
 
 
 def spawn(arrays: dict, selected, z, scale_div=1.6):

@@ -1,0 +1,519 @@
+// extern "C" entry points of libdass: argument checks, camera tables, dispatch to the kernel
+// launchers, and the per-stage driver dass_step (CUDA-graph replay of one iteration).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dass {
+
+// launchers defined in the other translation units
+int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
+                      const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
+                      dass_splat* splats, cudaStream_t st);
+int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
+                          const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
+                          const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
+                          unsigned flags, int accumulate, float* d_means, float* d_log_scales, float* d_quats,
+                          float* d_opacity_logit, float* d_sh, cudaStream_t st);
+int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
+                         float* accum, int* count, cudaStream_t st);
+size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
+int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
+                    uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
+int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
+                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st);
+int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
+                      int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
+                      dass_splat_grad* gsplat, cudaStream_t st);
+size_t loss_workspace_bytes(const CamTable& ct);
+int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
+                double* loss, void* ws, size_t ws_bytes, cudaStream_t st);
+int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats, float* om,
+                 float* oq, cudaStream_t st);
+int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
+                     const float* dq, float* doff, cudaStream_t st);
+int adam_launch(long long n_sel, int width, const int* rows, float* p, const float* g, float* m, float* v,
+                int* step_dev, const float* lr, float b1, float b2, float eps, int inc, cudaStream_t st);
+size_t inherit_workspace_bytes(long long n);
+int inherit_launch(long long n, int deg, const float* means, const float* ls, const float* quats, const float* logit,
+                   const float* sh, const uint8_t* is_var, const float* m, int erase, float* om, float* ols, float* oq,
+                   float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
+                   cudaStream_t st);
+size_t error_pass_workspace_bytes(const CamTable& ct);
+int error_pass_launch(const float* img, const float* tgt, const CamTable& ct, double quantile, long long n,
+                      const float* means, const uint8_t* is_var, float* error_map, float* gamma, uint8_t* s_err,
+                      void* ws, size_t ws_bytes, cudaStream_t st);
+size_t select_workspace_bytes(long long n);
+int select_launch(long long n, const float* accum, const int* count, const uint8_t* s_err, const uint8_t* is_var,
+                  float tau_pos, float tau_err, int k_max, int* selected, int* n_selected, void* ws, size_t ws_bytes,
+                  cudaStream_t st);
+int spawn_launch(long long n, int deg, float* means, float* ls, float* quats, float* logit, float* sh, uint8_t* is_var,
+                 const int* selected, const int* n_sel, int k_max, const float* z, long long* n_total,
+                 cudaStream_t st);
+
+static thread_local char g_err[512] = {0};
+
+void set_last_error(const char* what, cudaError_t e) {
+    snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(what, e);
+        return DASS_ERR_CUDA;
+    }
+    return DASS_OK;
+}
+
+bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec_stride, CamTable* out) {
+    if (!cams || n_cams < 1 || n_cams > DASS_MAX_CAMERAS) return false;
+    if (tile != 8 && tile != 16 && tile != 32) return false;
+    std::memset(out, 0, sizeof(CamTable));
+    out->n = n_cams;
+    out->tile = tile;
+    out->rec_stride = rec_stride;
+    long long tiles = 0, pix = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        const dass_camera& c = cams[i];
+        if (c.width <= 0 || c.height <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f)) return false;
+        CamInfo& ci = out->c[i];
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) ci.R[3 * r + k] = c.viewmat[4 * r + k];
+            ci.t[r] = c.viewmat[4 * r + 3];
+        }
+        ci.fx = c.fx; ci.fy = c.fy; ci.cx = c.cx; ci.cy = c.cy;
+        ci.W = c.width; ci.H = c.height;
+        for (int k = 0; k < 3; ++k)
+            ci.campos[k] = -(ci.R[k] * ci.t[0] + ci.R[3 + k] * ci.t[1] + ci.R[6 + k] * ci.t[2]);
+        // Alg. 1 full projection T (row vectors): [P,1] T = (p_x, p_y, p_z, p_hom) with p_hom = z
+        // and x_norm chosen so that 0.5((x_norm + 1) W - 1) = fx X/Z + cx. Built in double.
+        double W = c.width, H = c.height, zn = 0.01, zf = 100.0;
+        double K[4][4] = {{2.0 * c.fx / W, 0.0, (2.0 * c.cx + 1.0) / W - 1.0, 0.0},
+                          {0.0, 2.0 * c.fy / H, (2.0 * c.cy + 1.0) / H - 1.0, 0.0},
+                          {0.0, 0.0, (zf + zn) / (zf - zn), -2.0 * zf * zn / (zf - zn)},
+                          {0.0, 0.0, 1.0, 0.0}};
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 4; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < 4; ++j) s += K[r][j] * (double)c.viewmat[4 * j + k];
+                ci.proj[4 * k + r] = (float)s;   // transpose: row-vector convention
+            }
+        ci.tiles_x = (c.width + tile - 1) / tile;
+        ci.tiles_y = (c.height + tile - 1) / tile;
+        ci.tile_base = (int)tiles;
+        ci.pix_base = pix;
+        ci.rec_base = (long long)i * rec_stride;
+        tiles += (long long)ci.tiles_x * ci.tiles_y;
+        pix += (long long)c.width * c.height;
+    }
+    if (tiles >= (1ll << 31)) return false;
+    out->tiles_total = (int)tiles;
+    out->pixels_total = pix;
+    return true;
+}
+
+}  // namespace dass
+
+using namespace dass;
+
+static float3 bg3(const float* bg) { return bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f); }
+
+DASS_API int dass_version(void) { return DASS_VERSION; }
+
+DASS_API const char* dass_status_string(int s) {
+    switch (s) {
+        case DASS_OK: return "ok";
+        case DASS_ERR_INVALID_ARG: return "invalid argument";
+        case DASS_ERR_CUDA: return "CUDA error";
+        case DASS_ERR_OOM: return "workspace too small";
+        case DASS_ERR_CAPACITY: return "capacity exceeded";
+        case DASS_ERR_TIMEOUT: return "bounded wait timed out";
+        case DASS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+DASS_API const char* dass_last_error(void) { return dass::g_err; }
+
+DASS_API int dass_tile_layout(const dass_camera* cams, int n_cams, int tile, int32_t* tiles_total,
+                              int64_t* pixels_total) {
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    if (tiles_total) *tiles_total = ct.tiles_total;
+    if (pixels_total) *pixels_total = ct.pixels_total;
+    return DASS_OK;
+}
+
+DASS_API int dass_preprocess(int64_t n, int sh_degree, const float* means, const float* log_scales, const float* quats,
+                             const float* opacity_logit, const float* sh, const uint8_t* keep, const dass_camera* cams,
+                             int n_cams, int tile, dass_splat* splats, void* stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3) return DASS_ERR_INVALID_ARG;
+    if (n > 0 && (!means || !log_scales || !quats || !opacity_logit || !sh || !splats)) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, n, &ct)) return DASS_ERR_INVALID_ARG;
+    if (n == 0) return DASS_OK;
+    return preprocess_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, keep, ct, splats,
+                             as_stream(stream));
+}
+
+DASS_API int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total, size_t* bytes) {
+    if (n_records < 0 || pair_capacity < 0 || tiles_total < 0 || !bytes) return DASS_ERR_INVALID_ARG;
+    if (n_records >= (1ll << 32) || pair_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    *bytes = bin_sort_workspace_bytes(n_records, pair_capacity);
+    return DASS_OK;
+}
+
+DASS_API int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camera* cams, int n_cams, int tile,
+                           uint32_t* pair_rec, int64_t pair_capacity, uint32_t* tile_ranges, int64_t* counters,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+    if (rec_stride < 0 || pair_capacity < 0 || !tile_ranges || !counters) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
+    long long n_rec = (long long)n_cams * rec_stride;
+    if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (n_rec > 0 && (!splats || !pair_rec || !workspace)) return DASS_ERR_INVALID_ARG;
+    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity)) return DASS_ERR_OOM;
+    return bin_sort_launch(splats, n_rec, ct, pair_rec, pair_capacity, tile_ranges, (long long*)counters, workspace,
+                           workspace_bytes, as_stream(stream));
+}
+
+static bool batch_ok(int b) { return b == 64 || b == 128 || b == 256; }
+
+DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                             const dass_camera* cams, int n_cams, int tile, int batch, const float* bg, float* image,
+                             float* T_final, int32_t* n_last, void* stream) {
+    if (!batch_ok(batch) || !tile_ranges || !image || !T_final || !n_last) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    return render_fwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), image, T_final, n_last,
+                             as_stream(stream));
+}
+
+DASS_API int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
+                             const uint32_t* tile_ranges, const dass_camera* cams, int n_cams, int tile, int batch,
+                             const float* bg, const float* T_final, const int32_t* n_last, const float* dL_dimage,
+                             dass_splat_grad* splat_grads, void* stream) {
+    if (!batch_ok(batch) || n_records < 0 || !tile_ranges || !T_final || !n_last || !dL_dimage)
+        return DASS_ERR_INVALID_ARG;
+    if (n_records > 0 && !splat_grads) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    if (n_records > 0) DASS_CHECK_CUDA(cudaMemsetAsync(splat_grads, 0, sizeof(dass_splat_grad) * n_records, st));
+    return render_bwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), T_final, n_last, dL_dimage,
+                             splat_grads, st);
+}
+
+DASS_API int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, const float* log_scales,
+                                 const float* quats, const float* opacity_logit, const float* sh, const uint8_t* keep,
+                                 const dass_camera* cams, int n_cams, const dass_splat* splats,
+                                 const dass_splat_grad* splat_grads, const int32_t* rows, int64_t n_rows,
+                                 uint32_t grad_flags, int accumulate, float* d_means, float* d_log_scales,
+                                 float* d_quats, float* d_opacity_logit, float* d_sh, void* stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || (grad_flags & ~DASS_GRAD_ALL)) return DASS_ERR_INVALID_ARG;
+    long long nr = rows ? n_rows : n;
+    if (nr < 0) return DASS_ERR_INVALID_ARG;
+    if (nr > 0 && (!means || !log_scales || !quats || !opacity_logit || !sh || !splats || !splat_grads))
+        return DASS_ERR_INVALID_ARG;
+    if ((grad_flags & DASS_GRAD_MEANS) && !d_means) return DASS_ERR_INVALID_ARG;
+    if ((grad_flags & DASS_GRAD_SCALES) && !d_log_scales) return DASS_ERR_INVALID_ARG;
+    if ((grad_flags & DASS_GRAD_QUATS) && !d_quats) return DASS_ERR_INVALID_ARG;
+    if ((grad_flags & DASS_GRAD_OPACITY) && !d_opacity_logit) return DASS_ERR_INVALID_ARG;
+    if ((grad_flags & DASS_GRAD_SH) && !d_sh) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 8, n, &ct)) return DASS_ERR_INVALID_ARG;
+    return preprocess_bwd_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, keep, ct, splats,
+                                 splat_grads, rows, nr, grad_flags, accumulate, d_means, d_log_scales, d_quats,
+                                 d_opacity_logit, d_sh, as_stream(stream));
+}
+
+DASS_API int dass_densify_stats(int64_t n, const dass_splat* splats, const dass_splat_grad* splat_grads,
+                                const dass_camera* cams, int n_cams, float* accum, int32_t* count, void* stream) {
+    if (n < 0 || (n > 0 && (!splats || !splat_grads || !accum || !count))) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 8, n, &ct)) return DASS_ERR_INVALID_ARG;
+    return densify_stats_launch(n, ct, splats, splat_grads, accum, count, as_stream(stream));
+}
+
+DASS_API int dass_shift(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* means,
+                        const float* quats, float* out_means, float* out_quats, void* stream) {
+    if (n_dyn < 0) return DASS_ERR_INVALID_ARG;
+    if (n_dyn > 0 && (!dyn_idx || !offsets || !means || !quats || !out_means || !out_quats))
+        return DASS_ERR_INVALID_ARG;
+    return shift_launch(n_dyn, dyn_idx, offsets, means, quats, out_means, out_quats, as_stream(stream));
+}
+
+DASS_API int dass_shift_bwd(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* quats,
+                            const float* d_out_means, const float* d_out_quats, float* d_offsets, void* stream) {
+    if (n_dyn < 0) return DASS_ERR_INVALID_ARG;
+    if (n_dyn > 0 && (!dyn_idx || !offsets || !quats || !d_out_means || !d_out_quats || !d_offsets))
+        return DASS_ERR_INVALID_ARG;
+    return shift_bwd_launch(n_dyn, dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, as_stream(stream));
+}
+
+DASS_API int dass_adam(int64_t n_rows, int row_width, const int32_t* rows, int64_t n_sel, float* param,
+                       const float* grad, float* adam_m, float* adam_v, int32_t* step_dev, const float* lr, float beta1,
+                       float beta2, float eps, int increment_step, void* stream) {
+    if (n_rows < 0 || row_width < 1 || row_width > 16 || !lr || !step_dev) return DASS_ERR_INVALID_ARG;
+    long long ns = rows ? n_sel : n_rows;
+    if (ns < 0) return DASS_ERR_INVALID_ARG;
+    if (ns > 0 && (!param || !grad || !adam_m || !adam_v)) return DASS_ERR_INVALID_ARG;
+    return adam_launch(ns, row_width, rows, param, grad, adam_m, adam_v, step_dev, lr, beta1, beta2, eps,
+                       increment_step, as_stream(stream));
+}
+
+DASS_API int dass_loss_workspace(const dass_camera* cams, int n_cams, size_t* bytes) {
+    static thread_local CamTable ct;
+    if (!bytes || !make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    *bytes = loss_workspace_bytes(ct);
+    return DASS_OK;
+}
+
+DASS_API int dass_loss(const float* image, const float* target, const dass_camera* cams, int n_cams, float lambda,
+                       float* dL_dimage, double* loss, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!image || !target || !dL_dimage || !loss || !(lambda >= 0.f && lambda <= 1.f)) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    if (lambda > 0.f && workspace_bytes < loss_workspace_bytes(ct)) return DASS_ERR_OOM;
+    return loss_launch(image, target, ct, lambda, 1.f / (float)n_cams, dL_dimage, loss, workspace, workspace_bytes,
+                       as_stream(stream));
+}
+
+DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
+    *bytes = inherit_workspace_bytes(n);
+    return DASS_OK;
+}
+
+DASS_API int dass_inherit(int64_t n, int sh_degree, const float* means, const float* log_scales, const float* quats,
+                          const float* opacity_logit, const float* sh, const uint8_t* is_var, const float* m,
+                          int erase, float* out_means, float* out_log_scales, float* out_quats,
+                          float* out_opacity_logit, float* out_sh, uint8_t* is_var_out, int32_t* remap,
+                          int64_t* n_out, void* workspace, size_t workspace_bytes, void* stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !n_out) return DASS_ERR_INVALID_ARG;
+    if (n > 0 && (!means || !log_scales || !quats || !opacity_logit || !sh || !is_var || !out_means ||
+                  !out_log_scales || !out_quats || !out_opacity_logit || !out_sh || !is_var_out || !remap))
+        return DASS_ERR_INVALID_ARG;
+    return inherit_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, is_var, m, erase, out_means,
+                          out_log_scales, out_quats, out_opacity_logit, out_sh, is_var_out, remap, (long long*)n_out,
+                          workspace, workspace_bytes, as_stream(stream));
+}
+
+DASS_API int dass_error_pass_workspace(const dass_camera* cams, int n_cams, size_t* bytes) {
+    static thread_local CamTable ct;
+    if (!bytes || !make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    *bytes = error_pass_workspace_bytes(ct);
+    return DASS_OK;
+}
+
+DASS_API int dass_error_pass(const float* image, const float* target, const dass_camera* cams, int n_cams,
+                             float quantile, int64_t n, const float* means, const uint8_t* is_var, float* error_map,
+                             float* gamma, uint8_t* s_err, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!image || !target || n < 0 || !(quantile >= 0.f && quantile <= 1.f)) return DASS_ERR_INVALID_ARG;
+    if (n > 0 && (!means || !s_err)) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    return error_pass_launch(image, target, ct, (double)quantile, n, means, is_var, error_map, gamma, s_err, workspace,
+                             workspace_bytes, as_stream(stream));
+}
+
+DASS_API int dass_densify_select_workspace(int64_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
+    *bytes = select_workspace_bytes(n);
+    return DASS_OK;
+}
+
+DASS_API int dass_densify_select(int64_t n, const float* accum, const int32_t* count, const uint8_t* s_err,
+                                 const uint8_t* is_var, float tau_pos, float tau_err, int32_t k_max, int32_t* selected,
+                                 int32_t* n_selected, void* workspace, size_t workspace_bytes, void* stream) {
+    if (n < 0 || k_max < 0 || !n_selected || !(tau_pos >= 0.f) || !(tau_err >= 0.f)) return DASS_ERR_INVALID_ARG;
+    if (n > 0 && (!accum || !count || (k_max > 0 && !selected))) return DASS_ERR_INVALID_ARG;
+    if (n >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
+    return select_launch(n, accum, count, s_err, is_var, tau_pos, tau_err, k_max, selected, n_selected, workspace,
+                         workspace_bytes, as_stream(stream));
+}
+
+DASS_API int dass_spawn(int64_t n, int sh_degree, float* means, float* log_scales, float* quats, float* opacity_logit,
+                        float* sh, uint8_t* is_var, const int32_t* selected, const int32_t* n_selected, int32_t k_max,
+                        const float* z, int64_t* n_total, void* stream) {
+    if (n < 0 || k_max < 0 || sh_degree < 0 || sh_degree > 3 || !n_selected || !n_total) return DASS_ERR_INVALID_ARG;
+    if (!means || !log_scales || !quats || !opacity_logit || !sh || !is_var || (k_max > 0 && (!selected || !z)))
+        return DASS_ERR_INVALID_ARG;
+    return spawn_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, is_var, selected, n_selected, k_max,
+                        z, (long long*)n_total, as_stream(stream));
+}
+
+// ----------------------------------------------------------------- dass_step
+
+namespace {
+
+struct StepPlan {
+    CamTable all;
+    std::vector<CamTable> per;   // one-camera tables (plain mode)
+    size_t bin_ws = 0, loss_ws = 0;
+};
+
+bool plan_step(const dass_step_desc* d, StepPlan& p, int mode) {
+    if (!make_cam_table(d->cams, d->n_cams, d->tile, d->n, &p.all)) return false;
+    long long n_rec = (long long)d->n_cams * d->n;
+    p.bin_ws = bin_sort_workspace_bytes(mode == DASS_STEP_PLAIN ? d->n : n_rec, d->pair_capacity);
+    p.loss_ws = loss_workspace_bytes(p.all);
+    if (mode == DASS_STEP_PLAIN) {
+        p.per.resize(d->n_cams);
+        for (int c = 0; c < d->n_cams; ++c)
+            if (!make_cam_table(d->cams + c, 1, d->tile, d->n, &p.per[c])) return false;
+    }
+    return true;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+__global__ void or_flag_kernel(long long* counters) { counters[3] |= counters[1]; }
+
+int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStream_t st) {
+    char* ws = reinterpret_cast<char*>(d->workspace);
+    void* bin_ws = ws;
+    void* loss_ws = ws + align256(p.bin_ws);
+    const float3 bg = make_float3(0.f, 0.f, 0.f);
+    int rc = shift_launch(d->n_dyn, d->dyn_idx, d->offsets, d->means, d->quats, d->render_means, d->render_quats, st);
+    if (rc) return rc;
+    DASS_CHECK_CUDA(cudaMemsetAsync(d->loss, 0, sizeof(double), st));
+    const float inv_cams = 1.f / (float)d->n_cams;
+    if (mode == DASS_STEP_BATCHED) {
+        const CamTable& ct = p.all;
+        long long n_rec = (long long)d->n_cams * d->n;
+        rc = preprocess_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats, d->opacity_logit,
+                               d->sh, nullptr, ct, d->splats, st);
+        if (rc) return rc;
+        rc = bin_sort_launch(d->splats, n_rec, ct, d->pair_rec, d->pair_capacity, d->tile_ranges,
+                             (long long*)d->counters, bin_ws, p.bin_ws, st);
+        if (rc) return rc;
+        or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters);
+        rc = render_fwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image, d->T_final,
+                               d->n_last, st);
+        if (rc) return rc;
+        rc = loss_launch(d->image, d->targets, ct, d->lambda_dssim, inv_cams, d->dL_dimage, d->loss, loss_ws,
+                         p.loss_ws, st);
+        if (rc) return rc;
+        DASS_CHECK_CUDA(cudaMemsetAsync(d->splat_grads, 0, sizeof(dass_splat_grad) * n_rec, st));
+        rc = render_bwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final, d->n_last,
+                               d->dL_dimage, d->splat_grads, st);
+        if (rc) return rc;
+        rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
+                                   d->opacity_logit, d->sh, nullptr, ct, d->splats, d->splat_grads, d->dyn_idx,
+                                   d->n_dyn, DASS_GRAD_MEANS | DASS_GRAD_QUATS, 0, d->d_means_dyn, nullptr,
+                                   d->d_quats_dyn, nullptr, nullptr, st);
+        if (rc) return rc;
+        if (d->stat_accum && d->stat_count) {
+            rc = densify_stats_launch(d->n, ct, d->splats, d->splat_grads, d->stat_accum, d->stat_count, st);
+            if (rc) return rc;
+        }
+    } else {
+        for (int c = 0; c < d->n_cams; ++c) {
+            const CamTable& ct = p.per[c];
+            const CamInfo& full = p.all.c[c];
+            dass_splat* sp = d->splats + (long long)c * d->n;
+            dass_splat_grad* gs = d->splat_grads + (long long)c * d->n;
+            long long pb = full.pix_base;
+            rc = preprocess_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
+                                   d->opacity_logit, d->sh, nullptr, ct, sp, st);
+            if (rc) return rc;
+            rc = bin_sort_launch(sp, d->n, ct, d->pair_rec, d->pair_capacity, d->tile_ranges, (long long*)d->counters,
+                                 bin_ws, p.bin_ws, st);
+            if (rc) return rc;
+            or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters);
+            rc = render_fwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image + 3 * pb,
+                                   d->T_final + pb, d->n_last + pb, st);
+            if (rc) return rc;
+            rc = loss_launch(d->image + 3 * pb, d->targets + 3 * pb, ct, d->lambda_dssim, inv_cams,
+                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st);
+            if (rc) return rc;
+            DASS_CHECK_CUDA(cudaMemsetAsync(gs, 0, sizeof(dass_splat_grad) * d->n, st));
+            rc = render_bwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final + pb, d->n_last + pb,
+                                   d->dL_dimage + 3 * pb, gs, st);
+            if (rc) return rc;
+            rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
+                                       d->opacity_logit, d->sh, nullptr, ct, sp, gs, d->dyn_idx, d->n_dyn,
+                                       DASS_GRAD_MEANS | DASS_GRAD_QUATS, c > 0, d->d_means_dyn, nullptr,
+                                       d->d_quats_dyn, nullptr, nullptr, st);
+            if (rc) return rc;
+            if (d->stat_accum && d->stat_count) {
+                rc = densify_stats_launch(d->n, ct, sp, gs, d->stat_accum, d->stat_count, st);
+                if (rc) return rc;
+            }
+        }
+    }
+    rc = shift_bwd_launch(d->n_dyn, d->dyn_idx, d->offsets, d->quats, d->d_means_dyn, d->d_quats_dyn, d->offset_grad,
+                          st);
+    if (rc) return rc;
+    float lr[7] = {d->lr_mu, d->lr_mu, d->lr_mu, d->lr_sigma, d->lr_sigma, d->lr_sigma, d->lr_sigma};
+    return adam_launch(d->n_dyn, 7, nullptr, d->offsets, d->offset_grad, d->adam_m, d->adam_v, d->adam_step, lr,
+                       d->beta1, d->beta2, d->eps, 1, st);
+}
+
+bool desc_ok(const dass_step_desc* d) {
+    if (!d || d->n < 0 || d->n_dyn < 0 || d->sh_degree < 0 || d->sh_degree > 3) return false;
+    if (d->n >= (1ll << 31) || (long long)d->n_cams * d->n >= (1ll << 32)) return false;
+    if (!batch_ok(d->batch)) return false;
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logit || !d->sh || !d->targets) return false;
+    if (d->n_dyn > 0 && (!d->dyn_idx || !d->offsets || !d->offset_grad || !d->adam_m || !d->adam_v)) return false;
+    if (!d->adam_step || !d->render_means || !d->render_quats || !d->splats || !d->splat_grads) return false;
+    if (!d->pair_rec || !d->tile_ranges || !d->counters || !d->image || !d->T_final || !d->n_last) return false;
+    if (!d->dL_dimage || !d->loss || !d->workspace) return false;
+    if (d->n_dyn > 0 && (!d->d_means_dyn || !d->d_quats_dyn)) return false;
+    return true;
+}
+
+}  // namespace
+
+DASS_API int dass_step_workspace(const dass_step_desc* d, size_t* bytes) {
+    if (!d || !bytes) return DASS_ERR_INVALID_ARG;
+    StepPlan p;
+    if (!plan_step(d, p, DASS_STEP_BATCHED)) return DASS_ERR_INVALID_ARG;
+    *bytes = align256(p.bin_ws) + align256(p.loss_ws);
+    return DASS_OK;
+}
+
+DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* stream) {
+    if (!desc_ok(d) || n_iters < 0 || (mode != DASS_STEP_BATCHED && mode != DASS_STEP_PLAIN))
+        return DASS_ERR_INVALID_ARG;
+    StepPlan p;
+    if (!plan_step(d, p, mode)) return DASS_ERR_INVALID_ARG;
+    if (d->workspace_bytes < align256(p.bin_ws) + align256(p.loss_ws)) return DASS_ERR_OOM;
+    cudaStream_t st = as_stream(stream);
+    DASS_CHECK_CUDA(cudaMemsetAsync(d->counters, 0, sizeof(int64_t) * 4, st));
+    if (n_iters == 0) return DASS_OK;
+    if (mode == DASS_STEP_BATCHED) {
+        if (st == nullptr) return DASS_ERR_INVALID_ARG;   // the legacy stream cannot be captured
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        DASS_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = step_iteration(d, p, mode, st);
+        cudaError_t ec = cudaStreamEndCapture(st, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (ec != cudaSuccess) { set_last_error("cudaStreamEndCapture", ec); return DASS_ERR_CUDA; }
+        ec = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) { set_last_error("cudaGraphInstantiate", ec); return DASS_ERR_CUDA; }
+        for (int i = 0; i < n_iters; ++i) {
+            ec = cudaGraphLaunch(exec, st);
+            if (ec != cudaSuccess) { cudaGraphExecDestroy(exec); set_last_error("cudaGraphLaunch", ec); return DASS_ERR_CUDA; }
+        }
+        ec = cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(exec);
+        if (ec != cudaSuccess) { set_last_error("cudaStreamSynchronize", ec); return DASS_ERR_CUDA; }
+    } else {
+        for (int i = 0; i < n_iters; ++i) {
+            int rc = step_iteration(d, p, mode, st);
+            if (rc) return rc;
+        }
+        DASS_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    int64_t flags[4];
+    DASS_CHECK_CUDA(cudaMemcpy(flags, d->counters, sizeof(flags), cudaMemcpyDeviceToHost));
+    return flags[3] ? DASS_ERR_CAPACITY : DASS_OK;
+}

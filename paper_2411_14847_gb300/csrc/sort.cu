@@ -1,0 +1,432 @@
+// Tile binning and a hand-written stable LSD radix sort (no CUB) for the tile-based
+// rasteriser. The pair order is that of the 64-bit key (tile id << 32 | depth bits), ties in
+// record order: the 32 depth-bit digits are sorted on the records before duplication (all
+// pairs of a record share its depth), the tile-id digits on the pairs afterwards.
+//
+// Every kernel reads its item count from device memory and sizes its work from it, so the
+// whole sequence needs no host synchronisation and can be captured in a CUDA graph; grids are
+// launched for the capacity and surplus blocks exit at once.
+#include "common.cuh"
+
+namespace dass {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 2048 elements per scan block
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096 keys per radix block
+constexpr int kMaxDigitBits = 9;
+constexpr int kMaxDigits = 1 << kMaxDigitBits;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ----------------------------------------------------------------- exclusive scan (u32 -> u32)
+// Three passes: per-block sums, one-block scan of the sums (64-bit, also writes the total),
+// per-block scan with the block's offset. Length comes from *len (device).
+
+__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, const long long* len_dev,
+                                   unsigned long long* __restrict__ partial) {
+    long long len = *len_dev;
+    long long base = (long long)blockIdx.x * kScanTile;
+    if (base >= len) return;
+    unsigned long long s = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+        long long idx = base + i;
+        if (idx < len) s += in[idx];
+    }
+    __shared__ unsigned long long red[kScanThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// One block of 1024 threads scans nb partials in place (exclusive) and writes the total.
+__global__ void scan_partials_kernel(unsigned long long* partial, const long long* len_dev,
+                                     long long* total_out) {
+    long long len = *len_dev;
+    int nb = (int)((len + kScanTile - 1) / kScanTile);
+    __shared__ unsigned long long sh[1024];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        unsigned long long v = i < nb ? partial[i] : 0ull;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            unsigned long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        unsigned long long incl = sh[threadIdx.x];
+        if (i < nb) partial[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = (long long)carry;
+}
+
+__global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                 const long long* len_dev, const unsigned long long* __restrict__ partial) {
+    long long len = *len_dev;
+    long long base = (long long)blockIdx.x * kScanTile;
+    if (base >= len) return;
+    // blocked arrangement: thread t owns items [t*8, t*8+8)
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long long idx = base + threadIdx.x * kScanItems + k;
+        v[k] = idx < len ? in[idx] : 0u;
+        sum += v[k];
+    }
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += wsum[w];
+    uint32_t run = (uint32_t)partial[blockIdx.x] + woff + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long long idx = base + threadIdx.x * kScanItems + k;
+        if (idx < len) out[idx] = run;
+        run += v[k];
+    }
+}
+
+// ----------------------------------------------------------------- radix sort passes
+
+__device__ __forceinline__ long long radix_nblocks(long long n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+// Per-block digit counts, digit-major: hist[d * nb + b].
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                   const long long* n_dev, uint32_t* __restrict__ hist,
+                                                                   long long* hist_len, int shift, int dbits) {
+    long long n = *n_dev;
+    long long nb = radix_nblocks(n);
+    int nd = 1 << dbits;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hist_len = nb * nd;
+    if ((long long)blockIdx.x >= nb) return;
+    __shared__ uint32_t sh[kMaxDigits];
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) sh[d] = 0;
+    __syncthreads();
+    unsigned mask = (unsigned)nd - 1u;
+    long long base = (long long)blockIdx.x * kRadixTile;
+    int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        bool valid = idx < n;
+        unsigned digit = valid ? ((keys[idx] >> shift) & mask) : (unsigned)kMaxDigits;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[digit], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) hist[(long long)d * nb + blockIdx.x] = sh[d];
+}
+
+// Stable scatter: block-local ranks in item order (rounds of 256 items, warps in order,
+// lanes in order) plus the block's scanned digit offsets.
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const long long* n_dev, const uint32_t* __restrict__ hist_scanned, int shift,
+    int dbits) {
+    long long n = *n_dev;
+    long long nb = radix_nblocks(n);
+    if ((long long)blockIdx.x >= nb) return;
+    int nd = 1 << dbits;
+    unsigned mask = (unsigned)nd - 1u;
+    __shared__ uint32_t s_base[kMaxDigits];
+    __shared__ uint32_t s_cnt[kRadixWarps][kMaxDigits];
+    __shared__ uint32_t s_off[kRadixWarps][kMaxDigits];
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) {
+        s_base[d] = hist_scanned[(long long)d * nb + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) s_cnt[w][d] = 0;
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long base = (long long)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        bool valid = idx < n;
+        uint32_t key = valid ? keys_in[idx] : 0u;
+        uint32_t val = valid ? vals_in[idx] : 0u;
+        unsigned digit = valid ? ((key >> shift) & mask) : (unsigned)kMaxDigits;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        unsigned rank = __popc(peers & lanemask_lt());
+        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][digit] = (uint32_t)__popc(peers);
+        __syncthreads();
+        for (int d = threadIdx.x; d < nd; d += kRadixThreads) {
+            uint32_t run = s_base[d];
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) {
+                uint32_t c = s_cnt[w][d];
+                s_off[w][d] = run;
+                s_cnt[w][d] = 0;
+                run += c;
+            }
+            s_base[d] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_off[warp][digit] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- binning kernels
+
+// Record -> (depth key, own index, tile count).
+__global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                 uint32_t* __restrict__ counts) {
+    long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= n_rec) return;
+    int ci = (int)(rec / ct.rec_stride);
+    const CamInfo& cam = ct.c[ci];
+    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
+    float4 s0 = __ldg(sp);
+    float4 s2 = __ldg(sp + 2);
+    int r = __float_as_int(s2.z);
+    int cnt = tile_count(s0.x, s0.y, r, cam.tiles_x, cam.tiles_y, ct.tile);
+    keys[rec] = cnt > 0 ? __float_as_uint(s2.y) : 0xffffffffu;
+    vals[rec] = (uint32_t)rec;
+    counts[rec] = (uint32_t)cnt;
+}
+
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
+                                     uint32_t* __restrict__ out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = counts[order[i]];
+}
+
+// Emit the pairs of each record (depth order) into its scanned slot range.
+__global__ void duplicate_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
+                                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                                 const long long* total, long long capacity, uint32_t* __restrict__ pair_tile,
+                                 uint32_t* __restrict__ pair_rec, long long* counters) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        long long m = *total;
+        counters[0] = m;
+        counters[1] = m > capacity ? 1 : 0;
+        counters[2] = m > capacity ? capacity : m;   // pairs actually stored (sort length)
+    }
+    if (k >= n_rec) return;
+    uint32_t rec = order[k];
+    int ci = (int)(rec / ct.rec_stride);
+    const CamInfo& cam = ct.c[ci];
+    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
+    float4 s0 = __ldg(sp);
+    float4 s2 = __ldg(sp + 2);
+    int r = __float_as_int(s2.z);
+    if (r <= 0) return;
+    int x0, x1, y0, y1;
+    tile_rect(s0.x, s0.y, r, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
+    if (x0 > x1 || y0 > y1) return;
+    long long pos = offsets[k];
+    for (int y = y0; y <= y1; ++y) {
+        for (int x = x0; x <= x1; ++x) {
+            if (pos < capacity) {
+                pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
+                pair_rec[pos] = rec;
+            }
+            ++pos;
+        }
+    }
+}
+
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const long long* n_dev,
+                                   uint32_t* __restrict__ ranges) {
+    long long n = *n_dev;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = tiles[i];
+    if (i == 0 || tiles[i - 1] != t) ranges[2 * (long long)t] = (uint32_t)i;
+    if (i == n - 1 || tiles[i + 1] != t) ranges[2 * (long long)t + 1] = (uint32_t)(i + 1);
+}
+
+__global__ void set_len_kernel(long long* dst, long long v) { *dst = v; }
+
+// ----------------------------------------------------------------- host-side orchestration
+
+struct Carver {
+    char* p;
+    size_t used = 0;
+    size_t cap;
+    template <class T>
+    T* take(long long count) {
+        size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+        T* r = reinterpret_cast<T*>(p ? p + used : nullptr);
+        used += bytes;
+        return r;
+    }
+};
+
+struct SortScratch {
+    long long* scal;             // [8] device scalars: 0 n_rec, 1 hist_len, 2 total pairs, 3.. spare
+    uint32_t* kA; uint32_t* vA; uint32_t* kB; uint32_t* vB;   // record-sized
+    uint32_t* counts;            // record-sized
+    uint32_t* offsets;           // record-sized
+    uint32_t* hist;              // digits * max blocks
+    unsigned long long* partial; // scan partials
+    uint32_t* pk0; uint32_t* pk1; uint32_t* pv1;  // pair-sized
+};
+
+long long hist_capacity(long long n_max) {
+    return (long long)kMaxDigits * ((n_max + kRadixTile - 1) / kRadixTile + 1);
+}
+
+SortScratch carve(Carver& cv, long long n_rec, long long cap) {
+    SortScratch s;
+    long long big = n_rec > cap ? n_rec : cap;
+    s.scal = cv.take<long long>(8);
+    s.kA = cv.take<uint32_t>(n_rec);
+    s.vA = cv.take<uint32_t>(n_rec);
+    s.kB = cv.take<uint32_t>(n_rec);
+    s.vB = cv.take<uint32_t>(n_rec);
+    s.counts = cv.take<uint32_t>(n_rec);
+    s.offsets = cv.take<uint32_t>(n_rec);
+    s.hist = cv.take<uint32_t>(hist_capacity(big));
+    long long scan_len = hist_capacity(big) > n_rec ? hist_capacity(big) : n_rec;
+    s.partial = cv.take<unsigned long long>(scan_len / kScanTile + 2);
+    s.pk0 = cv.take<uint32_t>(cap);
+    s.pk1 = cv.take<uint32_t>(cap);
+    s.pv1 = cv.take<uint32_t>(cap);
+    return s;
+}
+
+// out = exclusive_scan(in) over *len_dev elements (capacity len_cap); total -> *total (optional).
+int scan_u32(const uint32_t* in, uint32_t* out, const long long* len_dev, long long len_cap,
+             unsigned long long* partial, long long* total, cudaStream_t st) {
+    int nb = div_up(len_cap > 0 ? len_cap : 1, kScanTile);
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, len_dev, partial);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(partial, len_dev, total);
+    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, len_dev, partial);
+    return check_launch("scan_u32");
+}
+
+// Stable sort of (keys, vals) by bits [0, bits) of the keys; n from *n_dev (<= n_cap).
+// Pass i reads buffer set i%2 and writes set (i+1)%2 of {(k0, v0), (k1, v1)}; returns the
+// index of the set holding the result.
+int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const long long* n_dev, long long n_cap,
+               int bits, SortScratch& s, cudaStream_t st, int* result_set) {
+    int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    if (passes < 1) passes = 1;
+    int dbits = (bits + passes - 1) / passes;
+    int nb = div_up(n_cap > 0 ? n_cap : 1, kRadixTile);
+    long long hist_cap = (long long)(1 << dbits) * nb;
+    uint32_t* kin = k0; uint32_t* vin = v0; uint32_t* kout = k1; uint32_t* vout = v1;
+    for (int p = 0; p < passes; ++p) {
+        int shift = p * dbits;
+        int db = dbits;
+        if (shift + db > bits) db = bits - shift;
+        radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kin, n_dev, s.hist, s.scal + 1, shift, db);
+        int rc = scan_u32(s.hist, s.hist, s.scal + 1, hist_cap, s.partial, nullptr, st);
+        if (rc) return rc;
+        radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kin, vin, kout, vout, n_dev, s.hist, shift, db);
+        int lc = check_launch("radix_pass");
+        if (lc) return lc;
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    *result_set = passes % 2;
+    return DASS_OK;
+}
+
+int bits_for(long long values) {
+    int b = 1;
+    while ((1ll << b) < values) ++b;
+    return b;
+}
+
+}  // namespace
+
+size_t bin_sort_workspace_bytes(long long n_rec, long long cap) {
+    Carver cv{nullptr, 0, 0};
+    carve(cv, n_rec, cap);
+    return cv.used;
+}
+
+int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec,
+                    long long cap, uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes,
+                    cudaStream_t st) {
+    Carver cv{reinterpret_cast<char*>(ws), 0, ws_bytes};
+    SortScratch s = carve(cv, n_rec, cap);
+    if (cv.used > ws_bytes) return DASS_ERR_OOM;
+    DASS_CHECK_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ct.tiles_total, st));
+    if (n_rec == 0) {
+        DASS_CHECK_CUDA(cudaMemsetAsync(counters, 0, sizeof(long long) * 3, st));
+        return DASS_OK;
+    }
+    set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec);
+    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.kA, s.vA, s.counts);
+    int rc = check_launch("bin_count");
+    if (rc) return rc;
+    // 1) depth digits on the records (32 bits)
+    int set = 0;
+    rc = radix_sort(s.kA, s.vA, s.kB, s.vB, s.scal + 0, n_rec, 32, s, st, &set);
+    if (rc) return rc;
+    uint32_t* order = set == 0 ? s.vA : s.vB;
+    // 2) pair offsets in depth order
+    gather_counts_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(order, s.counts, s.offsets, n_rec);
+    rc = scan_u32(s.offsets, s.offsets, s.scal + 0, n_rec, s.partial, s.scal + 2, st);
+    if (rc) return rc;
+    // 3) duplicate into tile-keyed pairs (stored count -> counters[2])
+    int tbits = bits_for(ct.tiles_total > 1 ? ct.tiles_total : 2);
+    int passes = (tbits + kMaxDigitBits - 1) / kMaxDigitBits;
+    // the sort must end in (pk?, pair_rec): pass i writes set (i+1)%2; choose the start set
+    uint32_t *k_out = s.pk0, *v_out = pair_rec, *k_tmp = s.pk1, *v_tmp = s.pv1;
+    uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
+    uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
+    duplicate_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, order, s.offsets, s.scal + 2, cap,
+                                                         k_start, v_start, counters);
+    rc = check_launch("duplicate");
+    if (rc) return rc;
+    // 4) tile digits on the pairs
+    const long long* m_dev = counters + 2;
+    if (passes % 2 == 0)
+        rc = radix_sort(k_out, v_out, k_tmp, v_tmp, m_dev, cap, tbits, s, st, &set);
+    else
+        rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
+    if (rc) return rc;
+    // 5) tile ranges
+    tile_ranges_kernel<<<div_up(cap, 256), 256, 0, st>>>(k_out, m_dev, tile_ranges);
+    return check_launch("tile_ranges");
+}
+
+// Generic pieces reused by other translation units.
+size_t scan_partials_bytes(long long len) { return sizeof(unsigned long long) * (size_t)(len / kScanTile + 2); }
+
+int scan_u32_public(const uint32_t* in, uint32_t* out, const long long* len_dev, long long len_cap,
+                    unsigned long long* partial, long long* total, cudaStream_t st) {
+    return scan_u32(in, out, len_dev, len_cap, partial, total, st);
+}
+
+}  // namespace dass

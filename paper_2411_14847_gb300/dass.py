@@ -1,0 +1,328 @@
+"""ctypes binding of libdass (include/dass.h): argument marshalling only.
+
+Every function below has the name of its C entry point, takes torch CUDA tensors for the
+device arrays and plain Python values for the rest, and raises DassError on a non-zero
+status. All compute happens in libdass; torch only provides device memory and streams.
+The library is loaded on first use; if it is missing the call fails (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdass.so")
+_lib = None
+
+MAX_CAMERAS = 64
+GRAD_MEANS, GRAD_SCALES, GRAD_QUATS, GRAD_OPACITY, GRAD_SH = 1, 2, 4, 8, 16
+GRAD_ALL = 31
+STEP_BATCHED, STEP_PLAIN = 0, 1
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+SPLAT_FLOATS = 12   # sizeof(dass_splat) / 4
+GRAD_FLOATS = 12    # sizeof(dass_splat_grad) / 4
+
+
+class DassError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        detail = ""
+        if _lib is not None:
+            detail = _lib.dass_last_error().decode()
+            name = _lib.dass_status_string(status).decode()
+        else:
+            name = str(status)
+        super().__init__(f"{fn} failed: {name} ({status}) {detail}".strip())
+
+
+class dass_camera(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 16), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class dass_step_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_cams", C.c_int32),
+        ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+        ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("cams", C.c_void_p), ("targets", C.c_void_p),
+        ("n_dyn", C.c_int64), ("dyn_idx", C.c_void_p), ("offsets", C.c_void_p), ("offset_grad", C.c_void_p),
+        ("adam_m", C.c_void_p), ("adam_v", C.c_void_p), ("adam_step", C.c_void_p),
+        ("lr_mu", C.c_float), ("lr_sigma", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+        ("eps", C.c_float), ("lambda_dssim", C.c_float),
+        ("tile", C.c_int32), ("batch", C.c_int32),
+        ("render_means", C.c_void_p), ("render_quats", C.c_void_p), ("d_means_dyn", C.c_void_p),
+        ("d_quats_dyn", C.c_void_p), ("splats", C.c_void_p), ("splat_grads", C.c_void_p),
+        ("pair_rec", C.c_void_p), ("pair_capacity", C.c_int64), ("tile_ranges", C.c_void_p),
+        ("counters", C.c_void_p), ("image", C.c_void_p), ("T_final", C.c_void_p), ("n_last", C.c_void_p),
+        ("dL_dimage", C.c_void_p), ("loss", C.c_void_p), ("stat_accum", C.c_void_p), ("stat_count", C.c_void_p),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+    ]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "dass_version": (C.c_int, []),
+    "dass_status_string": (C.c_char_p, [C.c_int]),
+    "dass_last_error": (C.c_char_p, []),
+    "dass_tile_layout": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
+    "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
+    "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
+    "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
+    "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
+    "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dass_preprocess_bwd": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P,
+                                      C.c_int64, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
+    "dass_shift": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
+    "dass_shift_bwd": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
+    "dass_adam": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_float, C.c_float,
+                            C.c_float, C.c_int, _P]),
+    "dass_loss_workspace": (C.c_int, [_P, C.c_int, _P]),
+    "dass_loss": (C.c_int, [_P, _P, _P, C.c_int, C.c_float, _P, _P, _P, C.c_size_t, _P]),
+    "dass_inherit_workspace": (C.c_int, [C.c_int64, _P]),
+    "dass_inherit": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
+                               _P, _P, _P, C.c_size_t, _P]),
+    "dass_error_pass_workspace": (C.c_int, [_P, C.c_int, _P]),
+    "dass_error_pass": (C.c_int, [_P, _P, _P, C.c_int, C.c_float, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_size_t,
+                                  _P]),
+    "dass_densify_select_workspace": (C.c_int, [C.c_int64, _P]),
+    "dass_densify_select": (C.c_int, [C.c_int64, _P, _P, _P, _P, C.c_float, C.c_float, C.c_int32, _P, _P, _P,
+                                      C.c_size_t, _P]),
+    "dass_spawn": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "dass_step_workspace": (C.c_int, [_P, _P]),
+    "dass_step": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+}
+
+
+def load():
+    """Open libdass.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdass.so not found at {LIB_PATH}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def _call(name, *args):
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != OK:
+        raise DassError(name, st)
+    return st
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def cameras(cams):
+    """ctypes array of dass_camera from objects with viewmat/fx/fy/cx/cy/width/height."""
+    arr = (dass_camera * len(cams))()
+    for i, c in enumerate(cams):
+        vm = np.asarray(c.viewmat, dtype=np.float32).reshape(-1)
+        arr[i].viewmat[:] = [float(v) for v in vm]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[i].width, arr[i].height = int(c.width), int(c.height)
+    return arr
+
+
+def tile_layout(cams, tile):
+    arr = cameras(cams)
+    t = C.c_int32()
+    p = C.c_int64()
+    _call("dass_tile_layout", arr, len(cams), tile, C.byref(t), C.byref(p))
+    return t.value, p.value
+
+
+# ----------------------------------------------------------------- raw entry points
+
+F32, I32, U8, I64, F64 = torch.float32, torch.int32, torch.uint8, torch.int64, torch.float64
+
+
+def dass_preprocess(g, cams, tile, splats, keep=None, stream=None):
+    n = g["means"].shape[0]
+    deg = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    arr = cameras(cams)
+    _call("dass_preprocess", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
+          _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), tile,
+          _ptr(splats, F32), _stream(stream))
+
+
+def dass_bin_sort_workspace(n_records, pair_capacity, tiles_total):
+    b = C.c_size_t()
+    _call("dass_bin_sort_workspace", n_records, pair_capacity, tiles_total, C.byref(b))
+    return b.value
+
+
+def dass_bin_sort(splats, rec_stride, cams, tile, pair_rec, tile_ranges, counters, workspace, stream=None):
+    arr = cameras(cams)
+    _call("dass_bin_sort", _ptr(splats, F32), rec_stride, arr, len(cams), tile, _ptr(pair_rec, I32),
+          pair_rec.numel(), _ptr(tile_ranges, I32), _ptr(counters, I64), _ptr(workspace, U8), workspace.numel(),
+          _stream(stream))
+
+
+def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, bg=None, stream=None):
+    arr = cameras(cams)
+    bgp = (C.c_float * 3)(*bg) if bg is not None else None
+    _call("dass_render_fwd", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams), tile,
+          batch, bgp, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _stream(stream))
+
+
+def dass_render_bwd(splats, pair_rec, tile_ranges, cams, tile, batch, T_final, n_last, dL_dimage, splat_grads,
+                    bg=None, stream=None):
+    arr = cameras(cams)
+    bgp = (C.c_float * 3)(*bg) if bg is not None else None
+    _call("dass_render_bwd", _ptr(splats, F32), splat_grads.numel() // GRAD_FLOATS, _ptr(pair_rec, I32),
+          _ptr(tile_ranges, I32), arr, len(cams), tile, batch, bgp, _ptr(T_final, F32), _ptr(n_last, I32),
+          _ptr(dL_dimage, F32), _ptr(splat_grads, F32), _stream(stream))
+
+
+def dass_preprocess_bwd(g, cams, splats, splat_grads, out, grad_flags=GRAD_ALL, rows=None, accumulate=False,
+                        keep=None, stream=None):
+    """out: dict with any of d_means, d_log_scales, d_quats, d_opacity_logit, d_sh tensors."""
+    n = g["means"].shape[0]
+    deg = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    arr = cameras(cams)
+    n_rows = rows.numel() if rows is not None else n
+    _call("dass_preprocess_bwd", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
+          _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), _ptr(splats, F32),
+          _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, grad_flags, int(bool(accumulate)),
+          _ptr(out.get("d_means"), F32), _ptr(out.get("d_log_scales"), F32), _ptr(out.get("d_quats"), F32),
+          _ptr(out.get("d_opacity_logit"), F32), _ptr(out.get("d_sh"), F32), _stream(stream))
+
+
+def dass_densify_stats(n, splats, splat_grads, cams, accum, count, stream=None):
+    arr = cameras(cams)
+    _call("dass_densify_stats", n, _ptr(splats, F32), _ptr(splat_grads, F32), arr, len(cams), _ptr(accum, F32),
+          _ptr(count, I32), _stream(stream))
+
+
+def dass_shift(dyn_idx, offsets, means, quats, out_means, out_quats, stream=None):
+    _call("dass_shift", dyn_idx.numel(), _ptr(dyn_idx, I32), _ptr(offsets, F32), _ptr(means, F32), _ptr(quats, F32),
+          _ptr(out_means, F32), _ptr(out_quats, F32), _stream(stream))
+
+
+def dass_shift_bwd(dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, stream=None):
+    _call("dass_shift_bwd", dyn_idx.numel(), _ptr(dyn_idx, I32), _ptr(offsets, F32), _ptr(quats, F32),
+          _ptr(d_out_means, F32), _ptr(d_out_quats, F32), _ptr(d_offsets, F32), _stream(stream))
+
+
+def dass_adam(param, grad, m, v, step_dev, lr, beta1=0.9, beta2=0.999, eps=1e-15, rows=None, increment_step=True,
+              stream=None):
+    """param/grad/m/v: [n_rows, width]; lr: list of width learning rates."""
+    n_rows, width = param.shape
+    lra = (C.c_float * width)(*[float(x) for x in lr])
+    _call("dass_adam", n_rows, width, _ptr(rows, I32), rows.numel() if rows is not None else n_rows,
+          _ptr(param, F32), _ptr(grad, F32), _ptr(m, F32), _ptr(v, F32), _ptr(step_dev, I32), lra, beta1, beta2, eps,
+          int(bool(increment_step)), _stream(stream))
+
+
+def dass_loss_workspace(cams):
+    arr = cameras(cams)
+    b = C.c_size_t()
+    _call("dass_loss_workspace", arr, len(cams), C.byref(b))
+    return b.value
+
+
+def dass_loss(image, target, cams, lam, dL_dimage, loss, workspace, stream=None):
+    arr = cameras(cams)
+    _call("dass_loss", _ptr(image, F32), _ptr(target, F32), arr, len(cams), lam, _ptr(dL_dimage, F32),
+          _ptr(loss, F64), _ptr(workspace, U8), workspace.numel() if workspace is not None else 0, _stream(stream))
+
+
+def dass_inherit_workspace(n):
+    b = C.c_size_t()
+    _call("dass_inherit_workspace", n, C.byref(b))
+    return b.value
+
+
+def dass_inherit(g, is_var, m, erase, out, is_var_out, remap, n_out, workspace, stream=None):
+    n = g["means"].shape[0]
+    deg = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    _call("dass_inherit", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
+          _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(is_var, U8), _ptr(m, F32), int(bool(erase)),
+          _ptr(out["means"], F32), _ptr(out["log_scales"], F32), _ptr(out["quats"], F32),
+          _ptr(out["opacity_logit"], F32), _ptr(out["sh"], F32), _ptr(is_var_out, U8), _ptr(remap, I32),
+          _ptr(n_out, I64), _ptr(workspace, U8), workspace.numel(), _stream(stream))
+
+
+def dass_error_pass_workspace(cams):
+    arr = cameras(cams)
+    b = C.c_size_t()
+    _call("dass_error_pass_workspace", arr, len(cams), C.byref(b))
+    return b.value
+
+
+def dass_error_pass(image, target, cams, quantile, means, is_var, s_err, workspace, error_map=None, gamma=None,
+                    stream=None):
+    arr = cameras(cams)
+    n = means.shape[0] if means is not None else 0
+    _call("dass_error_pass", _ptr(image, F32), _ptr(target, F32), arr, len(cams), quantile, n, _ptr(means, F32),
+          _ptr(is_var, U8), _ptr(error_map, F32), _ptr(gamma, F32), _ptr(s_err, U8), _ptr(workspace, U8),
+          workspace.numel(), _stream(stream))
+
+
+def dass_densify_select_workspace(n):
+    b = C.c_size_t()
+    _call("dass_densify_select_workspace", n, C.byref(b))
+    return b.value
+
+
+def dass_densify_select(accum, count, s_err, is_var, tau_pos, tau_err, k_max, selected, n_selected, workspace,
+                        stream=None):
+    _call("dass_densify_select", accum.numel(), _ptr(accum, F32), _ptr(count, I32), _ptr(s_err, U8),
+          _ptr(is_var, U8), tau_pos, tau_err, k_max, _ptr(selected, I32), _ptr(n_selected, I32),
+          _ptr(workspace, U8), workspace.numel(), _stream(stream))
+
+
+def dass_spawn(g, n, is_var, selected, n_selected, k_max, z, n_total, stream=None):
+    deg = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    _call("dass_spawn", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
+          _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(is_var, U8), _ptr(selected, I32),
+          _ptr(n_selected, I32), k_max, _ptr(z, F32), _ptr(n_total, I64), _stream(stream))
+
+
+def dass_step_workspace(desc):
+    b = C.c_size_t()
+    _call("dass_step_workspace", C.byref(desc), C.byref(b))
+    return b.value
+
+
+def dass_step(desc, n_iters, mode=STEP_BATCHED, stream=None):
+    lib = load()
+    st = lib.dass_step(C.byref(desc), n_iters, mode, _stream(stream))
+    if st not in (OK, ERR_CAPACITY):
+        raise DassError("dass_step", st)
+    return st

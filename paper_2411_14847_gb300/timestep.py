@@ -1,0 +1,201 @@
+"""Per-timestep driver of the streaming reconstruction on top of libdass.
+
+A timestep (Sec. 3.1) turns G_{t-1} into G_t with the multi-view images of timestep t:
+  1. selective inheritance copy (Sec. 3.2)                  -> dass_inherit
+  2. dynamics-aware shift stage, n_shift iterations (Sec. 3.3) -> dass_step (graph replay)
+  3. error pass on the last shift render, Eq. 4 selection and spawn (Sec. 3.4)
+                                                           -> dass_error_pass, dass_densify_select, dass_spawn
+This module only allocates buffers (PyTorch) and sequences the calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from . import dass as D
+from .raster import PARAM_NAMES, Frame
+
+
+def _vp(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class ShiftStage:
+    """Buffers and descriptor of one shift-stage optimisation over a fixed Gaussian set."""
+
+    def __init__(self, g, cams, targets, dyn_idx, offsets, tile=16, batch=128, lambda_dssim=0.2, lr_mu=1e-3,
+                 lr_sigma=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, pair_capacity=None, stats=True, stream=None):
+        self.g = {k: g[k].contiguous() for k in PARAM_NAMES}
+        self.cams = list(cams)
+        self.n = int(self.g["means"].shape[0])
+        self.deg = int(round(math.sqrt(self.g["sh"].shape[1]))) - 1
+        self.targets = targets.contiguous()
+        self.dyn_idx = dyn_idx.contiguous()
+        self.offsets = offsets.contiguous()
+        self.n_dyn = int(self.dyn_idx.numel())
+        dev = self.g["means"].device
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.frame = Frame(self.cams, self.n, tile=tile, batch=batch, pair_capacity=pair_capacity or 1024)
+        fr = self.frame
+        self.render_means = self.g["means"].clone()
+        self.render_quats = self.g["quats"].clone()
+        nd = max(1, self.n_dyn)
+        self.offset_grad = torch.zeros((nd, 7), device=dev)
+        self.adam_m = torch.zeros((nd, 7), device=dev)
+        self.adam_v = torch.zeros((nd, 7), device=dev)
+        self.adam_step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.d_means_dyn = torch.zeros((nd, 3), device=dev)
+        self.d_quats_dyn = torch.zeros((nd, 4), device=dev)
+        self.dL_dimage = torch.zeros_like(fr.image)
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.stat_accum = torch.zeros(self.n, device=dev) if stats else None
+        self.stat_count = torch.zeros(self.n, dtype=torch.int32, device=dev) if stats else None
+        self.hp = dict(lr_mu=lr_mu, lr_sigma=lr_sigma, beta1=beta1, beta2=beta2, eps=eps, lambda_dssim=lambda_dssim)
+        self._cams_arr = D.cameras(self.cams)
+        if pair_capacity is None:
+            # size the pair buffer from one binning of the unshifted scene (exact count + 25%)
+            fr.project(self.g)
+            m = fr.bin_sort()
+            fr._alloc_pairs(int(m * 1.25) + 4096)
+        self._build_desc()
+
+    def _build_desc(self):
+        fr = self.frame
+        d = D.dass_step_desc()
+        d.n, d.sh_degree, d.n_cams = self.n, self.deg, len(self.cams)
+        d.means, d.log_scales, d.quats = _vp(self.g["means"]), _vp(self.g["log_scales"]), _vp(self.g["quats"])
+        d.opacity_logit, d.sh = _vp(self.g["opacity_logit"]), _vp(self.g["sh"])
+        d.cams = C.cast(self._cams_arr, C.c_void_p)
+        d.targets = _vp(self.targets)
+        d.n_dyn = self.n_dyn
+        d.dyn_idx, d.offsets, d.offset_grad = _vp(self.dyn_idx), _vp(self.offsets), _vp(self.offset_grad)
+        d.adam_m, d.adam_v, d.adam_step = _vp(self.adam_m), _vp(self.adam_v), _vp(self.adam_step)
+        for k, v in self.hp.items():
+            setattr(d, k, v)
+        d.tile, d.batch = fr.tile, fr.batch
+        d.render_means, d.render_quats = _vp(self.render_means), _vp(self.render_quats)
+        d.d_means_dyn, d.d_quats_dyn = _vp(self.d_means_dyn), _vp(self.d_quats_dyn)
+        d.splats, d.splat_grads = _vp(fr.splats), _vp(fr.splat_grads)
+        d.pair_rec, d.pair_capacity = _vp(fr.pair_rec), fr.pair_capacity
+        d.tile_ranges, d.counters = _vp(fr.tile_ranges), _vp(fr.counters)
+        d.image, d.T_final, d.n_last = _vp(fr.image), _vp(fr.T_final), _vp(fr.n_last)
+        d.dL_dimage, d.loss = _vp(self.dL_dimage), _vp(self.loss_buf)
+        d.stat_accum, d.stat_count = _vp(self.stat_accum), _vp(self.stat_count)
+        d.workspace, d.workspace_bytes = None, 0
+        ws = D.dass_step_workspace(d)
+        self.workspace = torch.empty(max(1, ws), dtype=torch.uint8, device=self.g["means"].device)
+        d.workspace, d.workspace_bytes = _vp(self.workspace), ws
+        self.desc = d
+
+    @property
+    def loss(self):
+        return float(self.loss_buf.item())
+
+    def _snapshot(self):
+        return [t.clone() for t in (self.offsets, self.adam_m, self.adam_v, self.adam_step)] + \
+               ([self.stat_accum.clone(), self.stat_count.clone()] if self.stat_accum is not None else [])
+
+    def _restore(self, snap):
+        dst = [self.offsets, self.adam_m, self.adam_v, self.adam_step]
+        if self.stat_accum is not None:
+            dst += [self.stat_accum, self.stat_count]
+        for d, s in zip(dst, snap):
+            d.copy_(s)
+
+    def run(self, n_iters, mode=D.STEP_BATCHED, max_regrow=3):
+        """Run n_iters iterations; on pair-buffer overflow regrow and rerun from the saved state."""
+        torch.cuda.current_stream().synchronize()
+        for _ in range(max_regrow + 1):
+            snap = self._snapshot()
+            torch.cuda.synchronize()
+            st = D.dass_step(self.desc, n_iters, mode, stream=self.stream)
+            if st == D.OK:
+                return
+            m = int(self.frame.counters[0].item())
+            self._restore(snap)
+            self.frame._alloc_pairs(int(max(m, self.frame.pair_capacity) * 1.5) + 4096)
+            self._build_desc()
+        raise D.DassError("dass_step", D.ERR_CAPACITY)
+
+
+class Timestep:
+    """One full timestep t of the streaming pipeline over resident device buffers.
+
+    Scene arrays are allocated with room for `n_max` rows; `n` tracks the live count."""
+
+    def __init__(self, cams, n_max, sh_degree, tile=16, batch=128, lambda_dssim=0.2, n_shift=100,
+                 quantile=0.95, tau_pos=2e-4, tau_err=1e-4, k_max=5000, erase_every=20, device="cuda"):
+        self.cams = list(cams)
+        self.n_max = int(n_max)
+        self.deg = sh_degree
+        self.tile, self.batch = tile, batch
+        self.lambda_dssim = lambda_dssim
+        self.n_shift = n_shift
+        self.quantile, self.tau_pos, self.tau_err, self.k_max = quantile, tau_pos, tau_err, k_max
+        self.erase_every = erase_every
+        self.device = device
+        K = (sh_degree + 1) ** 2
+        shapes = dict(means=(3,), log_scales=(3,), quats=(4,), opacity_logit=(), sh=(K, 3))
+        self.bufs = [{k: torch.zeros((self.n_max,) + s, device=device) for k, s in shapes.items()} for _ in range(2)]
+        self.is_var = [torch.zeros(self.n_max, dtype=torch.uint8, device=device) for _ in range(2)]
+        self.cur = 0
+        self.n = 0
+
+    def load(self, arrays: dict, is_var=None):
+        n = int(arrays["means"].shape[0])
+        assert n + self.k_max <= self.n_max
+        for k in PARAM_NAMES:
+            self.bufs[self.cur][k][:n].copy_(torch.as_tensor(arrays[k], dtype=torch.float32))
+        self.is_var[self.cur].zero_()
+        if is_var is not None:
+            self.is_var[self.cur][:n].copy_(torch.as_tensor(is_var, dtype=torch.uint8))
+        self.n = n
+
+    def view(self, which=None):
+        b = self.bufs[self.cur if which is None else which]
+        return {k: v[:self.n] for k, v in b.items()}
+
+    def run(self, t, targets, dyn_idx, offsets, inherit_logits=None, z=None, mode=D.STEP_BATCHED):
+        """Reconstruct timestep t. Returns dict of per-stage results (loss, #Gaussians, #spawned)."""
+        dev = self.device
+        src, dst = self.cur, 1 - self.cur
+        n = self.n
+        # 1) selective inheritance copy (Sec. 3.2)
+        m = inherit_logits if inherit_logits is not None else torch.ones(n, device=dev)
+        ws = torch.empty(max(1, D.dass_inherit_workspace(n)), dtype=torch.uint8, device=dev)
+        remap = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+        out = {k: v for k, v in self.bufs[dst].items()}
+        D.dass_inherit(self.view(src), self.is_var[src][:n], m[:n].contiguous(), t % self.erase_every == 0, out,
+                       self.is_var[dst], remap, n_out, ws)
+        self.cur = dst
+        self.n = int(n_out.item())
+        g = self.view()
+        # dynamic rows follow the inherited layout (base rows keep their indices)
+        dyn = dyn_idx
+        # 2) shift stage
+        stage = ShiftStage(g, self.cams, targets, dyn, offsets, tile=self.tile, batch=self.batch,
+                           lambda_dssim=self.lambda_dssim)
+        stage.run(self.n_shift, mode)
+        # commit the shift into the scene (the learned offsets move the dynamic rows)
+        D.dass_shift(dyn, stage.offsets, g["means"].clone(), g["quats"].clone(), g["means"], g["quats"])
+        # 3) error-guided densification statistics, selection and spawn (Sec. 3.4)
+        n = self.n
+        s_err = torch.zeros(n, dtype=torch.uint8, device=dev)
+        ews = torch.empty(D.dass_error_pass_workspace(self.cams), dtype=torch.uint8, device=dev)
+        D.dass_error_pass(stage.frame.image, targets, self.cams, self.quantile, g["means"], self.is_var[self.cur][:n],
+                          s_err, ews)
+        sel = torch.empty(max(1, self.k_max), dtype=torch.int32, device=dev)
+        nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+        sws = torch.empty(D.dass_densify_select_workspace(n), dtype=torch.uint8, device=dev)
+        D.dass_densify_select(stage.stat_accum, stage.stat_count, s_err, self.is_var[self.cur][:n], self.tau_pos,
+                              self.tau_err, self.k_max, sel, nsel, sws)
+        if z is None:
+            z = torch.zeros((n, 3), device=dev)
+        n_total = torch.zeros(1, dtype=torch.int64, device=dev)
+        D.dass_spawn({k: v for k, v in self.bufs[self.cur].items()}, n, self.is_var[self.cur], sel, nsel,
+                     self.k_max, z[:n].contiguous(), n_total)
+        self.n = int(n_total.item())
+        return dict(loss=stage.loss, n=self.n, spawned=int(nsel.item()), stage=stage)

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports every entry point
+that include/dass.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dass.h")
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(dass_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_14847_gb300 import build, dass
+    build.ensure_built()
+    return dass.load()
+
+
+def test_header_declares_the_hot_path():
+    names = declared()
+    for required in ("dass_preprocess", "dass_bin_sort", "dass_render_fwd", "dass_render_bwd", "dass_shift",
+                     "dass_densify_stats", "dass_step"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2411_14847_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(dass_\w+)\b", out))
+    for name in declared():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    # nothing else leaks out of the library but the dass_ entry points
+    others = [l.split()[-1] for l in out.splitlines() if " T " in l and "dass_" not in l]
+    assert not [o for o in others if not o.startswith("_")], others
+
+
+def test_binding_covers_header():
+    from paper_2411_14847_gb300 import dass
+    assert sorted(dass.exported_symbols()) == declared()
+
+
+def test_host_side_argument_checks(lib):
+    from paper_2411_14847_gb300 import dass, synth
+    assert lib.dass_version() == 1
+    assert lib.dass_status_string(-4) == b"capacity exceeded"
+    cams = dass.cameras(synth.arc_cameras(2, 4.0, 100, 50))
+    t, p = C.c_int32(), C.c_int64()
+    assert lib.dass_tile_layout(cams, 2, 16, C.byref(t), C.byref(p)) == 0
+    assert (t.value, p.value) == (2 * 7 * 4, 2 * 5000)
+    assert lib.dass_tile_layout(cams, 2, 12, C.byref(t), C.byref(p)) == -1          # unsupported tile
+    assert lib.dass_tile_layout(cams, 65, 16, C.byref(t), C.byref(p)) == -1         # too many cameras
+    # bad sizes/NULLs are rejected before anything touches the device
+    assert lib.dass_preprocess(-1, 0, None, None, None, None, None, None, cams, 2, 16, None, None) == -1
+    assert lib.dass_preprocess(10, 4, None, None, None, None, None, None, cams, 2, 16, None, None) == -1
+    assert lib.dass_render_fwd(None, None, None, cams, 2, 16, 100, None, None, None, None, None) == -1
+    assert lib.dass_shift(-5, None, None, None, None, None, None, None) == -1
+    assert lib.dass_densify_select(10, None, None, None, None, 1e-4, -1.0, 10, None, None, None, 0, None) == -1
+    b = C.c_size_t()
+    assert lib.dass_bin_sort_workspace(1000, 5000, 10, C.byref(b)) == 0 and b.value > 0
+    # a workspace smaller than the query is reported as DASS_ERR_OOM
+    fake = C.c_void_p(16)
+    assert lib.dass_bin_sort(fake, 10, cams, 2, 16, fake, 100, fake, fake, fake, 8, None) == -3
+    # empty inputs are no-ops that succeed without launching
+    assert lib.dass_shift(0, None, None, None, None, None, None, None) == 0
+    assert lib.dass_preprocess(0, 0, None, None, None, None, None, None, cams, 2, 16, None, None) == 0

@@ -1,0 +1,227 @@
+"""GPU parity of the DASS stage kernels and of the per-stage driver against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import grad as og
+from oracle import stages as S
+from paper_2411_14847_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def cu(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+def test_shift_forward_backward(dass):
+    from paper_2411_14847_gb300 import dass as D
+    rng = np.random.default_rng(1)
+    n = 5000
+    means = rng.normal(size=(n, 3)).astype(np.float32)
+    quats = rng.normal(size=(n, 4)).astype(np.float32)
+    idx, off = synth.dynamic_split(n, 0.1, 3, dmu_std=0.05, dq_std=0.3)
+    om, oq = cu(means), cu(quats)
+    D.dass_shift(cu(idx, torch.int32), cu(off), cu(means), cu(quats), om, oq)
+    rm, rq = S.shift(means, quats, idx, off)
+    np.testing.assert_allclose(om.cpu().numpy(), rm.numpy(), atol=1e-6)
+    np.testing.assert_allclose(oq.cpu().numpy(), rq.numpy(), atol=2e-6)
+    static = np.setdiff1d(np.arange(n), idx)
+    assert np.array_equal(oq.cpu().numpy()[static], quats[static])
+    # backward: random upstream gradients of the shifted rows
+    gm = rng.normal(size=(len(idx), 3)).astype(np.float32)
+    gq = rng.normal(size=(len(idx), 4)).astype(np.float32)
+    doff = torch.empty((len(idx), 7), device="cuda")
+    D.dass_shift_bwd(cu(idx, torch.int32), cu(off), cu(quats), cu(gm), cu(gq), doff)
+    offt = torch.tensor(off, dtype=torch.float64, requires_grad=True)
+    m2, q2 = S.shift(means, quats, idx, offt)
+    (m2[idx] * torch.tensor(gm, dtype=torch.float64)).sum().add((q2[idx] * torch.tensor(gq, dtype=torch.float64)).sum()).backward()
+    assert rel_l2(doff.cpu().numpy(), offt.grad.numpy()) < 1e-5
+    # empty dynamic list is a no-op
+    D.dass_shift(cu(np.zeros(0), torch.int32), cu(np.zeros((0, 7))), cu(means), cu(quats), om, oq)
+
+
+def test_masked_adam(dass):
+    from paper_2411_14847_gb300 import dass as D
+    rng = np.random.default_rng(2)
+    p = rng.normal(size=(300, 7)).astype(np.float32)
+    rows = np.sort(rng.choice(300, 90, replace=False)).astype(np.int32)
+    lr = [1e-3] * 3 + [2e-3] * 4
+    tp, tm, tv = cu(p), torch.zeros((300, 7), device="cuda"), torch.zeros((300, 7), device="cuda")
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rp, rm, rv = p.astype(np.float64), np.zeros((300, 7)), np.zeros((300, 7))
+    for it in range(1, 4):
+        g = rng.normal(size=(300, 7)).astype(np.float32)
+        D.dass_adam(tp, cu(g), tm, tv, step, lr, rows=cu(rows, torch.int32))
+        rp, rm, rv = S.adam(rp, g, rm, rv, it, np.array(lr), rows=rows)
+    torch.cuda.synchronize()
+    assert int(step) == 3
+    np.testing.assert_allclose(tp.cpu().numpy(), rp, rtol=0, atol=2e-6)
+    other = np.setdiff1d(np.arange(300), rows)
+    assert np.array_equal(tp.cpu().numpy()[other], p[other])
+    np.testing.assert_allclose(tv.cpu().numpy(), rv, rtol=1e-4, atol=1e-9)
+
+
+@pytest.mark.parametrize("t", [3, 20])
+def test_inherit_copy(dass, t):
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene = synth.random_scene(4000, 3, 9)
+    rng = np.random.default_rng(4)
+    is_var = np.zeros(4000, np.uint8)
+    is_var[3000:] = 1
+    m = rng.normal(size=4000).astype(np.float32)
+    m[3100] = 0.0
+    g = raster.to_device(scene.arrays())
+    out = {k: torch.full_like(v, float("nan")) for k, v in g.items()}
+    var_out = torch.zeros(4000, dtype=torch.uint8, device="cuda")
+    remap = torch.empty(4000, dtype=torch.int32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(D.dass_inherit_workspace(4000), dtype=torch.uint8, device="cuda")
+    D.dass_inherit(g, cu(is_var, torch.uint8), cu(m), t % 20 == 0, out, var_out, remap, n_out, ws)
+    torch.cuda.synchronize()
+    ref, rvar, rremap = S.inherit(scene.arrays(), is_var, m, t)
+    k = int(n_out)
+    assert k == len(rvar)
+    for name in ref:
+        assert np.array_equal(out[name][:k].cpu().numpy(), ref[name]), name
+    assert np.array_equal(var_out[:k].cpu().numpy().astype(bool), rvar)
+    assert np.array_equal(remap.cpu().numpy(), rremap)
+
+
+def test_error_pass_and_selection(dass):
+    from paper_2411_14847_gb300 import dass as D
+    rng = np.random.default_rng(5)
+    cams = synth.arc_cameras(3, 4.0, 120, 90)
+    imgs = [rng.uniform(0, 1, (3, 90, 120)).astype(np.float32) for _ in cams]
+    tgts = [rng.uniform(0, 1, (3, 90, 120)).astype(np.float32) for _ in cams]
+    n = 20000
+    means = rng.uniform(-1.5, 1.5, (n, 3)).astype(np.float32)
+    is_var = (rng.uniform(size=n) < 0.1).astype(np.uint8)
+    x = cu(np.concatenate([i.reshape(-1) for i in imgs]))
+    y = cu(np.concatenate([i.reshape(-1) for i in tgts]))
+    s_err = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    emap = torch.empty(3 * 90 * 120, device="cuda")
+    gamma = torch.empty(3, dtype=torch.float32, device="cuda")
+    ws = torch.empty(D.dass_error_pass_workspace(cams), dtype=torch.uint8, device="cuda")
+    D.dass_error_pass(x, y, cams, 0.95, cu(means), cu(is_var, torch.uint8), s_err, ws, error_map=emap, gamma=gamma)
+    torch.cuda.synchronize()
+    Es = [S.error_map_f32(i, t) for i, t in zip(imgs, tgts)]
+    np.testing.assert_array_equal(emap.cpu().numpy(), np.concatenate([e.reshape(-1) for e in Es]))
+    gam = [S.percentile_lower(e, 0.95) for e in Es]
+    np.testing.assert_array_equal(gamma.cpu().numpy().view(np.uint32), np.array(gam, np.float32).view(np.uint32))
+    Ds = [S.error_bitmap(e, gm) for e, gm in zip(Es, gam)]
+    ref, amb = S.error_subset(means, cams, Ds, tie_eps=2e-3)
+    ref &= ~is_var.astype(bool)
+    got = s_err.cpu().numpy().astype(bool)
+    sure = ~amb
+    assert ref.sum() > 100
+    assert np.array_equal(got[sure], ref[sure])
+    # Eq. 4 selection on synthetic statistics (with value ties)
+    accum = (rng.integers(0, 50, n) * 1e-5).astype(np.float32)
+    count = rng.integers(0, 4, n).astype(np.int32)
+    for k_max in (100000, 700, 1):
+        sel = torch.empty(max(1, k_max), dtype=torch.int32, device="cuda")
+        nsel = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ws2 = torch.empty(D.dass_densify_select_workspace(n), dtype=torch.uint8, device="cuda")
+        D.dass_densify_select(cu(accum), cu(count, torch.int32), s_err, cu(is_var, torch.uint8), 1e-4, 5e-5, k_max,
+                              sel, nsel, ws2)
+        torch.cuda.synchronize()
+        gmean = S.mean_grad_f32(accum, count)
+        rsel = S.densify_select(gmean, got, ~is_var.astype(bool), 1e-4, 5e-5, k_max)
+        k = int(nsel)
+        assert k == len(rsel)
+        np.testing.assert_array_equal(sel[:k].cpu().numpy(), rsel)
+
+
+def test_spawn(dass):
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene = synth.random_scene(1000, 1, 12)
+    k_max = 64
+    cap = {k: np.concatenate([v, np.zeros((k_max,) + v.shape[1:], np.float32)]) for k, v in scene.arrays().items()}
+    g = raster.to_device(cap)
+    is_var = torch.zeros(1000 + k_max, dtype=torch.uint8, device="cuda")
+    sel = np.sort(np.random.default_rng(1).choice(1000, 40, replace=False)).astype(np.int32)
+    z = synth.standard_normal((1000, 3), 77)
+    n_total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    D.dass_spawn(g, 1000, is_var, cu(sel, torch.int32), cu([40], torch.int32), k_max, cu(z), n_total)
+    torch.cuda.synchronize()
+    assert int(n_total) == 1040
+    ref = S.spawn(scene.arrays(), sel, z)
+    for k in ref:
+        np.testing.assert_allclose(g[k][1000:1040].cpu().numpy(), ref[k], rtol=1e-5, atol=1e-6)
+    assert is_var[1000:1040].all() and not is_var[:1000].any() and not is_var[1040:].any()
+
+
+def test_densify_stats_accumulation(dass):
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene = synth.random_scene(1200, 0, 21, box=synth.ARC_BOX, log_scale_mean=-3.0)
+    cams = synth.arc_cameras(2, 4.0, 64, 48)
+    target = [np.zeros((3, 48, 64))] * 2
+    g = raster.to_device(scene.arrays())
+    fr = raster.Frame(cams, scene.n)
+    img = raster.render_autograd({k: v.clone().requires_grad_(True) for k, v in g.items()}, fr)
+    dimg = torch.empty_like(img)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    D.dass_loss(img.detach(), torch.zeros_like(img), cams, 0.0, dimg, loss, None)
+    fr.render_bwd(dimg)
+    accum = torch.zeros(scene.n, device="cuda")
+    count = torch.zeros(scene.n, dtype=torch.int32, device="cuda")
+    D.dass_densify_stats(scene.n, fr.splats, fr.splat_grads, cams, accum, count)
+    torch.cuda.synchronize()
+    ref = og.loss_grads(scene.arrays(), cams, 0, target, 0.0)
+    racc = np.zeros(scene.n)
+    rcnt = np.zeros(scene.n, np.int64)
+    for c, cam in enumerate(cams):
+        v = ref["visible"][c].numpy()
+        racc += np.where(v, S.ndc_grad_norm(ref["dmean2d"][c], cam.width, cam.height).numpy(), 0.0)
+        rcnt += v
+    assert np.mean(count.cpu().numpy() == rcnt) > 0.99
+    assert rel_l2(accum.cpu().numpy(), racc) < 1e-3
+
+
+def _step_setup(dass, n=2000, deg=1, n_cams=2, w=64, h=48, lam=0.2, seed=31, tile=16, batch=128):
+    from paper_2411_14847_gb300 import dass as D, raster, timestep
+    scene = synth.random_scene(n, deg, seed, box=synth.ARC_BOX, log_scale_mean=-3.0)
+    cams = synth.arc_cameras(n_cams, 4.0, w, h)
+    idx, off = synth.dynamic_split(n, 0.1, seed + 1, dmu_std=1e-3, dq_std=1e-3)
+    tgt_scene = synth.perturbed(scene, seed + 2)
+    targets = [t["image"].numpy() for t in og.render(tgt_scene.arrays(), cams, deg)]
+    st = timestep.ShiftStage(raster.to_device(scene.arrays()), cams, cu(np.concatenate([t.reshape(-1) for t in targets])),
+                             cu(idx, torch.int32), cu(off), tile=tile, batch=batch, lambda_dssim=lam)
+    return scene, cams, idx, off, targets, st
+
+
+def test_step_gradient_parity_and_update(dass):
+    from paper_2411_14847_gb300 import dass as D
+    scene, cams, idx, off, targets, st = _step_setup(dass)
+    st.run(1, D.STEP_BATCHED)
+    ref = og.loss_grads(scene.arrays(), cams, 1, targets, 0.2, dyn_idx=idx, offsets=off)
+    assert float(st.loss) == pytest.approx(ref["loss"], rel=1e-4)
+    g = st.offset_grad.cpu().numpy()
+    rg = ref["offsets"].numpy()
+    assert rel_l2(g, rg) < 1e-3
+    # first Adam step from zero moments moves each offset by lr * sign(g)
+    moved = st.offsets.cpu().numpy() - off
+    strong = np.abs(rg) > 1e-2 * np.abs(rg).max()
+    np.testing.assert_allclose(moved[strong], -1e-3 * np.sign(rg[strong]), rtol=1e-3)
+
+
+def test_step_plain_equals_batched(dass):
+    from paper_2411_14847_gb300 import dass as D
+    _, _, _, off, _, a = _step_setup(dass, n_cams=3)
+    _, _, _, _, _, b = _step_setup(dass, n_cams=3)
+    a.run(1, D.STEP_BATCHED)
+    b.run(1, D.STEP_PLAIN)
+    assert float(a.loss) == pytest.approx(float(b.loss), rel=1e-5)
+    assert rel_l2(a.offset_grad.cpu().numpy(), b.offset_grad.cpu().numpy()) < 1e-4
+    a.run(4, D.STEP_BATCHED)
+    b.run(4, D.STEP_PLAIN)
+    assert float(a.loss) == pytest.approx(float(b.loss), rel=1e-3)

@@ -445,7 +445,7 @@ def test_densify_select_eq4():
     base = np.array([1, 1, 1, 1, 1, 0], bool)
     # tau_pos = 2.5: {0, 2, 3}; S_err n g > 0.8: {1, 3}; var row 5 excluded
     sel = S.densify_select(g, s_err, base, 2.5, 0.8, 10)
-    assert sel.tolist() == [0, 2, 3, 1]
+    assert sel.tolist() == [0, 1, 2, 3]
     assert S.densify_select(g, s_err, base, 2.5, 0.8, 2).tolist() == [0, 2]
 
 
