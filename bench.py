@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Seconds per timestep of the DASS streaming hot path on one GB300 (synthetic multi-view scene).
+
+Workload (batched multi-view timestep): 300k Gaussians, SH degree 3, FP32, 20 cameras of
+1352x1014 on a forward-facing arc (yaw -30..+30 deg, radius 4), 10% of the Gaussians dynamic.
+One step = one timestep of the streaming reconstruction: selective-inheritance copy ->
+shift stage of 150 iterations (shift, preprocess, bin/sort, forward, L1 + 0.2 D-SSIM, backward,
+preprocess backward, shift backward, densification statistics, masked Adam), all cameras per
+launch, one iteration captured as a CUDA graph and replayed -> error pass (95th percentile),
+Eq. 4 selection (<= 5k) and spawn. Inputs are resident in HBM when the timed region starts;
+the working set (~1.5 GB) is far larger than L2 (129 MB), so L2 is not flushed.
+
+`--impl reference` times the FP64 CPU oracle on this host's cores on a bounded sample of the
+same workload (one camera's projection plus a pixel sample, forward + backward) and
+extrapolates to seconds per timestep.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s/timestep fwd+bwd @300k Gaussians x20 views; render p50/p99 ms; batched vs plain"
+UNIT = "s/timestep"
+WORKLOAD = "batched multi-view timestep: 300k Gaussians SH3 FP32, 20 cams 1352x1014 arc, 10% dynamic"
+# Algorithmic FP32 operations per (pixel, Gaussian) pair of the compositing kernels: evaluating
+# alpha costs 11 (2 sub, 4 mul, 2 fma, o*G, 1-alpha ... see the design doc); an added pair costs 20 in
+# the forward (alpha, T update, weight, 3 colour FMAs) and 64 in the backward (alpha, T_j,
+# weight, colour and alpha gradients, behind-colour update, 5 geometry gradients, 9 reduction adds).
+FLOP_EVAL = 11
+FLOP_FWD_ADD = 20
+FLOP_BWD_ADD = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dass", choices=["dass", "reference"])
+    ap.add_argument("--iters", type=int, default=150, help="shift-stage iterations per timestep")
+    ap.add_argument("--n", type=int, default=300_000)
+    ap.add_argument("--cams", type=int, default=20)
+    ap.add_argument("--width", type=int, default=1352)
+    ap.add_argument("--height", type=int, default=1014)
+    ap.add_argument("--tile", type=int, default=0, help="0 = autotune")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--plain-iters", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--render-reps", type=int, default=50)
+    ap.add_argument("--cpu-pixels", type=int, default=384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        out.update(sm_mhz=statistics.median(load) if load else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(scene, cams, n_pixels, seed=0):
+    """Time the FP64 oracle on one camera: projection of all Gaussians, then forward/backward
+    of two pixel samples (n/2 and n pixels) whose difference gives the per-pixel cost.
+    Returns (seconds per iteration extrapolated, sample seconds, threads, details)."""
+    import torch
+    from oracle import grad as og
+
+    cam = cams[0]
+    rng = np.random.default_rng(seed)
+    arrays = scene.arrays()
+
+    def vjp(p):
+        px = rng.integers(0, cam.width, p).astype(np.float64)
+        py = rng.integers(0, cam.height, p).astype(np.float64)
+        g = np.sign(rng.normal(size=(p, 3))) / (3.0 * cam.width * cam.height)
+        t0 = time.perf_counter()
+        og.image_vjp(arrays, [cam], scene.sh_degree, [(px, py, g)])
+        return time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    og.project_all(arrays, [cam], scene.sh_degree)
+    t_proj = time.perf_counter() - t0
+    half = max(1, n_pixels // 2)
+    t_half = vjp(half)
+    t_full = vjp(2 * half)
+    t_pix = max(t_full - t_half, 1e-9) / half
+    t_fixed = max(t_full - 2 * half * t_pix, 0.0)      # projection forward + backward of one camera
+    total_px = sum(c.width * c.height for c in cams)
+    per_iter = len(cams) * t_fixed + total_px * t_pix
+    return per_iter, t_proj + t_half + t_full, torch.get_num_threads(), dict(
+        t_camera_fixed_s=round(t_fixed, 4), t_pixel_ms=round(1e3 * t_pix, 4))
+
+
+def run_reference(args):
+    import torch
+    from paper_2411_14847_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, cams, _, _ = synth.config_c(n=args.n, n_cams=args.cams, width=args.width, height=args.height)
+    for _ in range(args.warmup):
+        oracle_sample(scene, cams, max(16, args.cpu_pixels // 8))
+    vals, secs = [], 0.0
+    for k in range(args.steps):
+        per_iter, s, threads, det = oracle_sample(scene, cams, args.cpu_pixels, seed=k)
+        vals.append(per_iter * args.iters)
+        secs += s
+    v = float(statistics.median(vals))
+    sample = (f"camera 0 of {args.cams}: projection of all {args.n} Gaussians + forward/backward of "
+              f"{args.cpu_pixels // 2} and {2 * (args.cpu_pixels // 2)} sampled pixels per step; extrapolated to {args.cams} cams x "
+              f"{args.width}x{args.height} px x {args.iters} iterations")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "iters_per_timestep": args.iters, "extrapolated": True},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2411_14847_gb300 import build, dass as D, raster, synth
+    from paper_2411_14847_gb300.autotune import autotune
+    from paper_2411_14847_gb300.timestep import ShiftStage, Timestep
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.ensure_built()
+    D.load()
+    dev = "cuda"
+
+    # ---------------- workload (replicas: every rank runs its own timestep stream)
+    scene, cams, dyn_idx, offsets0 = synth.config_c(seed=1003 + rank, n=args.n, n_cams=args.cams,
+                                                     width=args.width, height=args.height)
+    g0 = raster.to_device(scene.arrays())
+    fr = raster.Frame(cams, scene.n, tile=16, batch=128)
+    tgt_scene = synth.perturbed(scene, 2003 + rank)
+    fr.render(raster.to_device(tgt_scene.arrays()))
+    targets = fr.image.clone()
+    del fr
+    dyn_t = torch.as_tensor(dyn_idx, dtype=torch.int32, device=dev)
+    off_t = torch.as_tensor(offsets0, device=dev)
+    z = torch.as_tensor(synth.standard_normal((args.n + 100_000, 3), 4003 + rank), device=dev)
+
+    # ---------------- autotune tile x batch on the real workload (not timed)
+    if args.tile and args.batch:
+        tile, batch, table = args.tile, args.batch, None
+    else:
+        (tile, batch), table = autotune(g0, cams, targets, dyn_t, off_t, iters=3)
+
+    k_max = 5000
+    n_max = args.n + k_max * (args.warmup + args.steps + args.e2e_steps + 3)
+    ts = Timestep(cams, n_max, 3, tile=tile, batch=batch, lambda_dssim=0.2, n_shift=args.iters, k_max=k_max)
+    ts.load(scene.arrays())
+
+    def one_timestep(t, tgt):
+        return ts.run(t, tgt, dyn_t, off_t.clone(), z=z)
+
+    t = 1
+    for _ in range(args.warmup):
+        one_timestep(t, targets)
+        t += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---------------- timed region: K whole timesteps, device time by CUDA events
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = D.dass_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record()
+    results = []
+    for _ in range(args.steps):
+        results.append(one_timestep(t, targets))
+        t += 1
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = D.dass_kernel_launches() - l0
+    clk = clocks.stop()
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = ms_max / 1e3 / (args.steps * world)
+
+    # ---------------- dominant kernels, timed standalone on the last iteration's buffers
+    stage = results[-1]["stage"]
+    sfr = stage.frame
+    work = torch.zeros(4, dtype=torch.int64, device=dev)
+    D.dass_render_work(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch, sfr.image, sfr.T_final,
+                       sfr.n_last, work)
+    torch.cuda.synchronize()
+    n_eval, n_add, n_bwd, n_pix = (int(v) for v in work.tolist())
+    s_ = torch.cuda.current_stream()
+
+    def timed(fn, reps=10):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(s_)
+        for _ in range(reps):
+            fn()
+        b.record(s_)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # backward first (render_fwd recomputes the same T_final/n_last, so inputs stay consistent)
+    bwd_ms = timed(lambda: D.dass_render_bwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
+                                             sfr.T_final, sfr.n_last, stage.dL_dimage, sfr.splat_grads))
+    fwd_ms = timed(lambda: D.dass_render_fwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
+                                             sfr.image, sfr.T_final, sfr.n_last))
+    n_pairs = int(sfr.counters[0].item())
+    sort_ms = timed(lambda: D.dass_bin_sort(sfr.splats, sfr.n, cams, tile, sfr.pair_rec, sfr.tile_ranges,
+                                            sfr.counters, sfr.workspace), reps=5)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    mhz = clk["sm_mhz"] or 2070.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12   # TFLOP/s
+    bwd_flop = FLOP_EVAL * n_bwd + (FLOP_BWD_ADD - FLOP_EVAL) * n_add
+    fwd_flop = FLOP_EVAL * n_eval + (FLOP_FWD_ADD - FLOP_EVAL) * n_add
+    bwd_tf = bwd_flop / (bwd_ms * 1e-3) / 1e12
+    fwd_tf = fwd_flop / (fwd_ms * 1e-3) / 1e12
+    dom = "render_bwd" if bwd_ms >= fwd_ms else "render_fwd"
+    ach = bwd_tf if dom == "render_bwd" else fwd_tf
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
+                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)",
+                "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
+                "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
+    kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
+               "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
+               "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "pairs_evaluated_bwd": n_bwd,
+               "bin_sort_bytes_per_pair": None}
+
+    # ---------------- plain form (one launch per camera, no graph) vs batched, per iteration
+    plain_st = ShiftStage(ts.view(), cams, targets, dyn_t, off_t.clone(), tile=tile, batch=batch, lambda_dssim=0.2)
+    plain_st.run(1, D.STEP_PLAIN)
+    torch.cuda.synchronize()
+    a0 = time.perf_counter()
+    plain_st.run(args.plain_iters, D.STEP_PLAIN)
+    plain_ms = (time.perf_counter() - a0) * 1e3 / args.plain_iters
+    plain_st.run(1, D.STEP_BATCHED)
+    torch.cuda.synchronize()
+    a0 = time.perf_counter()
+    plain_st.run(args.plain_iters, D.STEP_BATCHED)
+    batched_ms = (time.perf_counter() - a0) * 1e3 / args.plain_iters
+    del plain_st
+    overhead_s = max(0.0, value - batched_ms * 1e-3 * args.iters)
+    plain = {"ms_per_iter": round(plain_ms, 3), "batched_ms_per_iter": round(batched_ms, 3),
+             "s_per_timestep": round(plain_ms * 1e-3 * args.iters + overhead_s, 4), "extrapolated": True,
+             "speedup_batched": round(plain_ms / batched_ms, 3)}
+
+    # ---------------- render latency: one novel 1352x1014 view, forward only, p50/p99
+    rfr = raster.Frame(cams[:1], ts.n, tile=tile, batch=batch)
+    gv = ts.view()
+    rfr.render(gv)
+    lat = []
+    for _ in range(args.render_reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rfr.project(gv)
+        rfr.bin_sort(grow=False)
+        rfr.render_fwd()
+        b.record()
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(b))
+    lat.sort()
+    render = {"p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+              "view": f"{cams[0].width}x{cams[0].height}", "gaussians": ts.n}
+    del rfr
+
+    # ---------------- end to end through the public API with host buffers
+    host_tgt = targets.cpu().pin_memory()
+    dev_tgt = torch.empty_like(targets)
+    one_timestep(t, targets)
+    t += 1
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h2d = d2h = 0
+    a.record()
+    for _ in range(args.e2e_steps):
+        dev_tgt.copy_(host_tgt, non_blocking=True)
+        r = ts.run(t, dev_tgt, dyn_t, off_t.clone(), z=z)
+        t += 1
+        gv = ts.view()
+        host = {k: v.to("cpu") for k, v in gv.items()}
+        loss_h = r["loss"]
+        h2d = host_tgt.numel() * 4
+        d2h = sum(v.numel() * 4 for v in host.values()) + 8
+    b.record()
+    torch.cuda.synchronize()
+    e2e_s = a.elapsed_time(b) / 1e3 / args.e2e_steps
+
+    # ---------------- CPU baseline (oracle) on a bounded sample, rank 0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_iter, secs, threads, det = oracle_sample(scene, cams, args.cpu_pixels)
+        cpu = {"value": per_iter * args.iters, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"camera 0 projection of {args.n} Gaussians + fwd/bwd of {args.cpu_pixels // 2} and "
+                          f"{2 * (args.cpu_pixels // 2)} sampled "
+                          f"pixels ({secs:.1f} s), extrapolated to {args.cams} cams x {args.width}x{args.height} "
+                          f"x {args.iters} iterations"), **det}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "gaussians": args.n, "cams": args.cams,
+                           "resolution": f"{args.width}x{args.height}", "iters_per_timestep": args.iters,
+                           "tile": tile, "batch": batch, "autotune_ms_per_iter": table,
+                           "l2": "not flushed: per-iteration working set ~1.5 GB >> 129 MB L2",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
+                "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
+                "plain": plain, "render_latency": render,
+                "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,10 @@ const char* dass_status_string(int status);
 /* Text of the last CUDA error seen by this thread (empty if none). */
 const char* dass_last_error(void);
 
+/* Number of libdass kernels this host thread has enqueued so far (a CUDA-graph replay counts
+ * every kernel it runs). Used to report the kernel launches inside a timed region. */
+int64_t dass_kernel_launches(void);
+
 /* Host helper: total tiles and pixels of a camera set at tile size B. */
 int dass_tile_layout(const dass_camera* cams, int n_cams, int tile, int32_t* tiles_total,
                      int64_t* pixels_total);
@@ -144,6 +148,15 @@ int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const ui
                     const dass_camera* cams /* host */, int n_cams, int tile, int batch,
                     const float* bg /* host, 3 */, float* image, float* T_final, int32_t* n_last,
                     void* stream);
+
+/* Measurement variant of dass_render_fwd (same outputs, black background) that also counts
+ * the algorithmic work of the compositing: work[0] = (pixel, Gaussian) pairs evaluated by the
+ * forward up to each pixel's own stop, work[1] = pairs added to a pixel, work[2] = pairs the
+ * backward evaluates (each pixel's list prefix up to its last added Gaussian), work[3] =
+ * pixels. work: device uint64[4], zeroed by the call. Not used on the timed path. */
+int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                     const dass_camera* cams /* host */, int n_cams, int tile, int batch, float* image,
+                     float* T_final, int32_t* n_last, uint64_t* work, void* stream);
 
 /* Reverse-order backward of dass_render_fwd. Recomputes alpha from the saved T_final and
  * n_last (T_j = T_{j+1} / (1 - alpha_j)); per Gaussian the 9 gradients are reduced across the

@@ -24,7 +24,8 @@ size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
-                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st);
+                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
+                      unsigned long long* work = nullptr);
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
                       dass_splat_grad* gsplat, cudaStream_t st);
@@ -55,6 +56,11 @@ int spawn_launch(long long n, int deg, float* means, float* ls, float* quats, fl
                  cudaStream_t st);
 
 static thread_local char g_err[512] = {0};
+static thread_local long long g_launches = 0;
+
+void count_launch(long long k) { g_launches += k; }
+long long launches_so_far() { return g_launches; }
+void set_launches(long long v) { g_launches = v; }
 
 void set_last_error(const char* what, cudaError_t e) {
     snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
@@ -139,6 +145,8 @@ DASS_API const char* dass_status_string(int s) {
 
 DASS_API const char* dass_last_error(void) { return dass::g_err; }
 
+DASS_API int64_t dass_kernel_launches(void) { return (int64_t)dass::launches_so_far(); }
+
 DASS_API int dass_tile_layout(const dass_camera* cams, int n_cams, int tile, int32_t* tiles_total,
                               int64_t* pixels_total) {
     static thread_local CamTable ct;
@@ -191,6 +199,18 @@ DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec,
     if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
     return render_fwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), image, T_final, n_last,
                              as_stream(stream));
+}
+
+DASS_API int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                              const dass_camera* cams, int n_cams, int tile, int batch, float* image, float* T_final,
+                              int32_t* n_last, uint64_t* work, void* stream) {
+    if (!batch_ok(batch) || !tile_ranges || !image || !T_final || !n_last || !work) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    DASS_CHECK_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t) * 4, st));
+    return render_fwd_launch(splats, pair_rec, tile_ranges, ct, batch, make_float3(0.f, 0.f, 0.f), image, T_final,
+                             n_last, st, reinterpret_cast<unsigned long long*>(work));
 }
 
 DASS_API int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
@@ -392,7 +412,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
         rc = bin_sort_launch(d->splats, n_rec, ct, d->pair_rec, d->pair_capacity, d->tile_ranges,
                              (long long*)d->counters, bin_ws, p.bin_ws, st);
         if (rc) return rc;
-        or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters);
+        or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters); count_launch();
         rc = render_fwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image, d->T_final,
                                d->n_last, st);
         if (rc) return rc;
@@ -425,7 +445,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
             rc = bin_sort_launch(sp, d->n, ct, d->pair_rec, d->pair_capacity, d->tile_ranges, (long long*)d->counters,
                                  bin_ws, p.bin_ws, st);
             if (rc) return rc;
-            or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters);
+            or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters); count_launch();
             rc = render_fwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image + 3 * pb,
                                    d->T_final + pb, d->n_last + pb, st);
             if (rc) return rc;
@@ -492,7 +512,10 @@ DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* str
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         DASS_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        long long l0 = launches_so_far();
         int rc = step_iteration(d, p, mode, st);
+        long long per_iter = launches_so_far() - l0;
+        set_launches(l0 + per_iter * (long long)n_iters);   // every replay runs the captured kernels
         cudaError_t ec = cudaStreamEndCapture(st, &graph);
         if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
         if (ec != cudaSuccess) { set_last_error("cudaStreamEndCapture", ec); return DASS_ERR_CUDA; }

@@ -15,6 +15,10 @@ namespace dass {
 
 void set_last_error(const char* what, cudaError_t e);
 int check_launch(const char* what);   // returns DASS_OK or DASS_ERR_CUDA
+// Number of kernels this thread has enqueued (graph replays count every captured kernel).
+void count_launch(long long k = 1);
+long long launches_so_far();
+void set_launches(long long v);
 
 #define DASS_CHECK_CUDA(call)                                              \
     do {                                                                   \

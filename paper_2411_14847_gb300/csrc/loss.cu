@@ -233,16 +233,16 @@ int loss_launch(const float* image, const float* target, const CamTable& ct, flo
     }
     if (lambda == 0.f) {
         dim3 grid(div_up(maxP, 256), 3 * ct.n);
-        l1_kernel<<<grid, 256, 0, st>>>(ct, a);
+        l1_kernel<<<grid, 256, 0, st>>>(ct, a); count_launch();
         return check_launch("l1_kernel");
     }
     if (ws_bytes < loss_workspace_bytes(ct)) return DASS_ERR_OOM;
     Window w = make_window();
     dim3 grid(div_up(maxW, kT), div_up(maxH, kT), 3 * ct.n);
-    ssim_fwd_kernel<<<grid, 256, 0, st>>>(ct, w, a);
+    ssim_fwd_kernel<<<grid, 256, 0, st>>>(ct, w, a); count_launch();
     int rc = check_launch("ssim_fwd_kernel");
     if (rc) return rc;
-    ssim_bwd_kernel<<<grid, 256, 0, st>>>(ct, w, a);
+    ssim_bwd_kernel<<<grid, 256, 0, st>>>(ct, w, a); count_launch();
     return check_launch("ssim_bwd_kernel");
 }
 

@@ -418,7 +418,7 @@ __global__ void densify_stats_kernel(long long n, CamTable ct, const dass_splat*
 template <int K>
 int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass_splat* out, cudaStream_t st) {
     int threads = 128;
-    preprocess_kernel<K><<<div_up(n, threads), threads, 0, st>>>(n, deg, prm, ct, out);
+    preprocess_kernel<K><<<div_up(n, threads), threads, 0, st>>>(n, deg, prm, ct, out); count_launch();
     return check_launch("preprocess_kernel");
 }
 
@@ -428,7 +428,7 @@ int launch_pre_bwd(long long n, int deg, const Params& prm, const CamTable& ct, 
                    const Grads& gr, cudaStream_t st) {
     int threads = 128;
     preprocess_bwd_kernel<K><<<div_up(n_rows, threads), threads, 0, st>>>(n, deg, prm, ct, sp, gsp, rows, n_rows,
-                                                                          flags, acc, gr);
+                                                                          flags, acc, gr); count_launch();
     return check_launch("preprocess_bwd_kernel");
 }
 
@@ -467,7 +467,7 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
 int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
                          float* accum, int* count, cudaStream_t st) {
     if (n <= 0) return DASS_OK;
-    densify_stats_kernel<<<div_up(n, 256), 256, 0, st>>>(n, ct, splats, gsp, accum, count);
+    densify_stats_kernel<<<div_up(n, 256), 256, 0, st>>>(n, ct, splats, gsp, accum, count); count_launch();
     return check_launch("densify_stats_kernel");
 }
 

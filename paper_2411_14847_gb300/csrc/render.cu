@@ -23,12 +23,16 @@ __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splat
     raw = make_float4(s0.z, s0.w, s1.x, 0.f);
 }
 
-template <int TILE, int BATCH>
+// COUNT = true is a separate instantiation used only to measure the algorithmic work of a
+// render (pairs each pixel evaluates before its own stop, pairs it adds, and pairs the
+// backward evaluates); the timed kernels are the COUNT = false instantiations.
+template <int TILE, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat* __restrict__ splats,
                                                                const uint32_t* __restrict__ pair_rec,
                                                                const uint32_t* __restrict__ ranges, CamTable ct,
                                                                float3 bg, float* __restrict__ image,
-                                                               float* __restrict__ T_final, int* __restrict__ n_last) {
+                                                               float* __restrict__ T_final, int* __restrict__ n_last,
+                                                               unsigned long long* __restrict__ work) {
     constexpr int NT = TILE * TILE;
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
@@ -45,6 +49,7 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int last = -1;
     bool done = !inside;
+    unsigned long long n_eval = 0, n_add = 0;
     for (uint32_t base = start; base < end; base += BATCH) {
         if (__syncthreads_count(done) == NT) break;
         const int cnt = min((uint32_t)BATCH, end - base);
@@ -60,9 +65,11 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat
                 const float dx = __fsub_rn(fx, A.x), dy = __fsub_rn(fy, A.y);
                 const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
                 const float alpha = splat_alpha(Bv.y, G);
+                if (COUNT) ++n_eval;
                 if (alpha < kAlphaMin) continue;
                 const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
                 if (test < kTStop) { done = true; break; }
+                if (COUNT) ++n_add;
                 const float w = __fmul_rn(alpha, T);
                 C0 = __fmaf_rn(Bv.z, w, C0);
                 C1 = __fmaf_rn(Bv.w, w, C1);
@@ -81,6 +88,13 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat
         img[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
         T_final[cam.pix_base + pix] = T;
         n_last[cam.pix_base + pix] = last;
+    }
+    if (COUNT) {
+        unsigned long long n_bwd = last >= 0 ? (unsigned long long)(last - (int)start + 1) : 0ull;
+        atomicAdd(work + 0, n_eval);
+        atomicAdd(work + 1, n_add);
+        atomicAdd(work + 2, n_bwd);
+        if (inside) atomicAdd(work + 3, 1ull);
     }
 }
 
@@ -236,9 +250,15 @@ __global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(
 
 template <int TILE, int BATCH>
 int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
-               float* img, float* tf, int* nl, cudaStream_t st) {
+               float* img, float* tf, int* nl, unsigned long long* work, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
-    render_fwd_kernel<TILE, BATCH><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl);
+    if (work)
+        render_fwd_kernel<TILE, BATCH, true><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
+                                                                                    work);
+    else
+        render_fwd_kernel<TILE, BATCH, false><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
+                                                                                     nullptr);
+    count_launch();
     return check_launch("render_fwd_kernel");
 }
 
@@ -247,6 +267,7 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
                const float* tf, const int* nl, const float* dimg, dass_splat_grad* gs, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     render_bwd_kernel<TILE, BATCH><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg, gs);
+    count_launch();
     return check_launch("render_bwd_kernel");
 }
 
@@ -267,8 +288,9 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
     }
 
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
-                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st) {
-    DASS_DISPATCH(launch_fwd, splats, pair_rec, ranges, ct, bg, image, T_final, n_last, st)
+                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
+                      unsigned long long* work) {
+    DASS_DISPATCH(launch_fwd, splats, pair_rec, ranges, ct, bg, image, T_final, n_last, work, st)
 }
 
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,

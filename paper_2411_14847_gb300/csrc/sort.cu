@@ -326,9 +326,9 @@ SortScratch carve(Carver& cv, long long n_rec, long long cap) {
 int scan_u32(const uint32_t* in, uint32_t* out, const long long* len_dev, long long len_cap,
              unsigned long long* partial, long long* total, cudaStream_t st) {
     int nb = div_up(len_cap > 0 ? len_cap : 1, kScanTile);
-    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, len_dev, partial);
-    scan_partials_kernel<<<1, 1024, 0, st>>>(partial, len_dev, total);
-    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, len_dev, partial);
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, len_dev, partial); count_launch();
+    scan_partials_kernel<<<1, 1024, 0, st>>>(partial, len_dev, total); count_launch();
+    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, len_dev, partial); count_launch();
     return check_launch("scan_u32");
 }
 
@@ -347,10 +347,10 @@ int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const lon
         int shift = p * dbits;
         int db = dbits;
         if (shift + db > bits) db = bits - shift;
-        radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kin, n_dev, s.hist, s.scal + 1, shift, db);
+        radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kin, n_dev, s.hist, s.scal + 1, shift, db); count_launch();
         int rc = scan_u32(s.hist, s.hist, s.scal + 1, hist_cap, s.partial, nullptr, st);
         if (rc) return rc;
-        radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kin, vin, kout, vout, n_dev, s.hist, shift, db);
+        radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kin, vin, kout, vout, n_dev, s.hist, shift, db); count_launch();
         int lc = check_launch("radix_pass");
         if (lc) return lc;
         uint32_t* tk = kin; kin = kout; kout = tk;
@@ -385,8 +385,8 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
         DASS_CHECK_CUDA(cudaMemsetAsync(counters, 0, sizeof(long long) * 3, st));
         return DASS_OK;
     }
-    set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec);
-    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.kA, s.vA, s.counts);
+    set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec); count_launch();
+    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.kA, s.vA, s.counts); count_launch();
     int rc = check_launch("bin_count");
     if (rc) return rc;
     // 1) depth digits on the records (32 bits)
@@ -395,7 +395,7 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
     if (rc) return rc;
     uint32_t* order = set == 0 ? s.vA : s.vB;
     // 2) pair offsets in depth order
-    gather_counts_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(order, s.counts, s.offsets, n_rec);
+    gather_counts_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(order, s.counts, s.offsets, n_rec); count_launch();
     rc = scan_u32(s.offsets, s.offsets, s.scal + 0, n_rec, s.partial, s.scal + 2, st);
     if (rc) return rc;
     // 3) duplicate into tile-keyed pairs (stored count -> counters[2])
@@ -406,7 +406,7 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
     uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
     uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
     duplicate_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, order, s.offsets, s.scal + 2, cap,
-                                                         k_start, v_start, counters);
+                                                         k_start, v_start, counters); count_launch();
     rc = check_launch("duplicate");
     if (rc) return rc;
     // 4) tile digits on the pairs
@@ -417,7 +417,7 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
         rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
     if (rc) return rc;
     // 5) tile ranges
-    tile_ranges_kernel<<<div_up(cap, 256), 256, 0, st>>>(k_out, m_dev, tile_ranges);
+    tile_ranges_kernel<<<div_up(cap, 256), 256, 0, st>>>(k_out, m_dev, tile_ranges); count_launch();
     return check_launch("tile_ranges");
 }
 

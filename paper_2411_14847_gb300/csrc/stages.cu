@@ -344,14 +344,14 @@ struct Carve {
 int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats,
                  float* om, float* oq, cudaStream_t st) {
     if (n_dyn <= 0) return DASS_OK;
-    shift_fwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, means, quats, om, oq);
+    shift_fwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, means, quats, om, oq); count_launch();
     return check_launch("shift_fwd_kernel");
 }
 
 int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
                      const float* dq, float* doff, cudaStream_t st) {
     if (n_dyn <= 0) return DASS_OK;
-    shift_bwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, quats, dm, dq, doff);
+    shift_bwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, quats, dm, dq, doff); count_launch();
     return check_launch("shift_bwd_kernel");
 }
 
@@ -362,12 +362,12 @@ int adam_launch(long long n_sel, int width, const int* rows, float* p, const flo
     for (int k = 0; k < 16; ++k) l.v[k] = k < width ? lr[k] : 0.f;
     long long tot = n_sel * width;
     if (tot > 0) {
-        adam_kernel<<<div_up(tot, 256), 256, 0, st>>>(n_sel, width, rows, p, g, m, v, step_dev, l, b1, b2, eps);
+        adam_kernel<<<div_up(tot, 256), 256, 0, st>>>(n_sel, width, rows, p, g, m, v, step_dev, l, b1, b2, eps); count_launch();
         int rc = check_launch("adam_kernel");
         if (rc) return rc;
     }
     if (inc) {
-        step_inc_kernel<<<1, 1, 0, st>>>(step_dev);
+        step_inc_kernel<<<1, 1, 0, st>>>(step_dev); count_launch();
         return check_launch("step_inc_kernel");
     }
     return DASS_OK;
@@ -397,8 +397,8 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
         DASS_CHECK_CUDA(cudaMemsetAsync(n_out, 0, sizeof(long long), st));
         return DASS_OK;
     }
-    set_i64_kernel<<<1, 1, 0, st>>>(sc + 2, n);
-    inherit_flags_kernel<<<div_up(n, 256), 256, 0, st>>>(n, is_var, m, erase, fb, fv);
+    set_i64_kernel<<<1, 1, 0, st>>>(sc + 2, n); count_launch();
+    inherit_flags_kernel<<<div_up(n, 256), 256, 0, st>>>(n, is_var, m, erase, fb, fv); count_launch();
     int rc = check_launch("inherit_flags");
     if (rc) return rc;
     rc = scan_u32_public(fb, sb, sc + 2, n, part, sc + 0, st);
@@ -407,7 +407,7 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
     if (rc) return rc;
     int K3 = 3 * (deg + 1) * (deg + 1);
     inherit_scatter_kernel<<<div_up(n, 256), 256, 0, st>>>(n, K3, fb, fv, sb, sv, sc, means, ls, quats, logit, sh, om,
-                                                           ols, oq, ologit, osh, ovar, remap, n_out);
+                                                           ols, oq, ologit, osh, ovar, remap, n_out); count_launch();
     return check_launch("inherit_scatter");
 }
 
@@ -445,15 +445,15 @@ int error_pass_launch(const float* img, const float* tgt, const CamTable& ct, do
     }
     DASS_CHECK_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * ct.n, st));
     DASS_CHECK_CUDA(cudaMemsetAsync(prefix, 0, sizeof(uint32_t) * ct.n, st));
-    set_ranks_kernel<<<1, DASS_MAX_CAMERAS, 0, st>>>(sg, ct.n, rank);
+    set_ranks_kernel<<<1, DASS_MAX_CAMERAS, 0, st>>>(sg, ct.n, rank); count_launch();
     dim3 g1(div_up(maxP, 256), ct.n);
-    error_map_kernel<<<g1, 256, 0, st>>>(img, tgt, ct, E, keys);
+    error_map_kernel<<<g1, 256, 0, st>>>(img, tgt, ct, E, keys); count_launch();
     int rc = check_launch("error_map");
     if (rc) return rc;
     dim3 g2(64, ct.n);
     for (int shift = 24; shift >= 0; shift -= 8) {
-        select_hist_kernel<<<g2, 256, 0, st>>>(keys, sg, prefix, hist, shift);
-        select_decide_kernel<<<ct.n, 256, 0, st>>>(hist, prefix, rank, neq, shift);
+        select_hist_kernel<<<g2, 256, 0, st>>>(keys, sg, prefix, hist, shift); count_launch();
+        select_decide_kernel<<<ct.n, 256, 0, st>>>(hist, prefix, rank, neq, shift); count_launch();
         rc = check_launch("error_select");
         if (rc) return rc;
     }
@@ -461,7 +461,7 @@ int error_pass_launch(const float* img, const float* tgt, const CamTable& ct, do
         DASS_CHECK_CUDA(cudaMemcpyAsync(gamma, prefix, sizeof(uint32_t) * ct.n, cudaMemcpyDeviceToDevice, st));
     }
     if (n > 0) {
-        s_err_kernel<<<div_up(n, 256), 256, 0, st>>>(n, means, is_var, ct, E, prefix, s_err);
+        s_err_kernel<<<div_up(n, 256), 256, 0, st>>>(n, means, is_var, ct, E, prefix, s_err); count_launch();
         return check_launch("s_err");
     }
     return DASS_OK;
@@ -493,13 +493,13 @@ int select_launch(long long n, const float* accum, const int* count, const uint8
         DASS_CHECK_CUDA(cudaMemsetAsync(n_selected, 0, sizeof(int), st));
         return DASS_OK;
     }
-    set_i64_kernel<<<1, 1, 0, st>>>(sc + 2, n);
+    set_i64_kernel<<<1, 1, 0, st>>>(sc + 2, n); count_launch();
     DASS_CHECK_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256, st));
     DASS_CHECK_CUDA(cudaMemsetAsync(prefix, 0, sizeof(uint32_t) * 4, st));
     DASS_CHECK_CUDA(cudaMemsetAsync(n_cand, 0, sizeof(unsigned long long) * 2, st));
     int nb = div_up(n, 256);
-    select_keys_kernel<<<nb, 256, 0, st>>>(n, accum, count, s_err, is_var, tau_pos, tau_err, keys, n_cand);
-    select_prepare_kernel<<<1, 1, 0, st>>>(n, n_cand, k_max, sc + 0);
+    select_keys_kernel<<<nb, 256, 0, st>>>(n, accum, count, s_err, is_var, tau_pos, tau_err, keys, n_cand); count_launch();
+    select_prepare_kernel<<<1, 1, 0, st>>>(n, n_cand, k_max, sc + 0); count_launch();
     int rc = check_launch("select_keys");
     if (rc) return rc;
     Segs one;
@@ -508,18 +508,18 @@ int select_launch(long long n, const float* accum, const int* count, const uint8
     one.rank[0] = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
         select_hist_kernel<<<dim3(div_up(n, 256) < 256 ? div_up(n, 256) : 256, 1), 256, 0, st>>>(keys, one, prefix,
-                                                                                                 hist, shift);
-        select_decide_kernel<<<1, 256, 0, st>>>(hist, prefix, sc + 0, sc + 1, shift);
+                                                                                                 hist, shift); count_launch();
+        select_decide_kernel<<<1, 256, 0, st>>>(hist, prefix, sc + 0, sc + 1, shift); count_launch();
         rc = check_launch("select_radix");
         if (rc) return rc;
     }
-    select_eq_flags_kernel<<<nb, 256, 0, st>>>(n, keys, prefix, eq);
+    select_eq_flags_kernel<<<nb, 256, 0, st>>>(n, keys, prefix, eq); count_launch();
     rc = scan_u32_public(eq, eqr, sc + 2, n, part, sc + 3, st);
     if (rc) return rc;
-    select_flags_kernel<<<nb, 256, 0, st>>>(n, keys, prefix, eqr, sc + 0, sc + 1, n_cand, k_max, flag);
+    select_flags_kernel<<<nb, 256, 0, st>>>(n, keys, prefix, eqr, sc + 0, sc + 1, n_cand, k_max, flag); count_launch();
     rc = scan_u32_public(flag, eq, sc + 2, n, part, sc + 4, st);
     if (rc) return rc;
-    compact_kernel<<<nb, 256, 0, st>>>(n, flag, eq, sc + 4, k_max, selected, n_selected);
+    compact_kernel<<<nb, 256, 0, st>>>(n, flag, eq, sc + 4, k_max, selected, n_selected); count_launch();
     return check_launch("select_compact");
 }
 
@@ -529,7 +529,7 @@ int spawn_launch(long long n, int deg, float* means, float* ls, float* quats, fl
     int K3 = 3 * (deg + 1) * (deg + 1);
     float log_div = logf(1.6f);
     spawn_kernel<<<div_up(k_max > 0 ? k_max : 1, 256), 256, 0, st>>>(n, K3, means, ls, quats, logit, sh, is_var,
-                                                                     selected, n_sel, k_max, z, n_total, log_div);
+                                                                     selected, n_sel, k_max, z, n_total, log_div); count_launch();
     return check_launch("spawn_kernel");
 }
 

@@ -69,7 +69,9 @@ _SIGS = {
     "dass_version": (C.c_int, []),
     "dass_status_string": (C.c_char_p, [C.c_int]),
     "dass_last_error": (C.c_char_p, []),
+    "dass_kernel_launches": (C.c_int64, []),
     "dass_tile_layout": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
+    "dass_render_work": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
     "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
@@ -198,6 +200,17 @@ def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_f
     bgp = (C.c_float * 3)(*bg) if bg is not None else None
     _call("dass_render_fwd", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams), tile,
           batch, bgp, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _stream(stream))
+
+
+def dass_kernel_launches():
+    return int(load().dass_kernel_launches())
+
+
+def dass_render_work(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, work, stream=None):
+    """work: int64 CUDA tensor of 4 (counts, see include/dass.h)."""
+    arr = cameras(cams)
+    _call("dass_render_work", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams), tile,
+          batch, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _ptr(work, I64), _stream(stream))
 
 
 def dass_render_bwd(splats, pair_rec, tile_ranges, cams, tile, batch, T_final, n_last, dL_dimage, splat_grads,
