@@ -35,7 +35,7 @@ METRIC = "s/timestep fwd+bwd @300k Gaussians x20 views; render p50/p99 ms; batch
 UNIT = "s/timestep"
 WORKLOAD = "batched multi-view timestep: 300k Gaussians SH3 FP32, 20 cams 1352x1014 arc, 10% dynamic"
 # Algorithmic FP32 operations per (pixel, Gaussian) pair of the compositing kernels: evaluating
-# alpha costs 11 (2 sub, 4 mul, 2 fma, o*G, 1-alpha ... see the design doc); an added pair costs 20 in
+# alpha costs 11 (2 sub, 4 mul, 2 fma, o*G, 1-alpha, ...); an added pair costs 20 in
 # the forward (alpha, T update, weight, 3 colour FMAs) and 64 in the backward (alpha, T_j,
 # weight, colour and alpha gradients, behind-colour update, 5 geometry gradients, 9 reduction adds).
 FLOP_EVAL = 11
