@@ -138,6 +138,29 @@ int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camer
                   uint32_t* tile_ranges, int64_t* counters, void* workspace,
                   size_t workspace_bytes, void* stream);
 
+/* Size of the static device scratch array used by dass_bin_sort_static (64 MiB). */
+#define DASS_BIN_SORT_STATIC_BYTES (64ull << 20)
+
+/* Same result as dass_bin_sort, for callers that cannot allocate device memory: the paper has no
+ * counterpart to this entry point. Some hosts own every device allocation through their own
+ * pool and do not allow a library to call cudaMalloc (real-time render plugins, engines with a
+ * fixed memory budget), and for some callers an allocation would block or synchronise the
+ * device at a moment they cannot afford. This variant takes the same inputs and outputs as
+ * dass_bin_sort but no workspace: its scratch is a file-scope device array of
+ * DASS_BIN_SORT_STATIC_BYTES bytes that every GPU loading the library holds until the process
+ * exits. The call itself allocates nothing.
+ *  - Limit: dass_bin_sort_workspace(n_cams * rec_stride, pair_capacity, ...) must not exceed
+ *    DASS_BIN_SORT_STATIC_BYTES (e.g. 500k records with 4M pairs fit); larger requests return
+ *    DASS_ERR_OOM with an explanation in dass_last_error() and launch nothing.
+ *  - Set-up: the first call on a device looks up the device address of the array (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - Sharing: every call uses the same array, which keeps the previous call's contents; the
+ *    sort writes every scratch word before reading it, so nothing needs clearing. Calls whose
+ *    work overlaps on the GPU (other streams, other threads) race on the array: serialise them. */
+int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, const dass_camera* cams /* host */,
+                         int n_cams, int tile, uint32_t* pair_rec, int64_t pair_capacity,
+                         uint32_t* tile_ranges, int64_t* counters, void* stream);
+
 /* Forward compositing of every tile of every camera in one launch (App. A.1 blending):
  * per pixel, front to back over its tile's list, alpha = min(0.99, o exp(power)); alpha
  * < 1/255 is skipped; before adding a Gaussian, T (1 - alpha) < 1e-4 stops the pixel and

@@ -62,6 +62,8 @@ void count_launch(long long k) { g_launches += k; }
 long long launches_so_far() { return g_launches; }
 void set_launches(long long v) { g_launches = v; }
 
+void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 void set_last_error(const char* what, cudaError_t e) {
     snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
 }

@@ -75,6 +75,7 @@ _SIGS = {
     "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
     "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
+    "dass_bin_sort_static": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]),
     "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
     "dass_preprocess_bwd": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P,
@@ -193,6 +194,13 @@ def dass_bin_sort(splats, rec_stride, cams, tile, pair_rec, tile_ranges, counter
     _call("dass_bin_sort", _ptr(splats, F32), rec_stride, arr, len(cams), tile, _ptr(pair_rec, I32),
           pair_rec.numel(), _ptr(tile_ranges, I32), _ptr(counters, I64), _ptr(workspace, U8), workspace.numel(),
           _stream(stream))
+
+
+def dass_bin_sort_static(splats, rec_stride, cams, tile, pair_rec, tile_ranges, counters, stream=None):
+    """dass_bin_sort without a workspace (static device scratch; see include/dass.h)."""
+    arr = cameras(cams)
+    _call("dass_bin_sort_static", _ptr(splats, F32), rec_stride, arr, len(cams), tile, _ptr(pair_rec, I32),
+          pair_rec.numel(), _ptr(tile_ranges, I32), _ptr(counters, I64), _stream(stream))
 
 
 def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, bg=None, stream=None):
