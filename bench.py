@@ -34,11 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = "s/timestep fwd+bwd @300k Gaussians x20 views; render p50/p99 ms; batched vs plain"
 UNIT = "s/timestep"
 WORKLOAD = "batched multi-view timestep: 300k Gaussians SH3 FP32, 20 cams 1352x1014 arc, 10% dynamic"
-# Algorithmic FP32 operations per (pixel, Gaussian) pair of the compositing kernels: evaluating
-# alpha costs 11 (2 sub, 4 mul, 2 fma, o*G, 1-alpha, ...); an added pair costs 20 in
-# the forward (alpha, T update, weight, 3 colour FMAs) and 64 in the backward (alpha, T_j,
-# weight, colour and alpha gradients, behind-colour update, 5 geometry gradients, 9 reduction adds).
-FLOP_EVAL = 11
+# Algorithmic FP32 work of the compositing kernels: only (pixel, Gaussian) pairs that a pixel
+# actually adds are counted (evaluating alpha for any other pair is overhead of the tiling). An
+# added pair costs 20 flop in the forward (alpha: 2 sub, 4 mul, 2 fma, o*G; T(1-alpha), alpha*T,
+# 3 colour FMAs) and 64 flop in the backward (alpha again, T_j = T/(1-alpha), weight, 3 colour
+# gradients, dL/dalpha, behind-colour update, dL/do, dL/du, dL/dv, 3 conic gradients, 9 adds of
+# the per-Gaussian reduction).
 FLOP_FWD_ADD = 20
 FLOP_BWD_ADD = 64
 
@@ -302,8 +303,8 @@ def main():
     sms = props.multi_processor_count
     mhz = clk["sm_mhz"] or 2070.0
     fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12   # TFLOP/s
-    bwd_flop = FLOP_EVAL * n_bwd + (FLOP_BWD_ADD - FLOP_EVAL) * n_add
-    fwd_flop = FLOP_EVAL * n_eval + (FLOP_FWD_ADD - FLOP_EVAL) * n_add
+    bwd_flop = FLOP_BWD_ADD * n_add
+    fwd_flop = FLOP_FWD_ADD * n_add
     bwd_tf = bwd_flop / (bwd_ms * 1e-3) / 1e12
     fwd_tf = fwd_flop / (fwd_ms * 1e-3) / 1e12
     dom = "render_bwd" if bwd_ms >= fwd_ms else "render_fwd"
@@ -315,7 +316,7 @@ def main():
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
                "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
-               "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "pairs_evaluated_bwd": n_bwd,
+               "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "list_prefix_bwd": n_bwd,
                "bin_sort_bytes_per_pair": None}
 
     # ---------------- plain form (one launch per camera, no graph) vs batched, per iteration

@@ -125,7 +125,9 @@ int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t ti
                             size_t* bytes);
 
 /* Tile binning and device radix sort (tile-based rasterisation, Sec. 1 / Sec. 4.2).
- * Each visible record emits one (tile, record) pair per covered tile; pairs are ordered by
+ * Each visible record (radius > 0) emits one (tile, record) pair per tile that its footprint
+ * ellipse {d : d^T conic d <= 2 ln(255 o) + 0.01} reaches (at a pixel centre of the tile; every
+ * pixel with alpha >= 1/255 lies inside that ellipse, so no contribution is lost); pairs are ordered by
  * the 64-bit key (global tile id << 32 | depth bits), stable in record order: an LSD radix
  * sort whose 32 depth-bit passes run on the records before duplication and whose tile-bit
  * passes run on the pairs. Outputs: pair_rec[M] (record id per sorted pair),
@@ -173,10 +175,10 @@ int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const ui
                     void* stream);
 
 /* Measurement variant of dass_render_fwd (same outputs, black background) that also counts
- * the algorithmic work of the compositing: work[0] = (pixel, Gaussian) pairs evaluated by the
- * forward up to each pixel's own stop, work[1] = pairs added to a pixel, work[2] = pairs the
- * backward evaluates (each pixel's list prefix up to its last added Gaussian), work[3] =
- * pixels. work: device uint64[4], zeroed by the call. Not used on the timed path. */
+ * the work of the compositing: work[0] = (pixel, Gaussian) pairs whose alpha the forward
+ * evaluates (after the per-warp footprint culling, up to each pixel's own stop), work[1] = pairs
+ * added to a pixel (the algorithmic work), work[2] = sum over pixels of the length of the tile
+ * list prefix up to the pixel's last added Gaussian, work[3] = pixels. work: device uint64[4], zeroed by the call. Not used on the timed path. */
 int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                      const dass_camera* cams /* host */, int n_cams, int tile, int batch, float* image,
                      float* T_final, int32_t* n_last, uint64_t* work, void* stream);

@@ -202,7 +202,20 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
 
 // ----------------------------------------------------------------- binning kernels
 
-// Record -> (depth key, own index, tile count).
+// Record -> (depth key, own index, number of tiles whose pixel centres the footprint ellipse
+// reaches). A visible record has radius > 0; its candidate tiles come from the ellipse's
+// bounding box and each is kept only if the ellipse intersects it (exact, conservative).
+__device__ __forceinline__ bool record_footprint(const dass_splat* __restrict__ splats, long long rec, Footprint& f,
+                                                 float& depth) {
+    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
+    float4 s0 = __ldg(sp);
+    float4 s1 = __ldg(sp + 1);
+    float4 s2 = __ldg(sp + 2);
+    depth = s2.y;
+    if (__float_as_int(s2.z) <= 0) return false;
+    return footprint_of(s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, f);
+}
+
 __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                  uint32_t* __restrict__ counts) {
@@ -210,12 +223,16 @@ __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long lon
     if (rec >= n_rec) return;
     int ci = (int)(rec / ct.rec_stride);
     const CamInfo& cam = ct.c[ci];
-    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
-    float4 s0 = __ldg(sp);
-    float4 s2 = __ldg(sp + 2);
-    int r = __float_as_int(s2.z);
-    int cnt = tile_count(s0.x, s0.y, r, cam.tiles_x, cam.tiles_y, ct.tile);
-    keys[rec] = cnt > 0 ? __float_as_uint(s2.y) : 0xffffffffu;
+    Footprint f;
+    float depth;
+    int cnt = 0;
+    if (record_footprint(splats, rec, f, depth)) {
+        int x0, x1, y0, y1;
+        footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) cnt += footprint_hits_tile(f, x, y, ct.tile) ? 1 : 0;
+    }
+    keys[rec] = cnt > 0 ? __float_as_uint(depth) : 0xffffffffu;
     vals[rec] = (uint32_t)rec;
     counts[rec] = (uint32_t)cnt;
 }
@@ -242,17 +259,15 @@ __global__ void duplicate_kernel(const dass_splat* __restrict__ splats, long lon
     uint32_t rec = order[k];
     int ci = (int)(rec / ct.rec_stride);
     const CamInfo& cam = ct.c[ci];
-    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
-    float4 s0 = __ldg(sp);
-    float4 s2 = __ldg(sp + 2);
-    int r = __float_as_int(s2.z);
-    if (r <= 0) return;
+    Footprint f;
+    float depth;
+    if (!record_footprint(splats, rec, f, depth)) return;
     int x0, x1, y0, y1;
-    tile_rect(s0.x, s0.y, r, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
-    if (x0 > x1 || y0 > y1) return;
+    footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
     long long pos = offsets[k];
     for (int y = y0; y <= y1; ++y) {
         for (int x = x0; x <= x1; ++x) {
+            if (!footprint_hits_tile(f, x, y, ct.tile)) continue;
             if (pos < capacity) {
                 pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
                 pair_rec[pos] = rec;

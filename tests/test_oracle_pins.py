@@ -290,18 +290,22 @@ def test_footprint_radius_contains_alpha_footprint():
 
 
 def test_binning_hand_example_and_ties():
-    cams = [_cam(64, 32), _cam(64, 32)]
-    # record 0: u=20, r=4 -> x tiles [1,1], y tiles [0,0]; record 1 spans 2x2 tiles; records 2,3 tie in depth
-    u = np.array([20.0, 15.5, 40.0, 40.0], np.float32)
-    v = np.array([5.0, 15.5, 20.0, 20.0], np.float32)
-    r = np.array([4, 2, 3, 3])
-    d = np.array([3.0, 2.0, 1.5, 1.5], np.float32)
-    cam_of = np.array([0, 0, 1, 1])
-    recs, tiles, ranges = binning.bin_and_sort(u, v, r, d, cam_of, cams, 16)
-    # camera 0 has 4x2 tiles (ids 0..7), camera 1 starts at 8
-    assert tiles.tolist() == [0, 1, 1, 4, 5, 8 + 4 + 2, 8 + 4 + 2]
-    assert recs.tolist() == [1, 1, 0, 1, 1, 2, 3]            # tile 1: depth 2 before depth 3; tie by index
-    assert ranges[1].tolist() == [1, 3] and ranges[14].tolist() == [5, 7]
+    cams = [_cam(64, 64), _cam(64, 64)]          # 4 x 4 tiles of 16 px per camera
+    u = np.array([20.0, 28.0, 20.0, 40.0])
+    v = np.array([5.0, 28.0, 8.0, 40.0])
+    sig = np.array([2.0, 1.5, 1.0, 1.5])          # isotropic footprints: conic = I / sigma^2
+    conic = np.stack([1 / sig ** 2, np.zeros(4), 1 / sig ** 2], 1)
+    opac = np.ones(4)                             # k2 = 2 ln 255 + 0.01 = 11.102
+    rad = np.array([7, 5, 4, 0])                  # record 3 is invisible
+    cam_of = np.array([0, 0, 0, 1])
+    sure, maybe, total = binning.bin_records(u, v, conic, opac, rad, cam_of, cams, 16)
+    assert total == 32 and not maybe
+    # record 1 at (28, 28): the corner tile (2, 2) is out (nearest pixel centre (32, 32) has
+    # q = 32 / 2.25 = 14.2 > k2) although the square of radius 5 would overlap it
+    assert sure == {0: {0}, 1: {0, 2}, 5: {1}, 6: {1}, 9: {1}}
+    assert sorted(sure[1], key=lambda r: binning.order_key([3.0, 2.0, 3.0, 1.0][r], r)) == [0, 2]
+    assert binning.rect_min_quadratic(1.0, 0.0, 1.0, 3.0, 5.0, -1.0, 1.0) == 9.0
+    assert binning.rect_min_quadratic(2.0, 1.0, 1.0, 1.0, 2.0, -10.0, 10.0) == pytest.approx(1.0)  # y = -x
 
 
 # ------------------------------------------------------------- loss

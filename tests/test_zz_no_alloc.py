@@ -24,8 +24,16 @@ def _records(n_cams, n, seed, width, height):
     rec = np.zeros((R, 12), np.float32)
     rec[:, 0] = rng.uniform(-20, width + 20, R)
     rec[:, 1] = rng.uniform(-20, height + 20, R)
+    sx, sy = rng.uniform(0.5, 7.0, R), rng.uniform(0.5, 7.0, R)      # footprint axes in pixels
+    th = rng.uniform(0, np.pi, R)
+    c, s = np.cos(th), np.sin(th)
+    cxx, cyy = c * c * sx * sx + s * s * sy * sy, s * s * sx * sx + c * c * sy * sy
+    cxy = c * s * (sx * sx - sy * sy)
+    det = cxx * cyy - cxy * cxy
+    rec[:, 2], rec[:, 3], rec[:, 4] = cyy / det, -cxy / det, cxx / det   # conic = covariance^-1
+    rec[:, 5] = rng.uniform(0.05, 1.0, R)                              # opacity
     rec[:, 9] = rng.integers(1, 200, R).astype(np.float32) * 0.05        # depth ties included
-    rad = rng.integers(0, 24, R).astype(np.int32)
+    rad = np.full(R, 30, np.int32)
     rad[rng.uniform(size=R) < 0.1] = 0
     rec[:, 10] = rad.view(np.float32)
     return torch.from_numpy(rec).cuda()
