@@ -123,7 +123,6 @@ __global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, P
 
     for (int ci = 0; ci < ct.n; ++ci) {
         const CamInfo& cam = ct.c[ci];
-        dass_splat rec;
         Proj P;
         project_one(cam, p, Sig, P);
         int radius = 0;

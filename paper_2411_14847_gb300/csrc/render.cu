@@ -1,8 +1,8 @@
 // Forward and backward alpha compositing (App. A.1) over every tile of every camera in one
-// launch. One CTA per B x B tile; each warp owns an 8 x 4 block of pixels, one pixel per lane.
+// launch. One CTA per B x B tile; each warp owns an 8 x 8 block of pixels, two pixels per lane.
 // The tile's depth-sorted Gaussians are staged through shared memory in batches; after each
 // batch is staged, every warp compacts (ballot + prefix popcount, order preserved) the entries
-// whose alpha >= 1/255 footprint ellipse reaches its own 8 x 4 block, and composites only
+// whose alpha >= 1/255 footprint ellipse reaches its own block of pixels, and composites only
 // those. The backward walks the lists in reverse from the last contributor, recomputing alpha
 // and T_j = T_{j+1}/(1-alpha_j) from the saved T_final, and reduces per-Gaussian gradients
 // warp-wide (shuffles), then block-wide (shared-memory atomics), then into global memory
@@ -13,14 +13,9 @@ namespace dass {
 
 namespace {
 
-struct Staged {
-    float4 A;    // u, v, a * kNegHalfLog2e, c * kNegHalfLog2e
-    float4 B;    // 2 b * kNegHalfLog2e, o, r, g
-    float4 F;    // a, b, c, k2 (footprint ellipse d^T conic d <= k2)
-    float blue;
-};
-
-// Stage one splat into its shared-memory form (identical in forward and backward).
+// Stage one splat into its shared-memory form (identical in forward and backward):
+//   A = (u, v, a * kNegHalfLog2e, c * kNegHalfLog2e), B = (2 b * kNegHalfLog2e, o, r, g),
+//   F = (a, b, c, k2) with the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
 __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splats, uint32_t rec, float4& A, float4& Bv,
                                             float4& F, float& blue) {
     const float4* sp = reinterpret_cast<const float4*>(splats + rec);
@@ -46,9 +41,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // at a point of each edge facing the centre (the clamped 1-D minimiser, computed with a fast
 // division); any point of the rectangle gives an upper bound of its minimum, so a Gaussian is
 // culled only if every pixel of the block is outside its footprint (up to k2's slack).
+template <int BH>
 __device__ __forceinline__ bool reaches_block(const float4 A, const float4 F, float bx, float by) {
     if (F.w < 0.f) return false;
-    const float x0 = bx - A.x, x1 = bx + 7.f - A.x, y0 = by - A.y, y1 = by + 3.f - A.y;
+    const float x0 = bx - A.x, x1 = bx + 7.f - A.x, y0 = by - A.y, y1 = by + (float)(BH - 1) - A.y;
     const bool in_x = x0 <= 0.f && x1 >= 0.f, in_y = y0 <= 0.f && y1 >= 0.f;
     if (in_x && in_y) return true;
     float qmin = 3.4e38f;
@@ -65,15 +61,16 @@ __device__ __forceinline__ bool reaches_block(const float4 A, const float4 F, fl
     return qmin <= F.w;
 }
 
-// Compact the indices [0, cnt) of the staged batch whose footprint reaches this warp's block
-// into list[] (ascending), optionally only indices <= jmax. Returns the count (warp-uniform).
+// Compact the indices [0, cnt) of the staged batch whose footprint reaches this warp's 8 x BH
+// block into list[] (ascending), only indices <= jmax. Returns the count (warp-uniform).
+template <int BH>
 __device__ __forceinline__ int warp_compact(const float4* __restrict__ sA, const float4* __restrict__ sF, int cnt,
                                             int jmax, float bx, float by, unsigned short* list, int lane) {
     int n = 0;
     int lim = min(cnt, jmax + 1);
     for (int j0 = 0; j0 < lim; j0 += 32) {
         int j = j0 + lane;
-        bool hit = j < lim && reaches_block(sA[j], sF[j], bx, by);
+        bool hit = j < lim && reaches_block<BH>(sA[j], sF[j], bx, by);
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[n + __popc(m & lanemask_lt())] = (unsigned short)j;
         n += __popc(m);
@@ -82,38 +79,63 @@ __device__ __forceinline__ int warp_compact(const float4* __restrict__ sA, const
     return n;
 }
 
-template <int TILE>
-struct Layout {
-    static constexpr int NT = TILE * TILE;
-    static constexpr int NW = NT / 32;
-    static constexpr int WX = TILE / 8;   // warp blocks per tile row
+// Forward state of one pixel.
+struct PixFwd {
+    float fy, T, C0, C1, C2;
+    int last;
+    bool done;
+    unsigned long long n_eval, n_add;
 };
 
-// Pixel of (tile, thread): warp w covers the 8x4 block (w % WX, w / WX) of the tile.
-template <int TILE>
-__device__ __forceinline__ void pixel_of(const CamInfo& cam, int local, int tid, int& px, int& py, float& bx,
-                                         float& by) {
-    const int warp = tid >> 5, lane = tid & 31;
-    const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
-    const int wx = (warp % Layout<TILE>::WX) * 8, wy = (warp / Layout<TILE>::WX) * 4;
-    px = tx0 + wx + (lane & 7);
-    py = ty0 + wy + (lane >> 3);
-    bx = (float)(tx0 + wx);
-    by = (float)(ty0 + wy);
+template <bool COUNT>
+__device__ __forceinline__ void pix_fwd_step(PixFwd& p, int pos, float dx, const float4 A, const float4 Bv,
+                                             const float* __restrict__ sC, int j) {
+    if (p.done) return;
+    const float dy = __fsub_rn(p.fy, A.y);
+    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
+    const float alpha = splat_alpha(Bv.y, G);
+    if (COUNT) ++p.n_eval;
+    if (alpha < kAlphaMin) return;
+    const float test = __fmul_rn(p.T, __fsub_rn(1.f, alpha));
+    if (test < kTStop) { p.done = true; return; }
+    if (COUNT) ++p.n_add;
+    const float w = __fmul_rn(alpha, p.T);
+    p.C0 = __fmaf_rn(Bv.z, w, p.C0);
+    p.C1 = __fmaf_rn(Bv.w, w, p.C1);
+    p.C2 = __fmaf_rn(sC[j], w, p.C2);
+    p.T = test;
+    p.last = pos;
 }
 
-// COUNT = true is a separate instantiation used only to measure the algorithmic work of a
-// render (pairs each pixel evaluates before its own stop, pairs it adds, and pairs the
-// backward evaluates); the timed kernels are the COUNT = false instantiations.
+__device__ __forceinline__ void pix_fwd_store(const PixFwd& p, const CamInfo& cam, int px, int py, float3 bg,
+                                              float* __restrict__ image, float* __restrict__ T_final,
+                                              int* __restrict__ n_last) {
+    if (!(px < cam.W && py < cam.H)) return;
+    const long long plane = (long long)cam.W * cam.H;
+    const long long pix = (long long)py * cam.W + px;
+    float* img = image + 3 * cam.pix_base;
+    img[pix] = __fmaf_rn(p.T, bg.x, p.C0);
+    img[plane + pix] = __fmaf_rn(p.T, bg.y, p.C1);
+    img[2 * plane + pix] = __fmaf_rn(p.T, bg.z, p.C2);
+    T_final[cam.pix_base + pix] = p.T;
+    n_last[cam.pix_base + pix] = p.last;
+}
+
+// One CTA per tile with TILE*TILE/2 threads: warp w owns the 8 x 8 block (w % (TILE/8), w / (TILE/8))
+// and each lane the two pixels (x, y) and (x, y + 4) of it.
+// COUNT = true is a separate instantiation used only to measure the work of a render (pairs
+// evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false instantiations.
 template <int TILE, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat* __restrict__ splats,
-                                                               const uint32_t* __restrict__ pair_rec,
-                                                               const uint32_t* __restrict__ ranges, CamTable ct,
-                                                               float3 bg, float* __restrict__ image,
-                                                               float* __restrict__ T_final, int* __restrict__ n_last,
-                                                               unsigned long long* __restrict__ work) {
-    constexpr int NT = Layout<TILE>::NT;
-    constexpr int NW = Layout<TILE>::NW;
+__global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_splat* __restrict__ splats,
+                                                                   const uint32_t* __restrict__ pair_rec,
+                                                                   const uint32_t* __restrict__ ranges, CamTable ct,
+                                                                   float3 bg, float* __restrict__ image,
+                                                                   float* __restrict__ T_final,
+                                                                   int* __restrict__ n_last,
+                                                                   unsigned long long* __restrict__ work) {
+    constexpr int NT = TILE * TILE / 2;
+    constexpr int NW = NT / 32;
+    constexpr int WX = TILE / 8;
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
     __shared__ float4 sF[BATCH];
@@ -122,61 +144,42 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(const dass_splat
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile_id = blockIdx.x;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
-    int px, py;
-    float bx, by;
-    pixel_of<TILE>(cam, tile_id - cam.tile_base, tid, px, py, bx, by);
-    const bool inside = px < cam.W && py < cam.H;
+    const int local = tile_id - cam.tile_base;
+    const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
+    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * 8;
+    const int px = bxi + (lane & 7);
+    const int py = byi + (lane >> 3);
+    const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
-    const float fx = (float)px, fy = (float)py;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = -1;
-    bool done = !inside;
-    unsigned long long n_eval = 0, n_add = 0;
+    const float fx = (float)px;
+    PixFwd p0{(float)py, 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py < cam.H), 0ull, 0ull};
+    PixFwd p1{(float)(py + 4), 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py + 4 < cam.H), 0ull, 0ull};
     for (uint32_t base = start; base < end; base += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
+        if (__syncthreads_count(p0.done && p1.done) == NT) break;
         const int cnt = min((uint32_t)BATCH, end - base);
         for (int i = tid; i < cnt; i += NT) stage_splat(splats, pair_rec[base + i], sA[i], sB[i], sF[i], sC[i]);
         __syncthreads();
-        if (__all_sync(0xffffffffu, done)) continue;
-        const int nl = warp_compact(sA, sF, cnt, BATCH, bx, by, sList[warp], lane);
-        if (!done) {
-            for (int t = 0; t < nl; ++t) {
-                const int j = sList[warp][t];
-                const float4 A = sA[j];
-                const float4 Bv = sB[j];
-                const float dx = __fsub_rn(fx, A.x), dy = __fsub_rn(fy, A.y);
-                const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
-                const float alpha = splat_alpha(Bv.y, G);
-                if (COUNT) ++n_eval;
-                if (alpha < kAlphaMin) continue;
-                const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (test < kTStop) { done = true; break; }
-                if (COUNT) ++n_add;
-                const float w = __fmul_rn(alpha, T);
-                C0 = __fmaf_rn(Bv.z, w, C0);
-                C1 = __fmaf_rn(Bv.w, w, C1);
-                C2 = __fmaf_rn(sC[j], w, C2);
-                T = test;
-                last = (int)(base + j);
-            }
+        if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
+        const int nl = warp_compact<8>(sA, sF, cnt, BATCH, bx, by, sList[warp], lane);
+        for (int t = 0; t < nl; ++t) {
+            if (p0.done && p1.done) break;
+            const int j = sList[warp][t];
+            const float4 A = sA[j];
+            const float4 Bv = sB[j];
+            const float dx = __fsub_rn(fx, A.x);
+            pix_fwd_step<COUNT>(p0, (int)(base + j), dx, A, Bv, sC, j);
+            pix_fwd_step<COUNT>(p1, (int)(base + j), dx, A, Bv, sC, j);
         }
     }
-    if (inside) {
-        const long long plane = (long long)cam.W * cam.H;
-        const long long pix = (long long)py * cam.W + px;
-        float* img = image + 3 * cam.pix_base;
-        img[pix] = __fmaf_rn(T, bg.x, C0);
-        img[plane + pix] = __fmaf_rn(T, bg.y, C1);
-        img[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
-        T_final[cam.pix_base + pix] = T;
-        n_last[cam.pix_base + pix] = last;
-    }
+    pix_fwd_store(p0, cam, px, py, bg, image, T_final, n_last);
+    pix_fwd_store(p1, cam, px, py + 4, bg, image, T_final, n_last);
     if (COUNT) {
-        unsigned long long n_bwd = last >= 0 ? (unsigned long long)(last - (int)start + 1) : 0ull;
-        atomicAdd(work + 0, n_eval);
-        atomicAdd(work + 1, n_add);
+        unsigned long long n_bwd = (p0.last >= 0 ? (unsigned long long)(p0.last - (int)start + 1) : 0ull) +
+                                   (p1.last >= 0 ? (unsigned long long)(p1.last - (int)start + 1) : 0ull);
+        atomicAdd(work + 0, p0.n_eval + p1.n_eval);
+        atomicAdd(work + 1, p0.n_add + p1.n_add);
         atomicAdd(work + 2, n_bwd);
-        if (inside) atomicAdd(work + 3, 1ull);
+        atomicAdd(work + 3, (unsigned long long)((px < cam.W && py < cam.H) + (px < cam.W && py + 4 < cam.H)));
     }
 }
 
@@ -212,13 +215,73 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Backward state of one pixel: transmittance behind the current Gaussian, upstream gradient,
+// colour behind the current Gaussian (background included) and last added list position.
+struct PixBwd {
+    float fy, T, g0, g1, g2, R0, R1, R2;
+    int last;
+};
+
+__device__ __forceinline__ void pix_bwd_load(PixBwd& p, const CamInfo& cam, int px, int py, float3 bg,
+                                             const float* __restrict__ T_final, const int* __restrict__ n_last,
+                                             const float* __restrict__ dL_dimage) {
+    p.fy = (float)py;
+    p.T = 1.f; p.g0 = p.g1 = p.g2 = 0.f; p.last = -1;
+    p.R0 = bg.x; p.R1 = bg.y; p.R2 = bg.z;
+    if (px < cam.W && py < cam.H) {
+        const long long plane = (long long)cam.W * cam.H;
+        const long long pix = (long long)py * cam.W + px;
+        const float* gi = dL_dimage + 3 * cam.pix_base;
+        p.g0 = gi[pix];
+        p.g1 = gi[plane + pix];
+        p.g2 = gi[2 * plane + pix];
+        p.T = T_final[cam.pix_base + pix];
+        p.last = n_last[cam.pix_base + pix];
+    }
+}
+
+// Gradient contribution of staged Gaussian (A, Bv, F, blue) at one pixel, added into v[0..7], eb.
+__device__ __forceinline__ bool pix_bwd_step(PixBwd& p, long long pos, float dx, const float4 A, const float4 Bv,
+                                             const float4 F, float blue, float* v, float& eb) {
+    if (pos > (long long)p.last) return false;
+    const float dy = __fsub_rn(p.fy, A.y);
+    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
+    const float alpha = splat_alpha(Bv.y, G);
+    if (alpha < kAlphaMin) return false;
+    const float om = 1.f - alpha;
+    const float Tj = p.T / om;
+    const float w = alpha * Tj;
+    v[6] += w * p.g0;
+    v[7] += w * p.g1;
+    eb += w * p.g2;
+    const float dLda = Tj * ((Bv.z - p.R0) * p.g0 + (Bv.w - p.R1) * p.g1 + (blue - p.R2) * p.g2);
+    p.R0 = Bv.z * alpha + om * p.R0;
+    p.R1 = Bv.w * alpha + om * p.R1;
+    p.R2 = blue * alpha + om * p.R2;
+    p.T = Tj;
+    if (Bv.y * G < kAlphaMax) {
+        const float dpow = dLda * alpha;
+        v[5] += dLda * G;
+        v[0] += dpow * (F.x * dx + F.y * dy);
+        v[1] += dpow * (F.z * dy + F.y * dx);
+        v[2] += -0.5f * dx * dx * dpow;
+        v[3] += -dx * dy * dpow;
+        v[4] += -0.5f * dy * dy * dpow;
+    }
+    return true;
+}
+
+// One CTA per tile with TILE*TILE/2 threads: warp w owns the 8 x 8 block (w % (TILE/8), w / (TILE/8))
+// and each lane the two pixels (x, y) and (x, y + 4) of it, so the per-Gaussian warp reduction is
+// shared by 64 pixels.
 template <int TILE, int BATCH>
-__global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(
+__global__ void __launch_bounds__(TILE* TILE / 2) render_bwd_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, dass_splat_grad* __restrict__ gsplat) {
-    constexpr int NT = Layout<TILE>::NT;
-    constexpr int NW = Layout<TILE>::NW;
+    constexpr int NT = TILE * TILE / 2;
+    constexpr int NW = NT / 32;
+    constexpr int WX = TILE / 8;
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
     __shared__ float4 sF[BATCH];
@@ -230,31 +293,23 @@ __global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile_id = blockIdx.x;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
-    int px, py;
-    float bx, by;
-    pixel_of<TILE>(cam, tile_id - cam.tile_base, tid, px, py, bx, by);
-    const bool inside = px < cam.W && py < cam.H;
+    const int local = tile_id - cam.tile_base;
+    const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
+    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * 8;
+    const int px = bxi + (lane & 7);
+    const int py = byi + (lane >> 3);
+    const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id];
-    const float fx = (float)px, fy = (float)py;
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    int last = -1;
-    if (inside) {
-        const long long plane = (long long)cam.W * cam.H;
-        const long long pix = (long long)py * cam.W + px;
-        const float* gi = dL_dimage + 3 * cam.pix_base;
-        g0 = gi[pix];
-        g1 = gi[plane + pix];
-        g2 = gi[2 * plane + pix];
-        T = T_final[cam.pix_base + pix];
-        last = n_last[cam.pix_base + pix];
-    }
+    const float fx = (float)px;
+    PixBwd p0, p1;
+    pix_bwd_load(p0, cam, px, py, bg, T_final, n_last, dL_dimage);
+    pix_bwd_load(p1, cam, px, py + 4, bg, T_final, n_last, dL_dimage);
     if (tid == 0) s_maxlast = -1;
     __syncthreads();
-    const int wlast = __reduce_max_sync(0xffffffffu, last);
+    const int wlast = __reduce_max_sync(0xffffffffu, max(p0.last, p1.last));
     if (lane == 0 && wlast >= 0) atomicMax(&s_maxlast, wlast);
     __syncthreads();
     const long long endpos = (long long)s_maxlast + 1;
-    float R0 = bg.x, R1 = bg.y, R2 = bg.z;   // colour behind the current Gaussian (incl. background)
     for (long long hi = endpos; hi > (long long)start; hi -= BATCH) {
         const long long lo = hi - BATCH > (long long)start ? hi - BATCH : (long long)start;
         const int cnt = (int)(hi - lo);
@@ -268,46 +323,19 @@ __global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(
         }
         __syncthreads();
         const int jmax = (int)((long long)wlast - lo);   // entries beyond every lane's last are skipped
-        const int nl = jmax >= 0 ? warp_compact(sA, sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
+        const int nl = jmax >= 0 ? warp_compact<8>(sA, sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
         for (int t = nl - 1; t >= 0; --t) {
             const int j = sList[warp][t];
             const long long pos = lo + j;
+            const float4 A = sA[j];
+            const float4 Bv = sB[j];
+            const float4 F = sF[j];
+            const float blue = sC[j];
+            const float dx = __fsub_rn(fx, A.x);
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float eb = 0.f;
-            bool contrib = false;
-            if (pos <= (long long)last) {
-                const float4 A = sA[j];
-                const float4 Bv = sB[j];
-                const float dx = __fsub_rn(fx, A.x), dy = __fsub_rn(fy, A.y);
-                const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
-                const float alpha = splat_alpha(Bv.y, G);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float om = 1.f - alpha;
-                    const float Tj = T / om;
-                    const float w = alpha * Tj;
-                    const float c2 = sC[j];
-                    v[6] = w * g0;
-                    v[7] = w * g1;
-                    eb = w * g2;
-                    const float dLda = Tj * ((Bv.z - R0) * g0 + (Bv.w - R1) * g1 + (c2 - R2) * g2);
-                    R0 = Bv.z * alpha + om * R0;
-                    R1 = Bv.w * alpha + om * R1;
-                    R2 = c2 * alpha + om * R2;
-                    T = Tj;
-                    const float oG = Bv.y * G;
-                    if (oG < kAlphaMax) {
-                        const float4 F = sF[j];   // (a, b, c) of the conic
-                        const float dpow = dLda * alpha;
-                        v[5] = dLda * G;
-                        v[0] = dpow * (F.x * dx + F.y * dy);
-                        v[1] = dpow * (F.z * dy + F.y * dx);
-                        v[2] = -0.5f * dx * dx * dpow;
-                        v[3] = -dx * dy * dpow;
-                        v[4] = -0.5f * dy * dy * dpow;
-                    }
-                }
-            }
+            bool contrib = pix_bwd_step(p0, pos, dx, A, Bv, F, blue, v, eb);
+            contrib |= pix_bwd_step(p1, pos, dx, A, Bv, F, blue, v, eb);
             if (__ballot_sync(0xffffffffu, contrib)) {
                 float r = warp_reduce8(v, lane);
                 float e = warp_sum(eb);
@@ -340,11 +368,11 @@ int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
                float* img, float* tf, int* nl, unsigned long long* work, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     if (work)
-        render_fwd_kernel<TILE, BATCH, true><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
-                                                                                    work);
+        render_fwd_kernel<TILE, BATCH, true><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
+                                                                                        nl, work);
     else
-        render_fwd_kernel<TILE, BATCH, false><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
-                                                                                     nullptr);
+        render_fwd_kernel<TILE, BATCH, false><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
+                                                                                         nl, nullptr);
     count_launch();
     return check_launch("render_fwd_kernel");
 }
@@ -353,7 +381,7 @@ template <int TILE, int BATCH>
 int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                const float* tf, const int* nl, const float* dimg, dass_splat_grad* gs, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
-    render_bwd_kernel<TILE, BATCH><<<ct.tiles_total, TILE * TILE, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg, gs);
+    render_bwd_kernel<TILE, BATCH><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg, gs);
     count_launch();
     return check_launch("render_bwd_kernel");
 }

@@ -136,11 +136,18 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_
     unsigned mask = (unsigned)nd - 1u;
     long long base = (long long)blockIdx.x * kRadixTile;
     int lane = threadIdx.x & 31;
-#pragma unroll 4
+    // all loads of the block are issued before any is used (one memory latency per block)
+    uint32_t kr[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        kr[r] = idx < n ? keys[idx] : 0u;
+    }
+#pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         long long idx = base + r * kRadixThreads + threadIdx.x;
         bool valid = idx < n;
-        unsigned digit = valid ? ((keys[idx] >> shift) & mask) : (unsigned)kMaxDigits;
+        unsigned digit = valid ? ((kr[r] >> shift) & mask) : (unsigned)kMaxDigits;
         unsigned peers = __match_any_sync(0xffffffffu, digit);
         if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[digit], (uint32_t)__popc(peers));
     }
@@ -170,11 +177,20 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
     __syncthreads();
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long base = (long long)blockIdx.x * kRadixTile;
+    // all loads of the block are issued before any is used (one memory latency per block)
+    uint32_t kr[kRadixItems], vr[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        kr[r] = idx < n ? keys_in[idx] : 0u;
+        vr[r] = idx < n ? vals_in[idx] : 0u;
+    }
+#pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         long long idx = base + r * kRadixThreads + threadIdx.x;
         bool valid = idx < n;
-        uint32_t key = valid ? keys_in[idx] : 0u;
-        uint32_t val = valid ? vals_in[idx] : 0u;
+        uint32_t key = kr[r];
+        uint32_t val = vr[r];
         unsigned digit = valid ? ((key >> shift) & mask) : (unsigned)kMaxDigits;
         unsigned peers = __match_any_sync(0xffffffffu, digit);
         unsigned rank = __popc(peers & lanemask_lt());
