@@ -119,6 +119,27 @@ int dass_preprocess(int64_t n, int sh_degree, const float* means, const float* l
                     const uint8_t* keep, const dass_camera* cams /* host */, int n_cams,
                     int tile, dass_splat* splats, void* stream);
 
+/* Gaussian set of one scene (device pointers, layout as above). */
+typedef struct dass_scene {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t pad;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logit;
+    const float* sh;
+} dass_scene;
+
+/* Serving form of dass_preprocess (novel-view rendering of resident scenes, no paper section:
+ * the render of App. A.1 applied to requests of several scenes in one launch). Camera c shows
+ * scenes[c] (host array [n_cams]; all scenes of one call share sh_degree); its records are
+ * splats[c * rec_stride + g] for g < scenes[c].n, and the records g in [scenes[c].n, rec_stride)
+ * are written as culled (radius 0), so dass_bin_sort / dass_render_fwd with the same rec_stride
+ * render every request of the batch in one launch each. rec_stride >= max n. */
+int dass_preprocess_scenes(const dass_scene* scenes /* host */, const dass_camera* cams /* host */,
+                           int n_cams, int tile, int64_t rec_stride, dass_splat* splats, void* stream);
+
 /* Bytes of scratch that dass_bin_sort needs for n_records = n_cams * rec_stride records,
  * `pair_capacity` (tile, Gaussian) pairs and `tiles_total` tiles. */
 int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total,

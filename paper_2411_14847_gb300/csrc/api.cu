@@ -13,6 +13,8 @@ namespace dass {
 int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                       dass_splat* splats, cudaStream_t st);
+int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
+                             cudaStream_t st);
 int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                           const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                           const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
@@ -168,6 +170,24 @@ DASS_API int dass_preprocess(int64_t n, int sh_degree, const float* means, const
     if (n == 0) return DASS_OK;
     return preprocess_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, keep, ct, splats,
                              as_stream(stream));
+}
+
+DASS_API int dass_preprocess_scenes(const dass_scene* scenes, const dass_camera* cams, int n_cams, int tile,
+                                   int64_t rec_stride, dass_splat* splats, void* stream) {
+    if (!scenes || rec_stride < 0 || n_cams < 1 || n_cams > DASS_MAX_CAMERAS) return DASS_ERR_INVALID_ARG;
+    int deg = scenes[0].sh_degree;
+    if (deg < 0 || deg > 3) return DASS_ERR_INVALID_ARG;
+    for (int c = 0; c < n_cams; ++c) {
+        const dass_scene& sc = scenes[c];
+        if (sc.sh_degree != deg || sc.n < 0 || sc.n > rec_stride) return DASS_ERR_INVALID_ARG;
+        if (sc.n > 0 && (!sc.means || !sc.log_scales || !sc.quats || !sc.opacity_logit || !sc.sh))
+            return DASS_ERR_INVALID_ARG;
+    }
+    if ((long long)n_cams * rec_stride >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (rec_stride > 0 && !splats) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
+    return preprocess_scenes_launch(scenes, deg, ct, splats, as_stream(stream));
 }
 
 DASS_API int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total, size_t* bytes) {

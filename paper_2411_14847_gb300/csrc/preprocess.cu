@@ -87,82 +87,117 @@ __device__ __forceinline__ int footprint_radius(float a, float b, float c, float
     return (int)ceilf(sqrtf(lam) * sqrtf(k2));
 }
 
+// Activated attributes of Gaussian g: mean, opacity, 3D covariance (6 unique entries), SH.
 template <int K>
-__global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, Params prm, CamTable ct,
-                                                         dass_splat* __restrict__ out) {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    float p[3], ls[3], q[4];
+__device__ __forceinline__ void gaussian_setup(const Params& prm, long long g, float* p, float& o, float* Sig,
+                                               float* coef) {
+    float ls[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) { p[i] = __ldg(prm.means + 3 * g + i); ls[i] = __ldg(prm.log_scales + 3 * g + i); }
     float4 q4 = __ldg(reinterpret_cast<const float4*>(prm.quats) + g);
-    q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
     float kp = prm.keep ? (float)prm.keep[g] : 1.f;
-    float o = sigmoidf_(__ldg(prm.opacity_logit + g)) * kp;
+    o = sigmoidf_(__ldg(prm.opacity_logit + g)) * kp;
     float s[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) s[i] = __expf(ls[i]) * kp;
-    float qn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     float R[9];
-    quat_to_rot(q[0] * qn, q[1] * qn, q[2] * qn, q[3] * qn, R);
+    quat_to_rot(q4.x * qn, q4.y * qn, q4.z * qn, q4.w * qn, R);
     // M = R diag(s); Sigma = M M^T
     float M[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * s[c];
-    float Sig[6];
     Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
     Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
     Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
     Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
     Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-    float coef[3 * K];
     load_sh<K>(prm.sh, g, coef);
+}
 
-    for (int ci = 0; ci < ct.n; ++ci) {
-        const CamInfo& cam = ct.c[ci];
-        Proj P;
-        project_one(cam, p, Sig, P);
-        int radius = 0;
-        int tiles = 0;
-        float conic_a = 0.f, conic_b = 0.f, conic_c = 0.f;
-        float rgb[3] = {0.f, 0.f, 0.f};
-        if (P.Z > kNear && P.det > 0.f) {
-            float idet = 1.f / P.det;
-            conic_a = P.c * idet;
-            conic_b = -P.b * idet;
-            conic_c = P.a * idet;
-            radius = footprint_radius(P.a, P.b, P.c, o);
-            tiles = tile_count(P.u, P.v, radius, cam.tiles_x, cam.tiles_y, ct.tile);
-            if (tiles == 0) radius = 0;
-        }
-        if (radius > 0) {
-            float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
-            float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-            dx *= inv; dy *= inv; dz *= inv;
-            float Yb[16];
-            sh_eval_basis(deg, dx, dy, dz, Yb);
+// Project one Gaussian into one camera and write its record (culled records: radius 0).
+template <int K>
+__device__ __forceinline__ void write_record(const CamInfo& cam, int tile, int deg, const float* p, float o,
+                                             const float* Sig, const float* coef, dass_splat* __restrict__ rec) {
+    Proj P;
+    project_one(cam, p, Sig, P);
+    int radius = 0;
+    int tiles = 0;
+    float conic_a = 0.f, conic_b = 0.f, conic_c = 0.f;
+    float rgb[3] = {0.f, 0.f, 0.f};
+    if (P.Z > kNear && P.det > 0.f) {
+        float idet = 1.f / P.det;
+        conic_a = P.c * idet;
+        conic_b = -P.b * idet;
+        conic_c = P.a * idet;
+        radius = footprint_radius(P.a, P.b, P.c, o);
+        tiles = tile_count(P.u, P.v, radius, cam.tiles_x, cam.tiles_y, tile);
+        if (tiles == 0) radius = 0;
+    }
+    if (radius > 0) {
+        float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        float Yb[16];
+        sh_eval_basis(deg, dx, dy, dz, Yb);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.5f;
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc += coef[3 * k + ch] * Yb[k];
-                rgb[ch] = fmaxf(acc, 0.f);
-            }
-        }
-        float4* dst = reinterpret_cast<float4*>(out + cam.rec_base + g);
-        if (radius > 0) {
-            dst[0] = make_float4(P.u, P.v, conic_a, conic_b);
-            dst[1] = make_float4(conic_c, o, rgb[0], rgb[1]);
-            dst[2] = make_float4(rgb[2], P.Z, __int_as_float(radius), __int_as_float(tiles));
-        } else {
-            dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            dst[2] = make_float4(0.f, P.Z, __int_as_float(0), __int_as_float(0));
+            for (int k = 0; k < K; ++k) acc += coef[3 * k + ch] * Yb[k];
+            rgb[ch] = fmaxf(acc, 0.f);
         }
     }
+    float4* dst = reinterpret_cast<float4*>(rec);
+    if (radius > 0) {
+        dst[0] = make_float4(P.u, P.v, conic_a, conic_b);
+        dst[1] = make_float4(conic_c, o, rgb[0], rgb[1]);
+        dst[2] = make_float4(rgb[2], P.Z, __int_as_float(radius), __int_as_float(tiles));
+    } else {
+        dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[2] = make_float4(0.f, P.Z, __int_as_float(0), __int_as_float(0));
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, Params prm, CamTable ct,
+                                                         dass_splat* __restrict__ out) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    float p[3], o, Sig[6], coef[3 * K];
+    gaussian_setup<K>(prm, g, p, o, Sig, coef);
+    for (int ci = 0; ci < ct.n; ++ci) write_record<K>(ct.c[ci], ct.tile, deg, p, o, Sig, coef, out + ct.c[ci].rec_base + g);
+}
+
+// Serving form: camera c shows its own scene; thread (g, c) writes record c * rec_stride + g,
+// culled (radius 0) for g beyond that scene's Gaussian count.
+struct SceneTable {
+    Params prm[DASS_MAX_CAMERAS];
+    long long n[DASS_MAX_CAMERAS];
+};
+
+template <int K>
+__global__ void __launch_bounds__(128) preprocess_scenes_kernel(int deg, SceneTable st, CamTable ct,
+                                                                dass_splat* __restrict__ out) {
+    const int ci = blockIdx.y;
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ct.rec_stride) return;
+    const CamInfo& cam = ct.c[ci];
+    dass_splat* rec = out + cam.rec_base + g;
+    if (g >= st.n[ci]) {
+        float4* dst = reinterpret_cast<float4*>(rec);
+        dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[2] = make_float4(0.f, 0.f, __int_as_float(0), __int_as_float(0));
+        return;
+    }
+    float p[3], o, Sig[6], coef[3 * K];
+    gaussian_setup<K>(st.prm[ci], g, p, o, Sig, coef);
+    write_record<K>(cam, ct.tile, deg, p, o, Sig, coef, rec);
 }
 
 struct Grads {
@@ -422,6 +457,13 @@ int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass
 }
 
 template <int K>
+int launch_pre_scenes(int deg, const SceneTable& stb, const CamTable& ct, dass_splat* out, cudaStream_t st) {
+    dim3 grid(div_up(ct.rec_stride, 128), ct.n);
+    preprocess_scenes_kernel<K><<<grid, 128, 0, st>>>(deg, stb, ct, out); count_launch();
+    return check_launch("preprocess_scenes_kernel");
+}
+
+template <int K>
 int launch_pre_bwd(long long n, int deg, const Params& prm, const CamTable& ct, const dass_splat* sp,
                    const dass_splat_grad* gsp, const int* rows, long long n_rows, unsigned flags, int acc,
                    const Grads& gr, cudaStream_t st) {
@@ -442,6 +484,24 @@ int preprocess_launch(long long n, int deg, const float* means, const float* log
         case 1: return launch_pre<4>(n, deg, prm, ct, splats, st);
         case 2: return launch_pre<9>(n, deg, prm, ct, splats, st);
         case 3: return launch_pre<16>(n, deg, prm, ct, splats, st);
+    }
+    return DASS_ERR_INVALID_ARG;
+}
+
+int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
+                             cudaStream_t st) {
+    static thread_local SceneTable stb;
+    for (int c = 0; c < ct.n; ++c) {
+        stb.prm[c] = Params{scenes[c].means, scenes[c].log_scales, scenes[c].quats, scenes[c].opacity_logit,
+                            scenes[c].sh, nullptr};
+        stb.n[c] = scenes[c].n;
+    }
+    if (ct.rec_stride <= 0) return DASS_OK;
+    switch (deg) {
+        case 0: return launch_pre_scenes<1>(deg, stb, ct, splats, st);
+        case 1: return launch_pre_scenes<4>(deg, stb, ct, splats, st);
+        case 2: return launch_pre_scenes<9>(deg, stb, ct, splats, st);
+        case 3: return launch_pre_scenes<16>(deg, stb, ct, splats, st);
     }
     return DASS_ERR_INVALID_ARG;
 }

@@ -64,6 +64,12 @@ class dass_step_desc(C.Structure):
     ]
 
 
+class dass_scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad", C.c_int32), ("means", C.c_void_p),
+                ("log_scales", C.c_void_p), ("quats", C.c_void_p), ("opacity_logit", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "dass_version": (C.c_int, []),
@@ -73,6 +79,7 @@ _SIGS = {
     "dass_tile_layout": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "dass_render_work": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
+    "dass_preprocess_scenes": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _P, _P]),
     "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort_static": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]),
@@ -181,6 +188,19 @@ def dass_preprocess(g, cams, tile, splats, keep=None, stream=None):
     _call("dass_preprocess", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
           _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), tile,
           _ptr(splats, F32), _stream(stream))
+
+
+def dass_preprocess_scenes(scenes, cams, tile, rec_stride, splats, stream=None):
+    """scenes: one dict of Gaussian tensors per camera (same SH degree)."""
+    arr = (dass_scene * len(cams))()
+    for i, g in enumerate(scenes):
+        n = g["means"].shape[0]
+        arr[i].n = n
+        arr[i].sh_degree = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+        for name in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+            setattr(arr[i], name, _ptr(g[name], F32).value)
+    _call("dass_preprocess_scenes", arr, cameras(cams), len(cams), tile, rec_stride, _ptr(splats, F32),
+          _stream(stream))
 
 
 def dass_bin_sort_workspace(n_records, pair_capacity, tiles_total):
