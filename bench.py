@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--render-reps", type=int, default=50)
     ap.add_argument("--cpu-pixels", type=int, default=384)
+    ap.add_argument("--serve-rates", default="500,1000", help="Poisson request rates (req/s) of the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=2.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -183,6 +185,70 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- serving under load
+
+def serve_load(rates, seconds, seed=1005):
+    """Serving workload: 8 resident scenes of 50k-500k Gaussians (SH3, log-uniform sizes), each
+    receiving a new timestep every second (buffer swap between two versions); novel-view
+    requests arrive as a Poisson process at each rate, resolutions uniform over 640x360,
+    1280x720, 1352x1014 and 2704x2028, poses on spheres of radius 3-5 around the origin.
+    Returns per-rate p50/p99 latency (submit -> result ready), frames/s and mean batch size."""
+    import threading
+    import torch
+    from paper_2411_14847_gb300 import raster, synth
+    from paper_2411_14847_gb300.serve import RenderServer, percentile
+
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(50_000), math.log(500_000), 8)).astype(int)
+    versions = []
+    for i, n in enumerate(sizes):
+        sc = synth.random_scene(int(n), 3, seed + 10 + i, box=synth.ARC_BOX)
+        versions.append([raster.to_device(sc.arrays()),
+                         raster.to_device(synth.perturbed(sc, seed + 100 + i).arrays())])
+    res = [(640, 360), (1280, 720), (1352, 1014), (2704, 2028)]
+    out = {"scenes": [int(n) for n in sizes]}
+    for rate in rates:
+        srv = RenderServer(tile=16, batch=128, max_batch=16, n_streams=3)
+        for i in range(8):
+            srv.set_scene(i, versions[i][0])
+        warm = [srv.submit(i % 8, c) for i, c in enumerate(synth.sphere_cameras(16, seed, 3.0, 5.0, res))]
+        for f in warm:
+            f.result(timeout=120)
+        srv.stats.latencies_ms.clear()
+        srv.stats.batch_sizes.clear()
+        n_req = int(rate * seconds)
+        cams = synth.sphere_cameras(n_req, seed + int(rate), 3.0, 5.0, res)
+        scene_of = rng.integers(0, 8, n_req)
+        gaps = rng.exponential(1.0 / rate, n_req)
+        futs = []
+        t0 = time.perf_counter()
+        nxt = t0
+        swap_at = t0 + 1.0
+        ver = 0
+        for k in range(n_req):
+            nxt += gaps[k]
+            dt = nxt - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)                       # sleeping releases the interpreter to the scheduler thread
+            if time.perf_counter() >= swap_at:          # a new timestep for every scene
+                ver ^= 1
+                for i in range(8):
+                    srv.set_scene(i, versions[i][ver])
+                swap_at += 1.0
+            futs.append(srv.submit(int(scene_of[k]), cams[k]))
+        for f in futs:
+            f.result(timeout=300)
+        t1 = time.perf_counter()
+        lat = srv.stats.latencies_ms
+        out[str(rate)] = {"requests": n_req, "p50_ms": round(percentile(lat, 0.5), 3),
+                          "p99_ms": round(percentile(lat, 0.99), 3), "frames_per_s": round(n_req / (t1 - t0), 1),
+                          "mean_batch": round(float(np.mean(srv.stats.batch_sizes)), 2),
+                          "offered_req_per_s": rate}
+        srv.close()
+        torch.cuda.synchronize()
+    return out
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -356,6 +422,9 @@ def main():
               "view": f"{cams[0].width}x{cams[0].height}", "gaussians": ts.n}
     del rfr
 
+    # ---------------- serving under mixed load (continuous batching)
+    serve = serve_load([int(r) for r in args.serve_rates.split(",") if r], args.serve_seconds) if rank == 0 else None
+
     # ---------------- end to end through the public API with host buffers
     host_tgt = targets.cpu().pin_memory()
     dev_tgt = torch.empty_like(targets)
@@ -399,7 +468,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
-                "plain": plain, "render_latency": render,
+                "plain": plain, "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "cpu_baseline": cpu}
         print(json.dumps(line))
