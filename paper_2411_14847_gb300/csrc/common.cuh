@@ -277,6 +277,42 @@ __device__ __forceinline__ bool footprint_hits_tile(const Footprint& f, int tx, 
     return rect_qmin(f, __fsub_rn(px0, f.u), __fsub_rn(px1, f.u), __fsub_rn(py0, f.v), __fsub_rn(py1, f.v)) <= f.k2;
 }
 
+// Tiles of row ty that the footprint reaches. The slice of the ellipse over the band of pixel
+// rows dy in [ya, yb] (offsets from v) projects onto an x-interval [L, R]: its right end is the
+// ellipse's rightmost point (+ex, -b ex / c) when that lies in the band, otherwise the right end
+// of the ellipse's chord on the band edge nearest to it (the right boundary is concave in dy);
+// the left end likewise. A tile of the row is reached iff its pixel-centre columns meet [L, R].
+// Returns false if the band misses the ellipse.
+__device__ __forceinline__ bool footprint_row(const Footprint& f, int ty, int tile, int tiles_x, int& tx0, int& tx1) {
+    const float B = (float)tile;
+    const float ya = __fsub_rn((float)(ty * tile), f.v);
+    const float yb = __fsub_rn((float)(ty * tile + tile - 1), f.v);
+    const float det = __fsub_rn(__fmul_rn(f.a, f.c), __fmul_rn(f.b, f.b));
+    const float ak2 = __fmul_rn(f.a, f.k2);
+    const float dyr = __fdiv_rn(-__fmul_rn(f.b, f.ex), f.c);   // dy of the rightmost point
+    float R, L;
+    if (dyr >= ya && dyr <= yb) {
+        R = f.ex;
+    } else {
+        const float yy = dyr < ya ? ya : yb;
+        const float disc = __fsub_rn(ak2, __fmul_rn(det, __fmul_rn(yy, yy)));
+        if (disc < 0.f) return false;
+        R = __fdiv_rn(__fadd_rn(-__fmul_rn(f.b, yy), __fsqrt_rn(disc)), f.a);
+    }
+    const float dyl = -dyr;                                     // dy of the leftmost point
+    if (dyl >= ya && dyl <= yb) {
+        L = -f.ex;
+    } else {
+        const float yy = dyl < ya ? ya : yb;
+        const float disc = __fsub_rn(ak2, __fmul_rn(det, __fmul_rn(yy, yy)));
+        if (disc < 0.f) return false;
+        L = __fdiv_rn(__fsub_rn(-__fmul_rn(f.b, yy), __fsqrt_rn(disc)), f.a);
+    }
+    tx0 = max(0, (int)ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(f.u, L), B - 1.f), B)));
+    tx1 = min(tiles_x - 1, (int)floorf(__fdiv_rn(__fadd_rn(f.u, R), B)));
+    return tx0 <= tx1;
+}
+
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace dass

@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
 // ----------------------------------------------------------------- binning kernels
 
 // Record -> (depth key, own index, number of tiles whose pixel centres the footprint ellipse
-// reaches). A visible record has radius > 0; its candidate tiles come from the ellipse's
-// bounding box and each is kept only if the ellipse intersects it (exact, conservative).
+// reaches). A visible record has radius > 0; its candidate tile rows come from the ellipse's
+// bounding box and each row contributes the contiguous run of tiles its band of the ellipse
+// reaches (exact, conservative).
 __device__ __forceinline__ bool record_footprint(const dass_splat* __restrict__ splats, long long rec, Footprint& f,
                                                  float& depth) {
     const float4* sp = reinterpret_cast<const float4*>(splats + rec);
@@ -245,8 +246,10 @@ __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long lon
     if (record_footprint(splats, rec, f, depth)) {
         int x0, x1, y0, y1;
         footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
-        for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x) cnt += footprint_hits_tile(f, x, y, ct.tile) ? 1 : 0;
+        for (int y = y0; y <= y1; ++y) {
+            int r0, r1;
+            if (footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) cnt += r1 - r0 + 1;
+        }
     }
     keys[rec] = cnt > 0 ? __float_as_uint(depth) : 0xffffffffu;
     vals[rec] = (uint32_t)rec;
@@ -282,8 +285,9 @@ __global__ void duplicate_kernel(const dass_splat* __restrict__ splats, long lon
     footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
     long long pos = offsets[k];
     for (int y = y0; y <= y1; ++y) {
-        for (int x = x0; x <= x1; ++x) {
-            if (!footprint_hits_tile(f, x, y, ct.tile)) continue;
+        int r0, r1;
+        if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
+        for (int x = r0; x <= r1; ++x) {
             if (pos < capacity) {
                 pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
                 pair_rec[pos] = rec;
