@@ -42,6 +42,9 @@ WORKLOAD = "batched multi-view timestep: 300k Gaussians SH3 FP32, 20 cams 1352x1
 # the per-Gaussian reduction).
 FLOP_FWD_ADD = 20
 FLOP_BWD_ADD = 64
+# Backward of a pair whose Gaussian only needs dL/dmean2D (static in the shift stage): alpha again,
+# T_j, dL/dalpha, behind-colour update, dpow, dL/du, dL/dv and 2 reduction adds = 43 flop.
+FLOP_BWD_MEAN_ADD = 43
 
 
 def parse():
@@ -338,11 +341,11 @@ def main():
     # ---------------- dominant kernels, timed standalone on the last iteration's buffers
     stage = results[-1]["stage"]
     sfr = stage.frame
-    work = torch.zeros(4, dtype=torch.int64, device=dev)
+    work = torch.zeros(5, dtype=torch.int64, device=dev)
     D.dass_render_work(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch, sfr.image, sfr.T_final,
-                       sfr.n_last, work)
+                       sfr.n_last, work, full_grad=stage.dyn_mask, rec_stride=sfr.n)
     torch.cuda.synchronize()
-    n_eval, n_add, n_bwd, n_pix = (int(v) for v in work.tolist())
+    n_eval, n_add, n_bwd, n_pix, n_add_dyn = (int(v) for v in work.tolist())
     s_ = torch.cuda.current_stream()
 
     def timed(fn, reps=10):
@@ -359,7 +362,8 @@ def main():
 
     # backward first (render_fwd recomputes the same T_final/n_last, so inputs stay consistent)
     bwd_ms = timed(lambda: D.dass_render_bwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
-                                             sfr.T_final, sfr.n_last, stage.dL_dimage, sfr.splat_grads))
+                                             sfr.T_final, sfr.n_last, stage.dL_dimage, sfr.splat_grads,
+                                             full_grad=stage.dyn_mask, rec_stride=sfr.n))
     fwd_ms = timed(lambda: D.dass_render_fwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
                                              sfr.image, sfr.T_final, sfr.n_last))
     n_pairs = int(sfr.counters[0].item())
@@ -369,7 +373,7 @@ def main():
     sms = props.multi_processor_count
     mhz = clk["sm_mhz"] or 2070.0
     fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12   # TFLOP/s
-    bwd_flop = FLOP_BWD_ADD * n_add
+    bwd_flop = FLOP_BWD_ADD * n_add_dyn + FLOP_BWD_MEAN_ADD * (n_add - n_add_dyn)
     fwd_flop = FLOP_FWD_ADD * n_add
     bwd_tf = bwd_flop / (bwd_ms * 1e-3) / 1e12
     fwd_tf = fwd_flop / (fwd_ms * 1e-3) / 1e12
@@ -382,7 +386,8 @@ def main():
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
                "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
-               "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "list_prefix_bwd": n_bwd,
+               "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "pairs_added_dynamic": n_add_dyn,
+               "list_prefix_bwd": n_bwd,
                "bin_sort_bytes_per_pair": None}
 
     # ---------------- plain form (one launch per camera, no graph) vs batched, per iteration

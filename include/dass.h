@@ -199,20 +199,27 @@ int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const ui
  * the work of the compositing: work[0] = (pixel, Gaussian) pairs whose alpha the forward
  * evaluates (after the per-warp footprint culling, up to each pixel's own stop), work[1] = pairs
  * added to a pixel (the algorithmic work), work[2] = sum over pixels of the length of the tile
- * list prefix up to the pixel's last added Gaussian, work[3] = pixels. work: device uint64[4], zeroed by the call. Not used on the timed path. */
+ * list prefix up to the pixel's last added Gaussian, work[3] = pixels, work[4] = added pairs whose
+ * Gaussian g = record % rec_stride has full_grad[g] != 0 (all of them if full_grad is NULL).
+ * work: device uint64[5], zeroed by the call. Not used on the timed path. */
 int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
-                     const dass_camera* cams /* host */, int n_cams, int tile, int batch, float* image,
-                     float* T_final, int32_t* n_last, uint64_t* work, void* stream);
+                     const dass_camera* cams /* host */, int n_cams, int tile, int batch,
+                     const uint8_t* full_grad, int64_t rec_stride, float* image, float* T_final,
+                     int32_t* n_last, uint64_t* work, void* stream);
 
 /* Reverse-order backward of dass_render_fwd. Recomputes alpha from the saved T_final and
  * n_last (T_j = T_{j+1} / (1 - alpha_j)); per Gaussian the 9 gradients are reduced across the
  * warp with shuffles, then per block in shared memory, then added to splat_grads[record]
- * with global atomics. splat_grads (n_records entries) is zeroed by this call first. */
+ * with global atomics. splat_grads (n_records entries) is zeroed by this call first.
+ * full_grad (optional, device uint8 per Gaussian g = record % rec_stride; NULL = all): Gaussians
+ * with full_grad[g] == 0 only receive splat_grads.mean2d (what the densification statistics
+ * read), their other fields stay 0 -- e.g. the static Gaussians of the shift stage (Sec. 3.3),
+ * whose parameters are not optimised; transmittance and colours are propagated identically. */
 int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
                     const uint32_t* tile_ranges, const dass_camera* cams /* host */, int n_cams,
                     int tile, int batch, const float* bg /* host, 3 */, const float* T_final,
-                    const int32_t* n_last, const float* dL_dimage, dass_splat_grad* splat_grads,
-                    void* stream);
+                    const int32_t* n_last, const float* dL_dimage, const uint8_t* full_grad,
+                    int64_t rec_stride, dass_splat_grad* splat_grads, void* stream);
 
 /* Chain rule from splat gradients to parameter gradients (App. A.1 projection, SH colour,
  * sigmoid/exp activations, Eq. 1 mask), summed over cameras. rows (optional, n_rows
@@ -337,6 +344,8 @@ typedef struct dass_step_desc {
     /* dynamic group and its learned offsets */
     int64_t n_dyn;
     const int32_t* dyn_idx;           /* [n_dyn] */
+    const uint8_t* dyn_mask;          /* [n] 1 for dynamic Gaussians (optional: NULL = full splat
+                                         gradients for every Gaussian in the backward) */
     float* offsets;                   /* [n_dyn][7] (dmu, sigma), updated in place */
     float* offset_grad;               /* [n_dyn][7] */
     float* adam_m;                    /* [n_dyn][7] */

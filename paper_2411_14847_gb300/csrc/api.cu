@@ -27,10 +27,11 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
-                      unsigned long long* work = nullptr);
+                      unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,
+                      long long rec_stride = 1);
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
-                      dass_splat_grad* gsplat, cudaStream_t st);
+                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
 size_t loss_workspace_bytes(const CamTable& ct);
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
                 double* loss, void* ws, size_t ws_bytes, cudaStream_t st);
@@ -224,30 +225,35 @@ DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec,
 }
 
 DASS_API int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
-                              const dass_camera* cams, int n_cams, int tile, int batch, float* image, float* T_final,
-                              int32_t* n_last, uint64_t* work, void* stream) {
+                              const dass_camera* cams, int n_cams, int tile, int batch, const uint8_t* full_grad,
+                              int64_t rec_stride, float* image, float* T_final, int32_t* n_last, uint64_t* work,
+                              void* stream) {
     if (!batch_ok(batch) || !tile_ranges || !image || !T_final || !n_last || !work) return DASS_ERR_INVALID_ARG;
+    if (full_grad && rec_stride <= 0) return DASS_ERR_INVALID_ARG;
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
-    DASS_CHECK_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t) * 4, st));
+    DASS_CHECK_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t) * 5, st));
     return render_fwd_launch(splats, pair_rec, tile_ranges, ct, batch, make_float3(0.f, 0.f, 0.f), image, T_final,
-                             n_last, st, reinterpret_cast<unsigned long long*>(work));
+                             n_last, st, reinterpret_cast<unsigned long long*>(work), full_grad,
+                             rec_stride > 0 ? rec_stride : 1);
 }
 
 DASS_API int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
                              const uint32_t* tile_ranges, const dass_camera* cams, int n_cams, int tile, int batch,
                              const float* bg, const float* T_final, const int32_t* n_last, const float* dL_dimage,
-                             dass_splat_grad* splat_grads, void* stream) {
+                             const uint8_t* full_grad, int64_t rec_stride, dass_splat_grad* splat_grads,
+                             void* stream) {
     if (!batch_ok(batch) || n_records < 0 || !tile_ranges || !T_final || !n_last || !dL_dimage)
         return DASS_ERR_INVALID_ARG;
+    if (full_grad && rec_stride <= 0) return DASS_ERR_INVALID_ARG;
     if (n_records > 0 && !splat_grads) return DASS_ERR_INVALID_ARG;
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     if (n_records > 0) DASS_CHECK_CUDA(cudaMemsetAsync(splat_grads, 0, sizeof(dass_splat_grad) * n_records, st));
     return render_bwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), T_final, n_last, dL_dimage,
-                             splat_grads, st);
+                             full_grad, rec_stride > 0 ? rec_stride : 1, splat_grads, st);
 }
 
 DASS_API int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, const float* log_scales,
@@ -443,7 +449,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemsetAsync(d->splat_grads, 0, sizeof(dass_splat_grad) * n_rec, st));
         rc = render_bwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final, d->n_last,
-                               d->dL_dimage, d->splat_grads, st);
+                               d->dL_dimage, d->dyn_mask, d->n, d->splat_grads, st);
         if (rc) return rc;
         rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
                                    d->opacity_logit, d->sh, nullptr, ct, d->splats, d->splat_grads, d->dyn_idx,
@@ -476,7 +482,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
             if (rc) return rc;
             DASS_CHECK_CUDA(cudaMemsetAsync(gs, 0, sizeof(dass_splat_grad) * d->n, st));
             rc = render_bwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final + pb, d->n_last + pb,
-                                   d->dL_dimage + 3 * pb, gs, st);
+                                   d->dL_dimage + 3 * pb, d->dyn_mask, d->n, gs, st);
             if (rc) return rc;
             rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
                                        d->opacity_logit, d->sh, nullptr, ct, sp, gs, d->dyn_idx, d->n_dyn,

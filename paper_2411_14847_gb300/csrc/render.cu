@@ -84,12 +84,12 @@ struct PixFwd {
     float fy, T, C0, C1, C2;
     int last;
     bool done;
-    unsigned long long n_eval, n_add;
+    unsigned long long n_eval, n_add, n_full;
 };
 
 template <bool COUNT>
 __device__ __forceinline__ void pix_fwd_step(PixFwd& p, int pos, float dx, const float4 A, const float4 Bv,
-                                             const float* __restrict__ sC, int j) {
+                                             const float* __restrict__ sC, int j, bool full = false) {
     if (p.done) return;
     const float dy = __fsub_rn(p.fy, A.y);
     const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
@@ -98,7 +98,7 @@ __device__ __forceinline__ void pix_fwd_step(PixFwd& p, int pos, float dx, const
     if (alpha < kAlphaMin) return;
     const float test = __fmul_rn(p.T, __fsub_rn(1.f, alpha));
     if (test < kTStop) { p.done = true; return; }
-    if (COUNT) ++p.n_add;
+    if (COUNT) { ++p.n_add; p.n_full += full ? 1ull : 0ull; }
     const float w = __fmul_rn(alpha, p.T);
     p.C0 = __fmaf_rn(Bv.z, w, p.C0);
     p.C1 = __fmaf_rn(Bv.w, w, p.C1);
@@ -132,7 +132,9 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
                                                                    float3 bg, float* __restrict__ image,
                                                                    float* __restrict__ T_final,
                                                                    int* __restrict__ n_last,
-                                                                   unsigned long long* __restrict__ work) {
+                                                                   unsigned long long* __restrict__ work,
+                                                                   const uint8_t* __restrict__ full_grad,
+                                                                   long long rec_stride) {
     constexpr int NT = TILE * TILE / 2;
     constexpr int NW = NT / 32;
     constexpr int WX = TILE / 8;
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
     __shared__ float4 sF[BATCH];
     __shared__ float sC[BATCH];
     __shared__ unsigned short sList[NW][BATCH];
+    __shared__ uint8_t sFullC[COUNT ? BATCH : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile_id = blockIdx.x;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
@@ -152,12 +155,16 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
     const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const float fx = (float)px;
-    PixFwd p0{(float)py, 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py < cam.H), 0ull, 0ull};
-    PixFwd p1{(float)(py + 4), 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py + 4 < cam.H), 0ull, 0ull};
+    PixFwd p0{(float)py, 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py < cam.H), 0ull, 0ull, 0ull};
+    PixFwd p1{(float)(py + 4), 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py + 4 < cam.H), 0ull, 0ull, 0ull};
     for (uint32_t base = start; base < end; base += BATCH) {
         if (__syncthreads_count(p0.done && p1.done) == NT) break;
         const int cnt = min((uint32_t)BATCH, end - base);
-        for (int i = tid; i < cnt; i += NT) stage_splat(splats, pair_rec[base + i], sA[i], sB[i], sF[i], sC[i]);
+        for (int i = tid; i < cnt; i += NT) {
+            const uint32_t rec = pair_rec[base + i];
+            stage_splat(splats, rec, sA[i], sB[i], sF[i], sC[i]);
+            if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
+        }
         __syncthreads();
         if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
         const int nl = warp_compact<8>(sA, sF, cnt, BATCH, bx, by, sList[warp], lane);
@@ -167,8 +174,9 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
             const float4 A = sA[j];
             const float4 Bv = sB[j];
             const float dx = __fsub_rn(fx, A.x);
-            pix_fwd_step<COUNT>(p0, (int)(base + j), dx, A, Bv, sC, j);
-            pix_fwd_step<COUNT>(p1, (int)(base + j), dx, A, Bv, sC, j);
+            const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
+            pix_fwd_step<COUNT>(p0, (int)(base + j), dx, A, Bv, sC, j, full);
+            pix_fwd_step<COUNT>(p1, (int)(base + j), dx, A, Bv, sC, j, full);
         }
     }
     pix_fwd_store(p0, cam, px, py, bg, image, T_final, n_last);
@@ -180,6 +188,7 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
         atomicAdd(work + 1, p0.n_add + p1.n_add);
         atomicAdd(work + 2, n_bwd);
         atomicAdd(work + 3, (unsigned long long)((px < cam.W && py < cam.H) + (px < cam.W && py + 4 < cam.H)));
+        atomicAdd(work + 4, p0.n_full + p1.n_full);
     }
 }
 
@@ -249,7 +258,7 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& p, long long pos, float dx,
     const float alpha = splat_alpha(Bv.y, G);
     if (alpha < kAlphaMin) return false;
     const float om = 1.f - alpha;
-    const float Tj = p.T / om;
+    const float Tj = __fdividef(p.T, om);
     const float w = alpha * Tj;
     v[6] += w * p.g0;
     v[7] += w * p.g1;
@@ -271,14 +280,53 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& p, long long pos, float dx,
     return true;
 }
 
+// The same pixel step when only dL/d(mean2D) of the Gaussian is wanted (its other splat gradients
+// are not needed by the caller): transmittance and behind-colour are updated exactly as above,
+// and only the two mean2D components are accumulated (su, sv).
+__device__ __forceinline__ bool pix_bwd_step_mean(PixBwd& p, long long pos, float dx, const float4 A,
+                                                  const float4 Bv, const float4 F, float blue, float& su, float& sv) {
+    if (pos > (long long)p.last) return false;
+    const float dy = __fsub_rn(p.fy, A.y);
+    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
+    const float alpha = splat_alpha(Bv.y, G);
+    if (alpha < kAlphaMin) return false;
+    const float om = 1.f - alpha;
+    const float Tj = __fdividef(p.T, om);
+    const float dLda = Tj * ((Bv.z - p.R0) * p.g0 + (Bv.w - p.R1) * p.g1 + (blue - p.R2) * p.g2);
+    p.R0 = Bv.z * alpha + om * p.R0;
+    p.R1 = Bv.w * alpha + om * p.R1;
+    p.R2 = blue * alpha + om * p.R2;
+    p.T = Tj;
+    if (Bv.y * G < kAlphaMax) {
+        const float dpow = dLda * alpha;
+        su += dpow * (F.x * dx + F.y * dy);
+        sv += dpow * (F.z * dy + F.y * dx);
+    }
+    return true;
+}
+
+// Sum two values across the warp: lane 0 ends with the sum of a, lane 16 with the sum of b.
+__device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
+    const bool h = lane & 16;
+    float r = (h ? b : a) + __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
+    r += __shfl_xor_sync(0xffffffffu, r, 8);
+    r += __shfl_xor_sync(0xffffffffu, r, 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
 // One CTA per tile with TILE*TILE/PPL threads: warp w owns the 8 x 4*PPL block
 // (w % (TILE/8), w / (TILE/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, so the
-// per-Gaussian warp reduction is shared by 32*PPL pixels.
+// per-Gaussian warp reduction is shared by 32*PPL pixels. full_grad (optional, per Gaussian of
+// the record stride) selects Gaussians whose complete splat gradient is wanted; the others only
+// receive dL/d(mean2D).
 template <int TILE, int BATCH, int PPL>
 __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
-    const float* __restrict__ dL_dimage, dass_splat_grad* __restrict__ gsplat) {
+    const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
+    dass_splat_grad* __restrict__ gsplat) {
     constexpr int NT = TILE * TILE / PPL;
     constexpr int NW = NT / 32;
     constexpr int WX = TILE / 8;
@@ -291,6 +339,7 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
     __shared__ uint32_t sRec[BATCH];
     __shared__ float sG[BATCH][12];
     __shared__ unsigned short sList[NW][BATCH];
+    __shared__ uint8_t sFull[BATCH];
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile_id = blockIdx.x;
@@ -323,6 +372,7 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
         for (int i = tid; i < cnt; i += NT) {
             uint32_t rec = pair_rec[lo + i];
             sRec[i] = rec;
+            sFull[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
             stage_splat(splats, rec, sA[i], sB[i], sF[i], sC[i]);
 #pragma unroll
             for (int k = 0; k < 12; ++k) sG[i][k] = 0.f;
@@ -338,19 +388,29 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
             const float4 F = sF[j];
             const float blue = sC[j];
             const float dx = __fsub_rn(fx, A.x);
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float eb = 0.f;
             bool contrib = false;
+            if (sFull[j]) {          // warp-uniform: the same Gaussian for every lane
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float eb = 0.f;
 #pragma unroll
-            for (int k = 0; k < PPL; ++k) contrib |= pix_bwd_step(pp[k], pos, dx, A, Bv, F, blue, v, eb);
-            if (__ballot_sync(0xffffffffu, contrib)) {
-                float r = warp_reduce8(v, lane);
-                float e = warp_sum(eb);
-                if ((lane & 3) == 0) {
-                    int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                    atomicAdd(&sG[j][idx], r);
+                for (int k = 0; k < PPL; ++k) contrib |= pix_bwd_step(pp[k], pos, dx, A, Bv, F, blue, v, eb);
+                if (__ballot_sync(0xffffffffu, contrib)) {
+                    float r = warp_reduce8(v, lane);
+                    float e = warp_sum(eb);
+                    if ((lane & 3) == 0) {
+                        int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        atomicAdd(&sG[j][idx], r);
+                    }
+                    if (lane == 1) atomicAdd(&sG[j][8], e);
                 }
-                if (lane == 1) atomicAdd(&sG[j][8], e);
+            } else {
+                float su = 0.f, sv = 0.f;
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) contrib |= pix_bwd_step_mean(pp[k], pos, dx, A, Bv, F, blue, su, sv);
+                if (__ballot_sync(0xffffffffu, contrib)) {
+                    float r = warp_reduce2(su, sv, lane);
+                    if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
+                }
             }
         }
         __syncthreads();
@@ -358,28 +418,25 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
             float4 a = make_float4(sG[i][0], sG[i][1], sG[i][2], sG[i][3]);
             float4 b = make_float4(sG[i][4], sG[i][5], sG[i][6], sG[i][7]);
             float c = sG[i][8];
-            bool nz = (a.x != 0.f) | (a.y != 0.f) | (a.z != 0.f) | (a.w != 0.f) | (b.x != 0.f) | (b.y != 0.f) |
-                      (b.z != 0.f) | (b.w != 0.f) | (c != 0.f);
-            if (nz) {
-                float4* dst = reinterpret_cast<float4*>(gsplat + sRec[i]);
-                atomicAdd(dst, a);
-                atomicAdd(dst + 1, b);
-                atomicAdd(reinterpret_cast<float*>(dst + 2), c);
-            }
+            float4* dst = reinterpret_cast<float4*>(gsplat + sRec[i]);
+            if ((a.x != 0.f) | (a.y != 0.f) | (a.z != 0.f) | (a.w != 0.f)) atomicAdd(dst, a);
+            if ((b.x != 0.f) | (b.y != 0.f) | (b.z != 0.f) | (b.w != 0.f)) atomicAdd(dst + 1, b);
+            if (c != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 2), c);
         }
     }
 }
 
 template <int TILE, int BATCH>
 int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
-               float* img, float* tf, int* nl, unsigned long long* work, cudaStream_t st) {
+               float* img, float* tf, int* nl, unsigned long long* work, const uint8_t* full, long long stride,
+               cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     if (work)
         render_fwd_kernel<TILE, BATCH, true><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
-                                                                                        nl, work);
+                                                                                        nl, work, full, stride);
     else
         render_fwd_kernel<TILE, BATCH, false><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
-                                                                                         nl, nullptr);
+                                                                                         nl, nullptr, nullptr, 1);
     count_launch();
     return check_launch("render_fwd_kernel");
 }
@@ -391,11 +448,12 @@ constexpr int bwd_ppl() { return TILE == 32 ? 4 : 2; }
 
 template <int TILE, int BATCH>
 int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
-               const float* tf, const int* nl, const float* dimg, dass_splat_grad* gs, cudaStream_t st) {
+               const float* tf, const int* nl, const float* dimg, const uint8_t* full, long long stride,
+               dass_splat_grad* gs, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int PPL = bwd_ppl<TILE>();
     render_bwd_kernel<TILE, BATCH, PPL><<<ct.tiles_total, TILE * TILE / PPL, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
-                                                                                    gs);
+                                                                                    full, stride, gs);
     count_launch();
     return check_launch("render_bwd_kernel");
 }
@@ -418,14 +476,16 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
 
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
-                      unsigned long long* work) {
-    DASS_DISPATCH(launch_fwd, splats, pair_rec, ranges, ct, bg, image, T_final, n_last, work, st)
+                      unsigned long long* work, const uint8_t* full_grad, long long rec_stride) {
+    DASS_DISPATCH(launch_fwd, splats, pair_rec, ranges, ct, bg, image, T_final, n_last, work, full_grad, rec_stride,
+                  st)
 }
 
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
-                      dass_splat_grad* gsplat, cudaStream_t st) {
-    DASS_DISPATCH(launch_bwd, splats, pair_rec, ranges, ct, bg, T_final, n_last, dL_dimage, gsplat, st)
+                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st) {
+    DASS_DISPATCH(launch_bwd, splats, pair_rec, ranges, ct, bg, T_final, n_last, dL_dimage, full_grad, rec_stride,
+                  gsplat, st)
 }
 
 }  // namespace dass

@@ -50,7 +50,8 @@ class dass_step_desc(C.Structure):
         ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_cams", C.c_int32),
         ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
         ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("cams", C.c_void_p), ("targets", C.c_void_p),
-        ("n_dyn", C.c_int64), ("dyn_idx", C.c_void_p), ("offsets", C.c_void_p), ("offset_grad", C.c_void_p),
+        ("n_dyn", C.c_int64), ("dyn_idx", C.c_void_p), ("dyn_mask", C.c_void_p), ("offsets", C.c_void_p),
+        ("offset_grad", C.c_void_p),
         ("adam_m", C.c_void_p), ("adam_v", C.c_void_p), ("adam_step", C.c_void_p),
         ("lr_mu", C.c_float), ("lr_sigma", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
         ("eps", C.c_float), ("lambda_dssim", C.c_float),
@@ -77,14 +78,15 @@ _SIGS = {
     "dass_last_error": (C.c_char_p, []),
     "dass_kernel_launches": (C.c_int64, []),
     "dass_tile_layout": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
-    "dass_render_work": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
+    "dass_render_work": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P]),
     "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
     "dass_preprocess_scenes": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _P, _P]),
     "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort_static": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]),
     "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
-    "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, C.c_int64,
+                                  _P, _P]),
     "dass_preprocess_bwd": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P,
                                       C.c_int64, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P]),
     "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
@@ -234,20 +236,22 @@ def dass_kernel_launches():
     return int(load().dass_kernel_launches())
 
 
-def dass_render_work(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, work, stream=None):
-    """work: int64 CUDA tensor of 4 (counts, see include/dass.h)."""
+def dass_render_work(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, work, full_grad=None,
+                     rec_stride=0, stream=None):
+    """work: int64 CUDA tensor of 5 (counts, see include/dass.h)."""
     arr = cameras(cams)
     _call("dass_render_work", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams), tile,
-          batch, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _ptr(work, I64), _stream(stream))
+          batch, _ptr(full_grad, U8), rec_stride, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32),
+          _ptr(work, I64), _stream(stream))
 
 
 def dass_render_bwd(splats, pair_rec, tile_ranges, cams, tile, batch, T_final, n_last, dL_dimage, splat_grads,
-                    bg=None, stream=None):
+                    bg=None, full_grad=None, rec_stride=0, stream=None):
     arr = cameras(cams)
     bgp = (C.c_float * 3)(*bg) if bg is not None else None
     _call("dass_render_bwd", _ptr(splats, F32), splat_grads.numel() // GRAD_FLOATS, _ptr(pair_rec, I32),
           _ptr(tile_ranges, I32), arr, len(cams), tile, batch, bgp, _ptr(T_final, F32), _ptr(n_last, I32),
-          _ptr(dL_dimage, F32), _ptr(splat_grads, F32), _stream(stream))
+          _ptr(dL_dimage, F32), _ptr(full_grad, U8), rec_stride, _ptr(splat_grads, F32), _stream(stream))
 
 
 def dass_preprocess_bwd(g, cams, splats, splat_grads, out, grad_flags=GRAD_ALL, rows=None, accumulate=False,

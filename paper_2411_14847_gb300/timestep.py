@@ -36,6 +36,10 @@ class ShiftStage:
         self.offsets = offsets.contiguous()
         self.n_dyn = int(self.dyn_idx.numel())
         dev = self.g["means"].device
+        # per-Gaussian dynamics mask (Sec. 3.3), the dense form of dyn_idx
+        self.dyn_mask = torch.zeros(max(1, self.n), dtype=torch.uint8, device=dev)
+        if self.n_dyn:
+            self.dyn_mask[self.dyn_idx.long()] = 1
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.frame = Frame(self.cams, self.n, tile=tile, batch=batch, pair_capacity=pair_capacity or 1024)
         fr = self.frame
@@ -71,6 +75,7 @@ class ShiftStage:
         d.targets = _vp(self.targets)
         d.n_dyn = self.n_dyn
         d.dyn_idx, d.offsets, d.offset_grad = _vp(self.dyn_idx), _vp(self.offsets), _vp(self.offset_grad)
+        d.dyn_mask = _vp(self.dyn_mask)
         d.adam_m, d.adam_v, d.adam_step = _vp(self.adam_m), _vp(self.adam_v), _vp(self.adam_step)
         for k, v in self.hp.items():
             setattr(d, k, v)

@@ -258,3 +258,27 @@ def test_loss_parity(dass):
         torch.cuda.synchronize()
         assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
         assert rel_l2(dx.cpu().numpy(), np.concatenate([g.reshape(-1).numpy() for g in ref_g])) < 1e-4
+
+
+def test_backward_mean_only_for_unmasked_gaussians(dass):
+    """With a per-Gaussian mask, unmasked Gaussians receive only dL/dmean2D (same values as the
+    full backward); masked ones receive the full splat gradient."""
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene, cams = _small_multicam(n=2500)
+    g = raster.to_device(scene.arrays())
+    fr = _frame(dass, cams, scene.n, tile=16, batch=128)
+    fr.render(g)
+    dimg = torch.randn_like(fr.image) * 1e-3
+    fr.render_bwd(dimg)
+    full = fr.splat_grads.clone()
+    mask = (torch.rand(scene.n, device="cuda") < 0.2).to(torch.uint8)
+    D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, cams, 16, 128, fr.T_final, fr.n_last, dimg,
+                      fr.splat_grads, full_grad=mask, rec_stride=scene.n)
+    torch.cuda.synchronize()
+    part = fr.splat_grads.view(len(cams), scene.n, 12)
+    ref = full.view(len(cams), scene.n, 12)
+    m = mask.bool()
+    assert rel_l2(part[:, m].cpu().numpy(), ref[:, m].cpu().numpy()) < 1e-5
+    assert rel_l2(part[:, ~m, 0:2].cpu().numpy(), ref[:, ~m, 0:2].cpu().numpy()) < 1e-5
+    assert float(part[:, ~m, 2:].abs().max()) == 0.0
+    assert float(ref[:, ~m, 2:9].abs().max()) > 0.0
