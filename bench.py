@@ -369,6 +369,18 @@ def main():
     n_pairs = int(sfr.counters[0].item())
     sort_ms = timed(lambda: D.dass_bin_sort(sfr.splats, sfr.n, cams, tile, sfr.pair_rec, sfr.tile_ranges,
                                             sfr.counters, sfr.workspace), reps=5)
+    # the other stages of one iteration, each timed alone on the same buffers
+    gs = {k: v for k, v in stage.g.items()}
+    gs["means"], gs["quats"] = stage.render_means, stage.render_quats
+    pre_ms = timed(lambda: D.dass_preprocess(gs, cams, tile, sfr.splats), reps=5)
+    loss_t = torch.zeros(1, dtype=torch.float64, device=dev)
+    lws = torch.empty(D.dass_loss_workspace(cams), dtype=torch.uint8, device=dev)
+    loss_ms = timed(lambda: D.dass_loss(sfr.image, stage.targets, cams, 0.2, stage.dL_dimage, loss_t, lws), reps=5)
+    pbwd_ms = timed(lambda: D.dass_preprocess_bwd(gs, cams, sfr.splats, sfr.splat_grads,
+                                                  {"d_means": stage.d_means_dyn, "d_quats": stage.d_quats_dyn},
+                                                  D.GRAD_MEANS | D.GRAD_QUATS, rows=stage.dyn_idx), reps=5)
+    stats_ms = timed(lambda: D.dass_densify_stats(sfr.n, sfr.splats, sfr.splat_grads, cams, stage.stat_accum,
+                                                  stage.stat_count), reps=5)
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     mhz = clk["sm_mhz"] or 2070.0
@@ -385,6 +397,8 @@ def main():
                 "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
+               "preprocess_ms": round(pre_ms, 3), "loss_ms": round(loss_ms, 3),
+               "preprocess_bwd_dyn_ms": round(pbwd_ms, 3), "densify_stats_ms": round(stats_ms, 3),
                "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
                "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "pairs_added_dynamic": n_add_dyn,
                "list_prefix_bwd": n_bwd,
