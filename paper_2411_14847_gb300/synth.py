@@ -218,3 +218,65 @@ def config_c(seed=1003, n=300_000, n_cams=20, width=1352, height=1014):
 
 def cameras_array(cams) -> np.ndarray:
     return np.stack([c.as_record() for c in cams])
+
+
+# ----------------------------------------------------------------- streaming scene
+
+@dataclass
+class MovingScene:
+    """A scene whose dynamic Gaussians move on seeded sinusoids and rotate, and whose `new`
+    Gaussians appear (opacity from ~0 to drawn values) at `t_appear` (the streaming workload).
+
+    means_dyn(t) = means0[dyn] + amplitude * sin(2 pi t / period + phase) * axis; orientation turned
+    by rate_deg * t degrees about a per-Gaussian world axis (composed with SciPy's Rotation).
+    """
+    base: Scene                 # every Gaussian at t = 0 (new ones with opacity logit -20)
+    dyn_idx: np.ndarray
+    axis: np.ndarray
+    phase: np.ndarray
+    rot_axis: np.ndarray
+    new_idx: np.ndarray
+    new_logit: np.ndarray
+    amplitude: float = 0.05
+    period: float = 40.0
+    rate_deg: float = 2.0
+    t_appear: int = 15
+
+    def at(self, t) -> Scene:
+        sc = self.base.copy()
+        d = self.dyn_idx
+        s = np.sin(2 * np.pi * t / self.period + self.phase)[:, None]
+        sc.means[d] = (self.base.means[d] + self.amplitude * s * self.axis).astype(np.float32)
+        # ground-truth rotation of the dynamic Gaussians, composed with SciPy (scalar-last quaternions)
+        from scipy.spatial.transform import Rotation
+        q0 = self.base.quats[d].astype(np.float64)[:, [1, 2, 3, 0]]
+        turn = Rotation.from_rotvec(np.deg2rad(self.rate_deg * t) * self.rot_axis)
+        q = (turn * Rotation.from_quat(q0)).as_quat()
+        sc.quats[d] = q[:, [3, 0, 1, 2]].astype(np.float32)
+        if t >= self.t_appear:
+            sc.opacity_logit[self.new_idx] = self.new_logit
+        return sc
+
+    def initial(self) -> Scene:
+        """G_0 as the reconstruction starts from it: every Gaussian except the ones not yet there."""
+        keep = np.setdiff1d(np.arange(self.base.n), self.new_idx)
+        b = self.base
+        return Scene(b.means[keep].copy(), b.log_scales[keep].copy(), b.quats[keep].copy(),
+                     b.opacity_logit[keep].copy(), b.sh[keep].copy(), b.sh_degree)
+
+
+def moving_scene(n_static, n_dyn, n_new, sh_degree, seed, box=ARC_BOX, log_scale_mean=-4.0, **kw) -> MovingScene:
+    """Streaming workload: n_static static + n_dyn dynamic Gaussians (dynamic ones first after the
+    static ones), plus n_new Gaussians that appear at t_appear (last rows)."""
+    n = n_static + n_dyn + n_new
+    sc = random_scene(n, sh_degree, seed, box=box, log_scale_mean=log_scale_mean)
+    rng = np.random.default_rng(seed + 1)
+    dyn = np.arange(n_static, n_static + n_dyn, dtype=np.int32)
+    new = np.arange(n_static + n_dyn, n, dtype=np.int64)
+    axis = rng.normal(size=(n_dyn, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    rax = rng.normal(size=(n_dyn, 3))
+    rax /= np.linalg.norm(rax, axis=1, keepdims=True)
+    new_logit = sc.opacity_logit[new].copy()
+    sc.opacity_logit[new] = -20.0
+    return MovingScene(sc, dyn, axis, rng.uniform(0, 2 * np.pi, n_dyn), rax, new, new_logit, **kw)
