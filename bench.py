@@ -45,6 +45,9 @@ FLOP_BWD_ADD = 64
 # Backward of a pair whose Gaussian only needs dL/dmean2D (static in the shift stage): alpha again,
 # T_j, dL/dalpha, behind-colour update, dpow, dL/du, dL/dv and 2 reduction adds = 43 flop.
 FLOP_BWD_MEAN_ADD = 43
+# DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture scaled to 20
+# cameras, profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
+RENDER_BWD_TRAFFIC = 8.80e8
 
 
 def parse():
@@ -392,7 +395,8 @@ def main():
     dom = "render_bwd" if bwd_ms >= fwd_ms else "render_fwd"
     ach = bwd_tf if dom == "render_bwd" else fwd_tf
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
-                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                "traffic": RENDER_BWD_TRAFFIC if (dom == "render_bwd" and tile == 32) else None,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)",
                 "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
