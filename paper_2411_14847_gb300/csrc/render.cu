@@ -125,8 +125,8 @@ __device__ __forceinline__ void pix_fwd_store(const PixFwd& p, const CamInfo& ca
 // and each lane the two pixels (x, y) and (x, y + 4) of it.
 // COUNT = true is a separate instantiation used only to measure the work of a render (pairs
 // evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false instantiations.
-template <int TILE, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_splat* __restrict__ splats,
+template <int TILE, int BATCH, bool COUNT, int CT = TILE>
+__global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat* __restrict__ splats,
                                                                    const uint32_t* __restrict__ pair_rec,
                                                                    const uint32_t* __restrict__ ranges, CamTable ct,
                                                                    float3 bg, float* __restrict__ image,
@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
                                                                    unsigned long long* __restrict__ work,
                                                                    const uint8_t* __restrict__ full_grad,
                                                                    long long rec_stride) {
-    constexpr int NT = TILE * TILE / 2;
+    constexpr int NT = CT * CT / 2;
     constexpr int NW = NT / 32;
-    constexpr int WX = TILE / 8;
+    constexpr int WX = CT / 8;
+    constexpr int S = TILE / CT;      // CTAs per tile side
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
     __shared__ float4 sF[BATCH];
@@ -145,10 +146,11 @@ __global__ void __launch_bounds__(TILE* TILE / 2) render_fwd_kernel(const dass_s
     __shared__ unsigned short sList[NW][BATCH];
     __shared__ uint8_t sFullC[COUNT ? BATCH : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile_id = blockIdx.x;
+    const int tile_id = blockIdx.x / (S * S);
+    const int sub = blockIdx.x % (S * S);
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
-    const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
+    const int tx0 = (local % cam.tiles_x) * TILE + (sub % S) * CT, ty0 = (local / cam.tiles_x) * TILE + (sub / S) * CT;
     const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * 8;
     const int px = bxi + (lane & 7);
     const int py = byi + (lane >> 3);
@@ -321,17 +323,18 @@ __device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
 // per-Gaussian warp reduction is shared by 32*PPL pixels. full_grad (optional, per Gaussian of
 // the record stride) selects Gaussians whose complete splat gradient is wanted; the others only
 // receive dL/d(mean2D).
-template <int TILE, int BATCH, int PPL>
-__global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
+template <int TILE, int BATCH, int PPL, int CT = TILE>
+__global__ void __launch_bounds__(CT* CT / PPL) render_bwd_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
     dass_splat_grad* __restrict__ gsplat) {
-    constexpr int NT = TILE * TILE / PPL;
+    constexpr int NT = CT * CT / PPL;
     constexpr int NW = NT / 32;
-    constexpr int WX = TILE / 8;
+    constexpr int WX = CT / 8;
     constexpr int BH = 4 * PPL;
-    static_assert(BH <= TILE, "warp block taller than the tile");
+    constexpr int S = TILE / CT;      // CTAs per tile side
+    static_assert(BH <= CT, "warp block taller than the CTA tile");
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
     __shared__ float4 sF[BATCH];
@@ -342,10 +345,11 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
     __shared__ uint8_t sFull[BATCH];
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile_id = blockIdx.x;
+    const int tile_id = blockIdx.x / (S * S);
+    const int sub = blockIdx.x % (S * S);
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
-    const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
+    const int tx0 = (local % cam.tiles_x) * TILE + (sub % S) * CT, ty0 = (local / cam.tiles_x) * TILE + (sub / S) * CT;
     const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * BH;
     const int px = bxi + (lane & 7);
     const int py = byi + (lane >> 3);
@@ -426,17 +430,28 @@ __global__ void __launch_bounds__(TILE* TILE / PPL) render_bwd_kernel(
     }
 }
 
+// CTA side of the compositing kernels for a binning tile: a tile's list can be composited by
+// (TILE/CT)^2 independent CTAs, each covering a CT x CT part of the tile. Measured on the 300k x
+// 20-view workload: 32-pixel bins are composited fastest by 16 x 16 forward CTAs (fewer warps
+// wait at each staged batch) and by whole-tile backward CTAs.
+template <int TILE>
+constexpr int fwd_cta() { return TILE == 32 ? 16 : TILE; }
+template <int TILE>
+constexpr int bwd_cta() { return TILE; }
+
 template <int TILE, int BATCH>
 int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                float* img, float* tf, int* nl, unsigned long long* work, const uint8_t* full, long long stride,
                cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
+    constexpr int CT = fwd_cta<TILE>();
+    constexpr int NB = (TILE / CT) * (TILE / CT);
     if (work)
-        render_fwd_kernel<TILE, BATCH, true><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
-                                                                                        nl, work, full, stride);
+        render_fwd_kernel<TILE, BATCH, true, CT><<<ct.tiles_total * NB, CT * CT / 2, 0, st>>>(sp, pr, rg, ct, bg, img,
+                                                                                             tf, nl, work, full, stride);
     else
-        render_fwd_kernel<TILE, BATCH, false><<<ct.tiles_total, TILE * TILE / 2, 0, st>>>(sp, pr, rg, ct, bg, img, tf,
-                                                                                         nl, nullptr, nullptr, 1);
+        render_fwd_kernel<TILE, BATCH, false, CT><<<ct.tiles_total * NB, CT * CT / 2, 0, st>>>(
+            sp, pr, rg, ct, bg, img, tf, nl, nullptr, nullptr, 1);
     count_launch();
     return check_launch("render_fwd_kernel");
 }
@@ -452,8 +467,10 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
                dass_splat_grad* gs, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int PPL = bwd_ppl<TILE>();
-    render_bwd_kernel<TILE, BATCH, PPL><<<ct.tiles_total, TILE * TILE / PPL, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
-                                                                                    full, stride, gs);
+    constexpr int CT = bwd_cta<TILE>();
+    constexpr int NB = (TILE / CT) * (TILE / CT);
+    render_bwd_kernel<TILE, BATCH, PPL, CT><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(sp, pr, rg, ct, bg, tf, nl,
+                                                                                          dimg, full, stride, gs);
     count_launch();
     return check_launch("render_bwd_kernel");
 }
