@@ -214,7 +214,10 @@ int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const u
  * full_grad (optional, device uint8 per Gaussian g = record % rec_stride; NULL = all): Gaussians
  * with full_grad[g] == 0 only receive splat_grads.mean2d (what the densification statistics
  * read), their other fields stay 0 -- e.g. the static Gaussians of the shift stage (Sec. 3.3),
- * whose parameters are not optimised; transmittance and colours are propagated identically. */
+ * whose parameters are not optimised; transmittance and colours are propagated identically.
+ * The first call for a (tile, batch) on a device opts the kernel in to more than 48 KB of
+ * shared memory per CTA (a host-side attribute): make that first call outside CUDA stream
+ * capture (dass_step does this itself before it captures). */
 int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
                     const uint32_t* tile_ranges, const dass_camera* cams /* host */, int n_cams,
                     int tile, int batch, const float* bg /* host, 3 */, const float* T_final,

@@ -29,6 +29,7 @@ int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
                       unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,
                       long long rec_stride = 1);
+int render_prepare(int tile, int batch);
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
@@ -539,6 +540,7 @@ DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* str
         if (st == nullptr) return DASS_ERR_INVALID_ARG;   // the legacy stream cannot be captured
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
+        if (int rc = render_prepare(d->tile, d->batch)) return rc;   // attributes are not set under capture
         DASS_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         long long l0 = launches_so_far();
         int rc = step_iteration(d, p, mode, st);

@@ -105,6 +105,21 @@ __device__ __forceinline__ float splat_alpha(float o, float G) {
     return fminf(kAlphaMax, __fmul_rn(o, G));
 }
 
+// Packed FP32x2 forms (sm_100+ two-lane add/mul/fma, round-to-nearest on each lane): the same
+// operation sequence as splat_gauss for two pixels at once, bit-identical lane by lane.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, one rounding
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 one_minus2(float2 a) { return sub2(make_float2(1.f, 1.f), a); }
+
+__device__ __forceinline__ float2 splat_gauss2(float2 ap, float2 b2p, float2 cp, float2 dx, float2 dy) {
+    const float2 t = __fmul2_rn(b2p, dy);
+    const float2 s = __ffma2_rn(ap, dx, t);
+    const float2 cdy = __fmul2_rn(cp, dy);
+    const float2 q = __ffma2_rn(dx, s, __fmul2_rn(cdy, dy));
+    return make_float2(ex2_approx(q.x), ex2_approx(q.y));
+}
+
 // ----------------------------------------------------------------- real SH (degree <= 3)
 
 // Real spherical harmonics without the Condon-Shortley phase, k = l*l + l + m. Constants are
@@ -223,12 +238,20 @@ struct Footprint {
     float u, v, a, b, c, k2, ex, ey;
 };
 
+// k2 of the footprint, or -1 if the splat has none (opacity <= 1/255 or a degenerate conic).
+__device__ __forceinline__ float footprint_k2(float a, float b, float c, float o) {
+    if (!(255.f * o > 1.f)) return -1.f;
+    float det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+    if (!(det > 0.f)) return -1.f;
+    return __fadd_rn(__fmul_rn(2.f, logf(__fmul_rn(255.f, o))), kRadiusSlack);
+}
+
 __device__ __forceinline__ bool footprint_of(float u, float v, float a, float b, float c, float o, Footprint& f) {
     if (!(255.f * o > 1.f)) return false;
     float det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
     if (!(det > 0.f)) return false;
     f.u = u; f.v = v; f.a = a; f.b = b; f.c = c;
-    f.k2 = __fadd_rn(__fmul_rn(2.f, logf(__fmul_rn(255.f, o))), kRadiusSlack);
+    f.k2 = footprint_k2(a, b, c, o);
     f.ex = __fsqrt_rn(__fdiv_rn(__fmul_rn(f.k2, c), det));
     f.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(f.k2, a), det));
     return true;

@@ -14,9 +14,9 @@ namespace dass {
 
 namespace {
 
-constexpr int kT = 16;           // output tile
+
 constexpr int kR = 5;            // window radius
-constexpr int kS = kT + 2 * kR;  // staged tile side (26)
+
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 

@@ -1,33 +1,72 @@
 // Forward and backward alpha compositing (App. A.1) over every tile of every camera in one
-// launch. One CTA per B x B tile; each warp owns an 8 x 8 block of pixels, two pixels per lane.
-// The tile's depth-sorted Gaussians are staged through shared memory in batches; after each
-// batch is staged, every warp compacts (ballot + prefix popcount, order preserved) the entries
-// whose alpha >= 1/255 footprint ellipse reaches its own block of pixels, and composites only
-// those. The backward walks the lists in reverse from the last contributor, recomputing alpha
-// and T_j = T_{j+1}/(1-alpha_j) from the saved T_final, and reduces per-Gaussian gradients
+// launch. A CTA covers a CT x CT part of a binning tile; each warp owns an 8 x 4*PPL block of
+// pixels and each lane PPL pixels of one column (rows y + 4k), handled as pixel pairs with the
+// packed FP32x2 arithmetic of sm_100+ (two-lane add/mul/fma that round like their scalar forms,
+// so the packed alpha is bit-identical to a scalar evaluation). The tile's depth-sorted
+// Gaussians are staged through shared memory in batches; after each batch is staged, every
+// warp compacts (ballot + prefix popcount, order preserved) the entries whose alpha >= 1/255
+// footprint ellipse reaches its own block of pixels, and composites only those. The backward
+// walks the lists in reverse from the last contributor, recomputing alpha and
+// T_j = T_{j+1}/(1-alpha_j) from the saved T_final, and reduces per-Gaussian gradients
 // warp-wide (shuffles), then block-wide (shared-memory atomics), then into global memory
 // (vector atomics).
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 
 namespace dass {
 
 namespace {
 
-// Stage one splat into its shared-memory form (identical in forward and backward):
-//   A = (u, v, a * kNegHalfLog2e, c * kNegHalfLog2e), B = (2 b * kNegHalfLog2e, o, r, g),
-//   F = (a, b, c, k2) with the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
-__device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splats, uint32_t rec, float4& A, float4& Bv,
-                                            float4& F, float& blue) {
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device (once per kernel and
+// device; a no-op up to the default 48 KB).
+int allow_smem(const void* kernel, int bytes) {
+    if (bytes <= 48 * 1024) return DASS_OK;
+    int dev = 0;
+    DASS_CHECK_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return DASS_OK;
+    DASS_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.insert({kernel, dev});
+    return DASS_OK;
+}
+
+// Staged form of a splat: NG float4 groups in structure-of-arrays shared memory. Every scalar
+// of the per-pixel math is stored twice, so one shared load yields the operand pair of the
+// packed arithmetic without register moves:
+//   P0 = (-u, -u, -v, -v)     P1 = (a', a', b2', b2')     P2 = (c', c', o, o)
+//   P3 = (r, r, g, g)         P4 = (blue, blue, a, a)     P5 = (b, b, c, c)   (backward only)
+// with a' = a kNegHalfLog2e, b2' = 2 b kNegHalfLog2e, c' = c kNegHalfLog2e (see splat_gauss);
+// F = (a, b, c, k2) is the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
+template <int NG, int BATCH>
+__device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splats, uint32_t rec, int i,
+                                            float4 (&sP)[NG][BATCH], float4 (&sF)[BATCH]) {
     const float4* sp = reinterpret_cast<const float4*>(splats + rec);
-    float4 s0 = __ldg(sp);
-    float4 s1 = __ldg(sp + 1);
-    float s2 = __ldg(reinterpret_cast<const float*>(sp + 2));
-    A = make_float4(s0.x, s0.y, __fmul_rn(s0.z, kNegHalfLog2e), __fmul_rn(s1.x, kNegHalfLog2e));
-    Bv = make_float4(__fmul_rn(2.f * s0.w, kNegHalfLog2e), s1.y, s1.z, s1.w);
-    Footprint f;
-    float k2 = footprint_of(s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, f) ? f.k2 : -1.f;
-    F = make_float4(s0.z, s0.w, s1.x, k2);
-    blue = s2;
+    const float4 s0 = __ldg(sp);        // u, v, a, b
+    const float4 s1 = __ldg(sp + 1);    // c, o, r, g
+    const float bl = __ldg(reinterpret_cast<const float*>(sp + 2));
+    const float ap = __fmul_rn(s0.z, kNegHalfLog2e), b2p = __fmul_rn(2.f * s0.w, kNegHalfLog2e),
+                cp = __fmul_rn(s1.x, kNegHalfLog2e);
+    sP[0][i] = make_float4(-s0.x, -s0.x, -s0.y, -s0.y);
+    sP[1][i] = make_float4(ap, ap, b2p, b2p);
+    sP[2][i] = make_float4(cp, cp, s1.y, s1.y);
+    sP[3][i] = make_float4(s1.z, s1.z, s1.w, s1.w);
+    sP[4][i] = make_float4(bl, bl, s0.z, s0.z);
+    if constexpr (NG > 5) sP[5][i] = make_float4(s0.w, s0.w, s1.x, s1.x);
+    sF[i] = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
+}
+
+__device__ __forceinline__ float2 lo2(const float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 v) { return make_float2(v.z, v.w); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -36,15 +75,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Does the footprint of staged entry (A.xy = centre, F = conic + k2) reach the warp's 8x4 block
-// whose first pixel centre is (bx, by)? Ellipse-rectangle test: the quadratic form is evaluated
-// at a point of each edge facing the centre (the clamped 1-D minimiser, computed with a fast
-// division); any point of the rectangle gives an upper bound of its minimum, so a Gaussian is
-// culled only if every pixel of the block is outside its footprint (up to k2's slack).
+// Does the footprint F of a staged entry centred at (u, v) = -(nu, nv) reach the warp's 8 x BH
+// block whose first pixel centre is (bx, by)? Ellipse-rectangle test: the quadratic form is
+// evaluated at a point of each edge facing the centre (the clamped 1-D minimiser, computed with
+// a fast division); any point of the rectangle gives an upper bound of its minimum, so a
+// Gaussian is culled only if every pixel of the block is outside its footprint (up to k2's slack).
 template <int BH>
-__device__ __forceinline__ bool reaches_block(const float4 A, const float4 F, float bx, float by) {
+__device__ __forceinline__ bool reaches_block(float nu, float nv, const float4 F, float bx, float by) {
     if (F.w < 0.f) return false;
-    const float x0 = bx - A.x, x1 = bx + 7.f - A.x, y0 = by - A.y, y1 = by + (float)(BH - 1) - A.y;
+    const float x0 = bx + nu, x1 = (bx + 7.f) + nu, y0 = by + nv, y1 = (by + (float)(BH - 1)) + nv;
     const bool in_x = x0 <= 0.f && x1 >= 0.f, in_y = y0 <= 0.f && y1 >= 0.f;
     if (in_x && in_y) return true;
     float qmin = 3.4e38f;
@@ -63,14 +102,18 @@ __device__ __forceinline__ bool reaches_block(const float4 A, const float4 F, fl
 
 // Compact the indices [0, cnt) of the staged batch whose footprint reaches this warp's 8 x BH
 // block into list[] (ascending), only indices <= jmax. Returns the count (warp-uniform).
-template <int BH>
-__device__ __forceinline__ int warp_compact(const float4* __restrict__ sA, const float4* __restrict__ sF, int cnt,
+template <int BH, int BATCH>
+__device__ __forceinline__ int warp_compact(const float4* __restrict__ sP0, const float4* __restrict__ sF, int cnt,
                                             int jmax, float bx, float by, unsigned short* list, int lane) {
     int n = 0;
     int lim = min(cnt, jmax + 1);
     for (int j0 = 0; j0 < lim; j0 += 32) {
         int j = j0 + lane;
-        bool hit = j < lim && reaches_block<BH>(sA[j], sF[j], bx, by);
+        bool hit = false;
+        if (j < lim) {
+            const float4 c = sP0[j];
+            hit = reaches_block<BH>(c.x, c.z, sF[j], bx, by);
+        }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[n + __popc(m & lanemask_lt())] = (unsigned short)j;
         n += __popc(m);
@@ -79,50 +122,66 @@ __device__ __forceinline__ int warp_compact(const float4* __restrict__ sA, const
     return n;
 }
 
-// Forward state of one pixel.
-struct PixFwd {
-    float fy, T, C0, C1, C2;
-    int last;
-    bool done;
+// Forward state of a lane's pixel pair (rows y and y + 4 of one column).
+struct PixFwd2 {
+    float2 fy, T, C0, C1, C2;
+    int last0, last1;
+    bool done0, done1;
     unsigned long long n_eval, n_add, n_full;
 };
 
+// Front-to-back step of staged entry P0..P4 (list position pos) for both pixels: skip alpha <
+// 1/255, stop before T (1 - alpha) < 1e-4, else blend. A pixel that skips or is done gets alpha
+// = 0 in the packed blend, which leaves its colour and transmittance exactly unchanged.
 template <bool COUNT>
-__device__ __forceinline__ void pix_fwd_step(PixFwd& p, int pos, float dx, const float4 A, const float4 Bv,
-                                             const float* __restrict__ sC, int j, bool full = false) {
-    if (p.done) return;
-    const float dy = __fsub_rn(p.fy, A.y);
-    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
-    const float alpha = splat_alpha(Bv.y, G);
-    if (COUNT) ++p.n_eval;
-    if (alpha < kAlphaMin) return;
-    const float test = __fmul_rn(p.T, __fsub_rn(1.f, alpha));
-    if (test < kTStop) { p.done = true; return; }
-    if (COUNT) { ++p.n_add; p.n_full += full ? 1ull : 0ull; }
-    const float w = __fmul_rn(alpha, p.T);
-    p.C0 = __fmaf_rn(Bv.z, w, p.C0);
-    p.C1 = __fmaf_rn(Bv.w, w, p.C1);
-    p.C2 = __fmaf_rn(sC[j], w, p.C2);
-    p.T = test;
-    p.last = pos;
+__device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 dx, const float4 P0, const float4 P1,
+                                              const float4 P2, const float4 P3, float2 blue, bool full) {
+    const float2 dy = __fadd2_rn(p.fy, hi2(P0));
+    const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
+    const float2 oG = __fmul2_rn(hi2(P2), G);
+    float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+    const float2 test = __fmul2_rn(p.T, one_minus2(alpha));
+    bool ok0 = !p.done0 && !(alpha.x < kAlphaMin);
+    bool ok1 = !p.done1 && !(alpha.y < kAlphaMin);
+    if (COUNT) p.n_eval += (unsigned long long)(!p.done0) + (unsigned long long)(!p.done1);
+    const bool stop0 = ok0 && test.x < kTStop, stop1 = ok1 && test.y < kTStop;
+    p.done0 = p.done0 || stop0;
+    p.done1 = p.done1 || stop1;
+    ok0 = ok0 && !stop0;
+    ok1 = ok1 && !stop1;
+    if (COUNT) {
+        const unsigned long long k = (unsigned long long)ok0 + (unsigned long long)ok1;
+        p.n_add += k;
+        p.n_full += full ? k : 0ull;
+    }
+    alpha.x = ok0 ? alpha.x : 0.f;
+    alpha.y = ok1 ? alpha.y : 0.f;
+    const float2 w = __fmul2_rn(alpha, p.T);
+    p.C0 = __ffma2_rn(lo2(P3), w, p.C0);
+    p.C1 = __ffma2_rn(hi2(P3), w, p.C1);
+    p.C2 = __ffma2_rn(blue, w, p.C2);
+    p.T.x = ok0 ? test.x : p.T.x;
+    p.T.y = ok1 ? test.y : p.T.y;
+    p.last0 = ok0 ? pos : p.last0;
+    p.last1 = ok1 ? pos : p.last1;
 }
 
-__device__ __forceinline__ void pix_fwd_store(const PixFwd& p, const CamInfo& cam, int px, int py, float3 bg,
-                                              float* __restrict__ image, float* __restrict__ T_final,
-                                              int* __restrict__ n_last) {
+__device__ __forceinline__ void pix_fwd_store(float T, float C0, float C1, float C2, int last, const CamInfo& cam,
+                                              int px, int py, float3 bg, float* __restrict__ image,
+                                              float* __restrict__ T_final, int* __restrict__ n_last) {
     if (!(px < cam.W && py < cam.H)) return;
     const long long plane = (long long)cam.W * cam.H;
     const long long pix = (long long)py * cam.W + px;
     float* img = image + 3 * cam.pix_base;
-    img[pix] = __fmaf_rn(p.T, bg.x, p.C0);
-    img[plane + pix] = __fmaf_rn(p.T, bg.y, p.C1);
-    img[2 * plane + pix] = __fmaf_rn(p.T, bg.z, p.C2);
-    T_final[cam.pix_base + pix] = p.T;
-    n_last[cam.pix_base + pix] = p.last;
+    img[pix] = __fmaf_rn(T, bg.x, C0);
+    img[plane + pix] = __fmaf_rn(T, bg.y, C1);
+    img[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
+    T_final[cam.pix_base + pix] = T;
+    n_last[cam.pix_base + pix] = last;
 }
 
-// One CTA per tile with TILE*TILE/2 threads: warp w owns the 8 x 8 block (w % (TILE/8), w / (TILE/8))
-// and each lane the two pixels (x, y) and (x, y + 4) of it.
+// One CTA per CT x CT part of a tile with CT*CT/2 threads: warp w owns the 8 x 8 block
+// (w % (CT/8), w / (CT/8)) and each lane the two pixels (x, y) and (x, y + 4) of it.
 // COUNT = true is a separate instantiation used only to measure the work of a render (pairs
 // evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false instantiations.
 template <int TILE, int BATCH, bool COUNT, int CT = TILE>
@@ -139,10 +198,8 @@ __global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat
     constexpr int NW = NT / 32;
     constexpr int WX = CT / 8;
     constexpr int S = TILE / CT;      // CTAs per tile side
-    __shared__ float4 sA[BATCH];
-    __shared__ float4 sB[BATCH];
+    __shared__ float4 sP[5][BATCH];
     __shared__ float4 sF[BATCH];
-    __shared__ float sC[BATCH];
     __shared__ unsigned short sList[NW][BATCH];
     __shared__ uint8_t sFullC[COUNT ? BATCH : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -156,41 +213,46 @@ __global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat
     const int py = byi + (lane >> 3);
     const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
-    const float fx = (float)px;
-    PixFwd p0{(float)py, 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py < cam.H), 0ull, 0ull, 0ull};
-    PixFwd p1{(float)(py + 4), 1.f, 0.f, 0.f, 0.f, -1, !(px < cam.W && py + 4 < cam.H), 0ull, 0ull, 0ull};
+    const float2 fx2 = make_float2((float)px, (float)px);
+    PixFwd2 p;
+    p.fy = make_float2((float)py, (float)(py + 4));
+    p.T = make_float2(1.f, 1.f);
+    p.C0 = p.C1 = p.C2 = make_float2(0.f, 0.f);
+    p.last0 = p.last1 = -1;
+    p.done0 = !(px < cam.W && py < cam.H);
+    p.done1 = !(px < cam.W && py + 4 < cam.H);
+    p.n_eval = p.n_add = p.n_full = 0ull;
     for (uint32_t base = start; base < end; base += BATCH) {
-        if (__syncthreads_count(p0.done && p1.done) == NT) break;
+        if (__syncthreads_count(p.done0 && p.done1) == NT) break;
         const int cnt = min((uint32_t)BATCH, end - base);
         for (int i = tid; i < cnt; i += NT) {
             const uint32_t rec = pair_rec[base + i];
-            stage_splat(splats, rec, sA[i], sB[i], sF[i], sC[i]);
+            stage_splat<5, BATCH>(splats, rec, i, sP, sF);
             if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
         }
         __syncthreads();
-        if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
-        const int nl = warp_compact<8>(sA, sF, cnt, BATCH, bx, by, sList[warp], lane);
+        if (__all_sync(0xffffffffu, p.done0 && p.done1)) continue;
+        const int nl = warp_compact<8, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
         for (int t = 0; t < nl; ++t) {
-            if (p0.done && p1.done) break;
+            if (p.done0 && p.done1) break;
             const int j = sList[warp][t];
-            const float4 A = sA[j];
-            const float4 Bv = sB[j];
-            const float dx = __fsub_rn(fx, A.x);
+            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
+            const float2 blue = lo2(sP[4][j]);
+            const float2 dx = __fadd2_rn(fx2, lo2(P0));
             const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
-            pix_fwd_step<COUNT>(p0, (int)(base + j), dx, A, Bv, sC, j, full);
-            pix_fwd_step<COUNT>(p1, (int)(base + j), dx, A, Bv, sC, j, full);
+            pix_fwd_step2<COUNT>(p, (int)(base + j), dx, P0, P1, P2, P3, blue, full);
         }
     }
-    pix_fwd_store(p0, cam, px, py, bg, image, T_final, n_last);
-    pix_fwd_store(p1, cam, px, py + 4, bg, image, T_final, n_last);
+    pix_fwd_store(p.T.x, p.C0.x, p.C1.x, p.C2.x, p.last0, cam, px, py, bg, image, T_final, n_last);
+    pix_fwd_store(p.T.y, p.C0.y, p.C1.y, p.C2.y, p.last1, cam, px, py + 4, bg, image, T_final, n_last);
     if (COUNT) {
-        unsigned long long n_bwd = (p0.last >= 0 ? (unsigned long long)(p0.last - (int)start + 1) : 0ull) +
-                                   (p1.last >= 0 ? (unsigned long long)(p1.last - (int)start + 1) : 0ull);
-        atomicAdd(work + 0, p0.n_eval + p1.n_eval);
-        atomicAdd(work + 1, p0.n_add + p1.n_add);
+        unsigned long long n_bwd = (p.last0 >= 0 ? (unsigned long long)(p.last0 - (int)start + 1) : 0ull) +
+                                   (p.last1 >= 0 ? (unsigned long long)(p.last1 - (int)start + 1) : 0ull);
+        atomicAdd(work + 0, p.n_eval);
+        atomicAdd(work + 1, p.n_add);
         atomicAdd(work + 2, n_bwd);
         atomicAdd(work + 3, (unsigned long long)((px < cam.W && py < cam.H) + (px < cam.W && py + 4 < cam.H)));
-        atomicAdd(work + 4, p0.n_full + p1.n_full);
+        atomicAdd(work + 4, p.n_full);
     }
 }
 
@@ -226,87 +288,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Backward state of one pixel: transmittance behind the current Gaussian, upstream gradient,
-// colour behind the current Gaussian (background included) and last added list position.
-struct PixBwd {
-    float fy, T, g0, g1, g2, R0, R1, R2;
-    int last;
-};
-
-__device__ __forceinline__ void pix_bwd_load(PixBwd& p, const CamInfo& cam, int px, int py, float3 bg,
-                                             const float* __restrict__ T_final, const int* __restrict__ n_last,
-                                             const float* __restrict__ dL_dimage) {
-    p.fy = (float)py;
-    p.T = 1.f; p.g0 = p.g1 = p.g2 = 0.f; p.last = -1;
-    p.R0 = bg.x; p.R1 = bg.y; p.R2 = bg.z;
-    if (px < cam.W && py < cam.H) {
-        const long long plane = (long long)cam.W * cam.H;
-        const long long pix = (long long)py * cam.W + px;
-        const float* gi = dL_dimage + 3 * cam.pix_base;
-        p.g0 = gi[pix];
-        p.g1 = gi[plane + pix];
-        p.g2 = gi[2 * plane + pix];
-        p.T = T_final[cam.pix_base + pix];
-        p.last = n_last[cam.pix_base + pix];
-    }
-}
-
-// Gradient contribution of staged Gaussian (A, Bv, F, blue) at one pixel, added into v[0..7], eb.
-__device__ __forceinline__ bool pix_bwd_step(PixBwd& p, long long pos, float dx, const float4 A, const float4 Bv,
-                                             const float4 F, float blue, float* v, float& eb) {
-    if (pos > (long long)p.last) return false;
-    const float dy = __fsub_rn(p.fy, A.y);
-    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
-    const float alpha = splat_alpha(Bv.y, G);
-    if (alpha < kAlphaMin) return false;
-    const float om = 1.f - alpha;
-    const float Tj = __fdividef(p.T, om);
-    const float w = alpha * Tj;
-    v[6] += w * p.g0;
-    v[7] += w * p.g1;
-    eb += w * p.g2;
-    const float dLda = Tj * ((Bv.z - p.R0) * p.g0 + (Bv.w - p.R1) * p.g1 + (blue - p.R2) * p.g2);
-    p.R0 = Bv.z * alpha + om * p.R0;
-    p.R1 = Bv.w * alpha + om * p.R1;
-    p.R2 = blue * alpha + om * p.R2;
-    p.T = Tj;
-    if (Bv.y * G < kAlphaMax) {
-        const float dpow = dLda * alpha;
-        v[5] += dLda * G;
-        v[0] += dpow * (F.x * dx + F.y * dy);
-        v[1] += dpow * (F.z * dy + F.y * dx);
-        v[2] += -0.5f * dx * dx * dpow;
-        v[3] += -dx * dy * dpow;
-        v[4] += -0.5f * dy * dy * dpow;
-    }
-    return true;
-}
-
-// The same pixel step when only dL/d(mean2D) of the Gaussian is wanted (its other splat gradients
-// are not needed by the caller): transmittance and behind-colour are updated exactly as above,
-// and only the two mean2D components are accumulated (su, sv).
-__device__ __forceinline__ bool pix_bwd_step_mean(PixBwd& p, long long pos, float dx, const float4 A,
-                                                  const float4 Bv, const float4 F, float blue, float& su, float& sv) {
-    if (pos > (long long)p.last) return false;
-    const float dy = __fsub_rn(p.fy, A.y);
-    const float G = splat_gauss(A.z, Bv.x, A.w, dx, dy);
-    const float alpha = splat_alpha(Bv.y, G);
-    if (alpha < kAlphaMin) return false;
-    const float om = 1.f - alpha;
-    const float Tj = __fdividef(p.T, om);
-    const float dLda = Tj * ((Bv.z - p.R0) * p.g0 + (Bv.w - p.R1) * p.g1 + (blue - p.R2) * p.g2);
-    p.R0 = Bv.z * alpha + om * p.R0;
-    p.R1 = Bv.w * alpha + om * p.R1;
-    p.R2 = blue * alpha + om * p.R2;
-    p.T = Tj;
-    if (Bv.y * G < kAlphaMax) {
-        const float dpow = dLda * alpha;
-        su += dpow * (F.x * dx + F.y * dy);
-        sv += dpow * (F.z * dy + F.y * dx);
-    }
-    return true;
-}
-
 // Sum two values across the warp: lane 0 ends with the sum of a, lane 16 with the sum of b.
 __device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
     const bool h = lane & 16;
@@ -318,13 +299,117 @@ __device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
     return r;
 }
 
-// One CTA per tile with TILE*TILE/PPL threads: warp w owns the 8 x 4*PPL block
-// (w % (TILE/8), w / (TILE/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, so the
+// Backward state of a lane's pixel pair: transmittance behind the current Gaussian, upstream
+// gradient g = dL/dC, S = g . R with R the colour behind the current Gaussian (background
+// included), last added list position. dL/dalpha_j only needs R through g . R, and R's recurrence
+// R_j = alpha_j c_j + (1 - alpha_j) R_{j+1} carries over to S_j = alpha_j (g . c_j) + (1 - alpha_j) S_{j+1},
+// so one scalar replaces the three channels.
+struct PixBwd2 {
+    float2 fy, T, S;
+    int last0, last1;
+};
+
+__device__ __forceinline__ void pix_bwd_load1(const CamInfo& cam, int px, int py, const float* __restrict__ T_final,
+                                              const int* __restrict__ n_last, const float* __restrict__ dL_dimage,
+                                              float& T, float& g0, float& g1, float& g2, int& last) {
+    T = 1.f; g0 = g1 = g2 = 0.f; last = -1;
+    if (px < cam.W && py < cam.H) {
+        const long long plane = (long long)cam.W * cam.H;
+        const long long pix = (long long)py * cam.W + px;
+        const float* gi = dL_dimage + 3 * cam.pix_base;
+        g0 = gi[pix];
+        g1 = gi[plane + pix];
+        g2 = gi[2 * plane + pix];
+        T = T_final[cam.pix_base + pix];
+        last = n_last[cam.pix_base + pix];
+    }
+}
+
+// Loads the pair's state; its upstream gradient goes to shared memory, gp[0], gp[NT], gp[2 NT]
+// (per-thread slots, read back at every step instead of being held in registers).
+template <int NT>
+__device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamInfo& cam, int px, int py, float3 bg,
+                                              const float* __restrict__ T_final, const int* __restrict__ n_last,
+                                              const float* __restrict__ dL_dimage) {
+    float2 g0, g1, g2;
+    p.fy = make_float2((float)py, (float)(py + 4));
+    pix_bwd_load1(cam, px, py, T_final, n_last, dL_dimage, p.T.x, g0.x, g1.x, g2.x, p.last0);
+    pix_bwd_load1(cam, px, py + 4, T_final, n_last, dL_dimage, p.T.y, g0.y, g1.y, g2.y, p.last1);
+    p.S = __ffma2_rn(g2, make_float2(bg.z, bg.z),
+                     __ffma2_rn(g1, make_float2(bg.y, bg.y), __fmul2_rn(g0, make_float2(bg.x, bg.x))));
+    gp[0] = g0;
+    gp[NT] = g1;
+    gp[2 * NT] = g2;
+}
+
+// Reverse step of staged entry P0..P5 (list position pos) for both pixels of the pair; adds the
+// entry's gradient contributions: vm[0..1] (packed, both pixels) dL/d(u, v); if FULL also vf[0..2]
+// the sums of dx^2, dx dy, dy^2 times dL/d(power) (dL/d(a, b, c) after scaling by -1/2, -1, -1/2),
+// vf[3] dL/do and vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
+// 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. Returns
+// whether either pixel took part.
+template <bool FULL, int NT>
+__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, const float4 P0,
+                                              const float4 P1, const float4 P2, const float4 P3, const float4 P4,
+                                              const float4 P5, float2* vm, float2* vf) {
+    bool val0 = pos <= p.last0, val1 = pos <= p.last1;
+    if (!(val0 || val1)) return false;
+    const float2 dy = __fadd2_rn(p.fy, hi2(P0));
+    const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
+    const float2 oG = __fmul2_rn(hi2(P2), G);
+    const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+    val0 = val0 && !(alpha.x < kAlphaMin);
+    val1 = val1 && !(alpha.y < kAlphaMin);
+    if (!(val0 || val1)) return false;
+    const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
+    const float2 om = one_minus2(am);
+    const float2 Tj = __fmul2_rn(p.T, make_float2(val0 ? rcp_approx(om.x) : 1.f, val1 ? rcp_approx(om.y) : 1.f));
+    const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
+    const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
+    const float2 dLda = __fmul2_rn(Tj, sub2(gc, p.S));
+    p.S = __ffma2_rn(om, p.S, __fmul2_rn(am, gc));
+    p.T = Tj;
+    // the clamp alpha = 0.99 has zero derivative
+    const bool cm0 = val0 && oG.x < kAlphaMax, cm1 = val1 && oG.y < kAlphaMax;
+    const float2 dpow = __fmul2_rn(dLda, make_float2(cm0 ? alpha.x : 0.f, cm1 ? alpha.y : 0.f));
+    const float2 Fa = hi2(P4), Fb = lo2(P5), Fc = hi2(P5);
+    vm[0] = __ffma2_rn(dpow, __ffma2_rn(Fa, dx, __fmul2_rn(Fb, dy)), vm[0]);
+    vm[1] = __ffma2_rn(dpow, __ffma2_rn(Fc, dy, __fmul2_rn(Fb, dx)), vm[1]);
+    if (FULL) {
+        vf[0] = __ffma2_rn(__fmul2_rn(dx, dx), dpow, vf[0]);
+        vf[1] = __ffma2_rn(__fmul2_rn(dx, dy), dpow, vf[1]);
+        vf[2] = __ffma2_rn(__fmul2_rn(dy, dy), dpow, vf[2]);
+        vf[3] = __ffma2_rn(dLda, make_float2(cm0 ? G.x : 0.f, cm1 ? G.y : 0.f), vf[3]);
+        const float2 w = __fmul2_rn(am, Tj);
+        vf[4] = __ffma2_rn(w, g0, vf[4]);
+        vf[5] = __ffma2_rn(w, g1, vf[5]);
+        vf[6] = __ffma2_rn(w, g2, vf[6]);
+    }
+    return true;
+}
+
+// Dynamic shared-memory layout of the backward CTA (byte offsets; every part 16-byte aligned).
+template <int BATCH, int NT, int NP>
+struct BwdSmem {
+    static constexpr int kP = 0;                                  // float4 [6][BATCH] staged splats
+    static constexpr int kF = kP + 6 * BATCH * 16;                // float4 [BATCH] footprints
+    static constexpr int kGp = kF + BATCH * 16;                   // float2 [NP][3][NT] dL/dC of the lanes' pixels
+    static constexpr int kG = kGp + NP * 3 * NT * 8;              // float [BATCH][9] block-reduced gradients
+    static constexpr int kRec = kG + ((BATCH * 9 * 4 + 15) / 16) * 16;   // uint32 [BATCH] record indices
+    static constexpr int kList = kRec + BATCH * 4;                // ushort [NT/32][BATCH] per-warp lists
+    static constexpr int kFull = kList + ((NT / 32) * BATCH * 2 + 15) / 16 * 16;   // uint8 [BATCH]
+    static constexpr int kBytes = kFull + ((BATCH + 15) / 16) * 16;
+};
+
+// One CTA per CT x CT part of a tile with CT*CT/PPL threads: warp w owns the 8 x 4*PPL block
+// (w % (CT/8), w / (CT/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, so the
 // per-Gaussian warp reduction is shared by 32*PPL pixels. full_grad (optional, per Gaussian of
 // the record stride) selects Gaussians whose complete splat gradient is wanted; the others only
-// receive dL/d(mean2D).
+// receive dL/d(mean2D). With 4 pixels per lane the kernel is held to 80 registers so that three
+// 256-thread CTAs share an SM (the upstream gradients live in shared memory for that reason):
+// warps waiting at a CTA's batch barrier leave issue slots to the other CTAs.
 template <int TILE, int BATCH, int PPL, int CT = TILE>
-__global__ void __launch_bounds__(CT* CT / PPL) render_bwd_kernel(
+__global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
@@ -333,16 +418,18 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_bwd_kernel(
     constexpr int NW = NT / 32;
     constexpr int WX = CT / 8;
     constexpr int BH = 4 * PPL;
+    constexpr int NP = PPL / 2;       // pixel pairs per lane
     constexpr int S = TILE / CT;      // CTAs per tile side
-    static_assert(BH <= CT, "warp block taller than the CTA tile");
-    __shared__ float4 sA[BATCH];
-    __shared__ float4 sB[BATCH];
-    __shared__ float4 sF[BATCH];
-    __shared__ float sC[BATCH];
-    __shared__ uint32_t sRec[BATCH];
-    __shared__ float sG[BATCH][12];
-    __shared__ unsigned short sList[NW][BATCH];
-    __shared__ uint8_t sFull[BATCH];
+    static_assert(BH <= CT && PPL % 2 == 0, "warp block taller than the CTA tile, or odd pixels per lane");
+    using L = BwdSmem<BATCH, NT, NP>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    auto& sP = *reinterpret_cast<float4(*)[6][BATCH]>(smem + L::kP);
+    auto& sF = *reinterpret_cast<float4(*)[BATCH]>(smem + L::kF);
+    float2* sGp = reinterpret_cast<float2*>(smem + L::kGp);        // [NP][3][NT] upstream gradients
+    auto& sG = *reinterpret_cast<float(*)[BATCH][9]>(smem + L::kG);
+    uint32_t* sRec = reinterpret_cast<uint32_t*>(smem + L::kRec);
+    auto& sList = *reinterpret_cast<unsigned short(*)[NW][BATCH]>(smem + L::kList);
+    uint8_t* sFull = smem + L::kFull;
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile_id = blockIdx.x / (S * S);
@@ -355,13 +442,17 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_bwd_kernel(
     const int py = byi + (lane >> 3);
     const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id];
-    const float fx = (float)px;
-    PixBwd pp[PPL];
+    const float2 fx2 = make_float2((float)px, (float)px);
+    const uint32_t stride = (uint32_t)rec_stride;
+    // the reduced dx^2, dx dy, dy^2 sums become dL/d(a, b, c) after this lane-constant scale
+    const int gidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    const float gscale = gidx == 3 ? -1.f : (gidx == 2 || gidx == 4) ? -0.5f : 1.f;
+    PixBwd2 pp[NP];
     int mylast = -1;
 #pragma unroll
-    for (int k = 0; k < PPL; ++k) {
-        pix_bwd_load(pp[k], cam, px, py + 4 * k, bg, T_final, n_last, dL_dimage);
-        mylast = max(mylast, pp[k].last);
+    for (int k = 0; k < NP; ++k) {
+        pix_bwd_load2<NT>(pp[k], sGp + 3 * NT * k + tid, cam, px, py + 8 * k, bg, T_final, n_last, dL_dimage);
+        mylast = max(mylast, max(pp[k].last0, pp[k].last1));
     }
     if (tid == 0) s_maxlast = -1;
     __syncthreads();
@@ -374,45 +465,46 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_bwd_kernel(
         const int cnt = (int)(hi - lo);
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            uint32_t rec = pair_rec[lo + i];
+            const uint32_t rec = pair_rec[lo + i];
             sRec[i] = rec;
-            sFull[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
-            stage_splat(splats, rec, sA[i], sB[i], sF[i], sC[i]);
+            sFull[i] = full_grad ? full_grad[rec % stride] : (uint8_t)1;
+            stage_splat<6, BATCH>(splats, rec, i, sP, sF);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) sG[i][k] = 0.f;
+            for (int k = 0; k < 9; ++k) sG[i][k] = 0.f;
         }
         __syncthreads();
         const int jmax = (int)((long long)wlast - lo);   // entries beyond every lane's last are skipped
-        const int nl = jmax >= 0 ? warp_compact<BH>(sA, sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
+        const int nl = jmax >= 0 ? warp_compact<BH, BATCH>(sP[0], sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
         for (int t = nl - 1; t >= 0; --t) {
             const int j = sList[warp][t];
-            const long long pos = lo + j;
-            const float4 A = sA[j];
-            const float4 Bv = sB[j];
-            const float4 F = sF[j];
-            const float blue = sC[j];
-            const float dx = __fsub_rn(fx, A.x);
+            const int pos = (int)(lo + j);
+            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j], P5 = sP[5][j];
+            const float2 dx = __fadd2_rn(fx2, lo2(P0));
             bool contrib = false;
+            float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (sFull[j]) {          // warp-uniform: the same Gaussian for every lane
-                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                float eb = 0.f;
+                float2 vf[7];
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) contrib |= pix_bwd_step(pp[k], pos, dx, A, Bv, F, blue, v, eb);
+                for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
+                                                       P5, vm, vf);
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    float r = warp_reduce8(v, lane);
-                    float e = warp_sum(eb);
-                    if ((lane & 3) == 0) {
-                        int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                        atomicAdd(&sG[j][idx], r);
-                    }
+                    float r[8] = {vm[0].x + vm[0].y, vm[1].x + vm[1].y, vf[0].x + vf[0].y, vf[1].x + vf[1].y,
+                                  vf[2].x + vf[2].y, vf[3].x + vf[3].y, vf[4].x + vf[4].y, vf[5].x + vf[5].y};
+                    const float s = warp_reduce8(r, lane);
+                    const float e = warp_sum(vf[6].x + vf[6].y);
+                    if ((lane & 3) == 0) atomicAdd(&sG[j][gidx], s * gscale);
                     if (lane == 1) atomicAdd(&sG[j][8], e);
                 }
             } else {
-                float su = 0.f, sv = 0.f;
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) contrib |= pix_bwd_step_mean(pp[k], pos, dx, A, Bv, F, blue, su, sv);
+                for (int k = 0; k < NP; ++k)
+                    contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
+                                                        P5, vm, nullptr);
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    float r = warp_reduce2(su, sv, lane);
+                    const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
                     if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
                 }
             }
@@ -462,6 +554,14 @@ template <int TILE>
 constexpr int bwd_ppl() { return TILE == 32 ? 4 : 2; }
 
 template <int TILE, int BATCH>
+int prepare_bwd() {
+    constexpr int PPL = bwd_ppl<TILE>();
+    constexpr int CT = bwd_cta<TILE>();
+    constexpr int bytes = BwdSmem<BATCH, CT * CT / PPL, PPL / 2>::kBytes;
+    return allow_smem(reinterpret_cast<const void*>(render_bwd_kernel<TILE, BATCH, PPL, CT>), bytes);
+}
+
+template <int TILE, int BATCH>
 int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                const float* tf, const int* nl, const float* dimg, const uint8_t* full, long long stride,
                dass_splat_grad* gs, cudaStream_t st) {
@@ -469,8 +569,11 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
     constexpr int PPL = bwd_ppl<TILE>();
     constexpr int CT = bwd_cta<TILE>();
     constexpr int NB = (TILE / CT) * (TILE / CT);
-    render_bwd_kernel<TILE, BATCH, PPL, CT><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(sp, pr, rg, ct, bg, tf, nl,
-                                                                                          dimg, full, stride, gs);
+    constexpr int NT = CT * CT / PPL;
+    constexpr int bytes = BwdSmem<BATCH, NT, PPL / 2>::kBytes;
+    if (int rc = prepare_bwd<TILE, BATCH>()) return rc;
+    render_bwd_kernel<TILE, BATCH, PPL, CT><<<ct.tiles_total * NB, NT, bytes, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
+                                                                                   full, stride, gs);
     count_launch();
     return check_launch("render_bwd_kernel");
 }
@@ -503,6 +606,12 @@ int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st) {
     DASS_DISPATCH(launch_bwd, splats, pair_rec, ranges, ct, bg, T_final, n_last, dL_dimage, full_grad, rec_stride,
                   gsplat, st)
+}
+
+// Kernel attributes that must be set outside stream capture (dynamic shared memory above 48 KB).
+int render_prepare(int tile, int batch) {
+    struct { int tile; } ct{tile};
+    DASS_DISPATCH(prepare_bwd)
 }
 
 }  // namespace dass

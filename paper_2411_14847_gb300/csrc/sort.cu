@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_
     __syncthreads();
     unsigned mask = (unsigned)nd - 1u;
     long long base = (long long)blockIdx.x * kRadixTile;
-    int lane = threadIdx.x & 31;
     // all loads of the block are issued before any is used (one memory latency per block)
     uint32_t kr[kRadixItems];
 #pragma unroll
@@ -146,73 +145,142 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         long long idx = base + r * kRadixThreads + threadIdx.x;
-        bool valid = idx < n;
-        unsigned digit = valid ? ((kr[r] >> shift) & mask) : (unsigned)kMaxDigits;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[digit], (uint32_t)__popc(peers));
+        if (idx < n) atomicAdd(&sh[(kr[r] >> shift) & mask], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < nd; d += kRadixThreads) hist[(long long)d * nb + blockIdx.x] = sh[d];
 }
 
-// Stable scatter: block-local ranks in item order (rounds of 256 items, warps in order,
-// lanes in order) plus the block's scanned digit offsets.
+// Lanes of `among` whose digit equals this lane's (one ballot per digit bit; the cost does not
+// grow with the number of distinct digits in the warp).
+__device__ __forceinline__ unsigned digit_peers(unsigned digit, int dbits, unsigned among) {
+    unsigned peers = among;
+#pragma unroll
+    for (int b = 0; b < kMaxDigitBits; ++b) {
+        if (b < dbits) {
+            const bool bit = (digit >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+    }
+    return peers;
+}
+
+// Block-wide exclusive scan of v over the 256 threads (one value each); returns the prefix.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) woff += w < warp ? s_warp[w] : 0u;
+    return woff + incl - v;
+}
+
+// Stable scatter of one pass. Warp w owns the contiguous keys [w*kRadixItems*32, (w+1)*...) of
+// the block's tile (blocked arrangement: warp, then round, then lane is key order). A key's
+// rank among equal digits is its warp's running count (ballot-based peer masks per round) plus the counts of
+// the warps before it; a block-wide scan over digits gives each key its slot in a block-local
+// digit-sorted order. Keys and values are exchanged through shared memory into that order and
+// written out so that consecutive threads write consecutive positions of each digit's output
+// run (coalesced), at the block's scanned global digit offsets.
 __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const long long* n_dev, const uint32_t* __restrict__ hist_scanned, int shift,
     int dbits) {
-    long long n = *n_dev;
-    long long nb = radix_nblocks(n);
+    const long long n = *n_dev;
+    const long long nb = radix_nblocks(n);
     if ((long long)blockIdx.x >= nb) return;
-    int nd = 1 << dbits;
-    unsigned mask = (unsigned)nd - 1u;
-    __shared__ uint32_t s_base[kMaxDigits];
-    __shared__ uint32_t s_cnt[kRadixWarps][kMaxDigits];
-    __shared__ uint32_t s_off[kRadixWarps][kMaxDigits];
+    const int nd = 1 << dbits;
+    const unsigned mask = (unsigned)nd - 1u;
+    constexpr int kWarpItems = kRadixItems * 32;
+    // s_cnt (per-warp digit counts, then per-warp offsets) and later the exchanged keys/values
+    // share one buffer: the counts are dead once every key knows its local slot.
+    __shared__ uint32_t s_buf[2 * kRadixTile];
+    __shared__ uint32_t s_start[kMaxDigits];    // block-local start of each digit
+    __shared__ uint32_t s_gbase[kMaxDigits];    // global output start of each digit (this block)
+    __shared__ uint32_t s_warp[kRadixWarps];
+    uint32_t(*s_cnt)[kMaxDigits] = reinterpret_cast<uint32_t(*)[kMaxDigits]>(s_buf);
+    uint32_t* s_key = s_buf;
+    uint32_t* s_val = s_buf + kRadixTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long tile0 = (long long)blockIdx.x * kRadixTile;
+    const long long base = tile0 + (long long)warp * kWarpItems;
+    // the block's keys and values are requested first, so the global latency of the (strided)
+    // digit offsets below overlaps with them
+    uint32_t kr[kRadixItems], vr[kRadixItems], slot[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const long long idx = base + r * 32 + lane;
+        kr[r] = idx < n ? __ldcs(keys_in + idx) : 0u;
+        vr[r] = idx < n ? __ldcs(vals_in + idx) : 0u;
+    }
     for (int d = threadIdx.x; d < nd; d += kRadixThreads) {
-        s_base[d] = hist_scanned[(long long)d * nb + blockIdx.x];
+        s_gbase[d] = hist_scanned[(long long)d * nb + blockIdx.x];
 #pragma unroll
         for (int w = 0; w < kRadixWarps; ++w) s_cnt[w][d] = 0;
     }
     __syncthreads();
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long base = (long long)blockIdx.x * kRadixTile;
-    // all loads of the block are issued before any is used (one memory latency per block)
-    uint32_t kr[kRadixItems], vr[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        long long idx = base + r * kRadixThreads + threadIdx.x;
-        kr[r] = idx < n ? keys_in[idx] : 0u;
-        vr[r] = idx < n ? vals_in[idx] : 0u;
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned digit = (kr[r] >> shift) & mask;
+        const unsigned peers = digit_peers(digit, dbits, __ballot_sync(0xffffffffu, valid));
+        const uint32_t before = valid ? s_cnt[warp][digit] : 0u;
+        slot[r] = before + (uint32_t)__popc(peers & lanemask_lt());
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][digit] = before + (uint32_t)__popc(peers);
+        __syncwarp();
     }
+    __syncthreads();
+    // per digit: warp offsets within the digit and the digit's total; 2 digits per thread
+    uint32_t tot = 0;
+    for (int d = 2 * threadIdx.x; d < 2 * threadIdx.x + 2 && d < nd; ++d) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) {
+            const uint32_t c = s_cnt[w][d];
+            s_cnt[w][d] = run;
+            run += c;
+        }
+        s_start[d] = run;     // digit total for now
+        tot += run;
+    }
+    const uint32_t pre = block_exclusive_scan(tot, s_warp);
+    if (2 * threadIdx.x < nd) {
+        const uint32_t t0 = s_start[2 * threadIdx.x];
+        s_start[2 * threadIdx.x] = pre;
+        if (2 * threadIdx.x + 1 < nd) s_start[2 * threadIdx.x + 1] = pre + t0;
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        long long idx = base + r * kRadixThreads + threadIdx.x;
-        bool valid = idx < n;
-        uint32_t key = kr[r];
-        uint32_t val = vr[r];
-        unsigned digit = valid ? ((key >> shift) & mask) : (unsigned)kMaxDigits;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        unsigned rank = __popc(peers & lanemask_lt());
-        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][digit] = (uint32_t)__popc(peers);
-        __syncthreads();
-        for (int d = threadIdx.x; d < nd; d += kRadixThreads) {
-            uint32_t run = s_base[d];
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned digit = (kr[r] >> shift) & mask;
+        if (valid) slot[r] += s_start[digit] + s_cnt[warp][digit];
+    }
+    __syncthreads();    // counts are dead from here on: the buffer takes the keys and values
 #pragma unroll
-            for (int w = 0; w < kRadixWarps; ++w) {
-                uint32_t c = s_cnt[w][d];
-                s_off[w][d] = run;
-                s_cnt[w][d] = 0;
-                run += c;
-            }
-            s_base[d] = run;
+    for (int r = 0; r < kRadixItems; ++r) {
+        if (base + r * 32 + lane < n) {
+            s_key[slot[r]] = kr[r];
+            s_val[slot[r]] = vr[r];
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = s_off[warp][digit] + rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
-        }
+    }
+    __syncthreads();
+    const int cnt = (int)(n - tile0 < kRadixTile ? n - tile0 : kRadixTile);
+    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+        const uint32_t key = s_key[i];
+        const unsigned digit = (key >> shift) & mask;
+        const uint32_t pos = s_gbase[digit] + (uint32_t)i - s_start[digit];
+        keys_out[pos] = key;
+        vals_out[pos] = s_val[i];
     }
 }
 
@@ -262,49 +330,83 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const u
     if (i < n) out[i] = counts[order[i]];
 }
 
-// Emit the pairs of each record (depth order) into its scanned slot range.
-__global__ void duplicate_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
-                                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                                 const long long* total, long long capacity, uint32_t* __restrict__ pair_tile,
-                                 uint32_t* __restrict__ pair_rec, long long* counters) {
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Emit the pairs of each record (depth order) into its scanned slot range. A warp's 32
+// consecutive records own one contiguous output range: pairs that fall in its first kDupStage
+// slots are staged in shared memory and written by the whole warp in order (coalesced), the
+// rest (records with very large footprints) are written directly.
+constexpr int kDupThreads = 256;
+constexpr int kDupStage = 256;
+__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
+    const dass_splat* __restrict__ splats, long long n_rec, CamTable ct, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ offsets, const long long* total, long long capacity,
+    uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rec, long long* counters) {
+    __shared__ uint32_t s_tile[kDupThreads / 32][kDupStage];
+    __shared__ uint32_t s_rec[kDupThreads / 32][kDupStage];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long m = *total;
     if (k == 0) {
-        long long m = *total;
         counters[0] = m;
         counters[1] = m > capacity ? 1 : 0;
         counters[2] = m > capacity ? capacity : m;   // pairs actually stored (sort length)
     }
-    if (k >= n_rec) return;
-    uint32_t rec = order[k];
-    int ci = (int)(rec / ct.rec_stride);
-    const CamInfo& cam = ct.c[ci];
+    const long long k0 = k - lane;
+    if (k0 >= n_rec) return;                          // warp-uniform
+    const bool active = k < n_rec;
+    uint32_t rec = 0;
+    long long pos = 0;
+    if (active) {
+        rec = order[k];
+        pos = offsets[k];
+    }
+    // output range of the warp: [first record's offset, next warp's first offset or the total)
+    const long long wbase = __shfl_sync(0xffffffffu, pos, 0);
+    const long long wend = k0 + 32 < n_rec ? (long long)offsets[k0 + 32] : m;
     Footprint f;
     float depth;
-    if (!record_footprint(splats, rec, f, depth)) return;
-    int x0, x1, y0, y1;
-    footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
-    long long pos = offsets[k];
-    for (int y = y0; y <= y1; ++y) {
-        int r0, r1;
-        if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
-        for (int x = r0; x <= r1; ++x) {
-            if (pos < capacity) {
-                pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
-                pair_rec[pos] = rec;
+    if (active && record_footprint(splats, rec, f, depth)) {
+        const int ci = (int)(rec / ct.rec_stride);
+        const CamInfo& cam = ct.c[ci];
+        int x0, x1, y0, y1;
+        footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
+        for (int y = y0; y <= y1; ++y) {
+            int r0, r1;
+            if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
+            for (int x = r0; x <= r1; ++x) {
+                const uint32_t tile = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
+                const long long local = pos - wbase;
+                if (local < kDupStage) {
+                    s_tile[warp][local] = tile;
+                    s_rec[warp][local] = rec;
+                } else if (pos < capacity) {
+                    pair_tile[pos] = tile;
+                    pair_rec[pos] = rec;
+                }
+                ++pos;
             }
-            ++pos;
+        }
+    }
+    __syncwarp();
+    const long long staged = wend - wbase < kDupStage ? wend - wbase : kDupStage;
+    for (int i = lane; i < staged; i += 32) {
+        const long long p = wbase + i;
+        if (p < capacity) {
+            pair_tile[p] = s_tile[warp][i];
+            pair_rec[p] = s_rec[warp][i];
         }
     }
 }
 
+// [start, end) of every tile's run in the sorted pair list (grid-stride over the pairs).
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const long long* n_dev,
                                    uint32_t* __restrict__ ranges) {
-    long long n = *n_dev;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t t = tiles[i];
-    if (i == 0 || tiles[i - 1] != t) ranges[2 * (long long)t] = (uint32_t)i;
-    if (i == n - 1 || tiles[i + 1] != t) ranges[2 * (long long)t + 1] = (uint32_t)(i + 1);
+    const long long n = *n_dev;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+        const uint32_t t = tiles[i];
+        if (i == 0 || tiles[i - 1] != t) ranges[2 * (long long)t] = (uint32_t)i;
+        if (i == n - 1 || tiles[i + 1] != t) ranges[2 * (long long)t + 1] = (uint32_t)(i + 1);
+    }
 }
 
 __global__ void set_len_kernel(long long* dst, long long v) { *dst = v; }
@@ -440,8 +542,9 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
     uint32_t *k_out = s.pk0, *v_out = pair_rec, *k_tmp = s.pk1, *v_tmp = s.pv1;
     uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
     uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
-    duplicate_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, order, s.offsets, s.scal + 2, cap,
-                                                         k_start, v_start, counters); count_launch();
+    duplicate_kernel<<<div_up(n_rec, kDupThreads), kDupThreads, 0, st>>>(splats, n_rec, ct, order, s.offsets,
+                                                                         s.scal + 2, cap, k_start, v_start, counters);
+    count_launch();
     rc = check_launch("duplicate");
     if (rc) return rc;
     // 4) tile digits on the pairs
@@ -452,7 +555,9 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
         rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
     if (rc) return rc;
     // 5) tile ranges
-    tile_ranges_kernel<<<div_up(cap, 256), 256, 0, st>>>(k_out, m_dev, tile_ranges); count_launch();
+    tile_ranges_kernel<<<div_up(cap, 256) < 152 * 16 ? div_up(cap, 256) : 152 * 16, 256, 0, st>>>(k_out, m_dev,
+                                                                                                tile_ranges);
+    count_launch();
     return check_launch("tile_ranges");
 }
 
