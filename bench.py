@@ -37,18 +37,19 @@ WORKLOAD = "batched multi-view timestep: 300k Gaussians SH3 FP32, 20 cams 1352x1
 # Algorithmic FP32 work of the compositing kernels: only (pixel, Gaussian) pairs that a pixel
 # actually adds are counted (evaluating alpha for any other pair is overhead of the tiling). An
 # added pair costs 20 flop in the forward (alpha: 2 sub, 4 mul, 2 fma, o*G; T(1-alpha), alpha*T,
-# 3 colour FMAs) and 62 flop in the backward as the kernel formulates it: alpha again (12),
+# 3 colour FMAs) and 56 flop in the backward as the kernel formulates it: alpha again (12),
 # T_j = T/(1-alpha) (2), g.c (5), dL/dalpha = T_j (g.c - S) (2), S = (1-alpha) S + alpha g.c (3),
-# dpow (1), dL/du, dL/dv (10), the 3 conic gradient sums (9), dL/do (2), weight and 3 colour
-# gradients (7), 9 adds of the per-Gaussian reduction.
+# dpow (1), the sums of dpow dx and dpow dy (4; dL/du, dL/dv apply the Gaussian's conic to them once
+# per Gaussian), the 3 conic gradient sums (9), dL/do (2), weight and 3 colour gradients (7),
+# 9 adds of the per-Gaussian reduction.
 FLOP_FWD_ADD = 20
-FLOP_BWD_ADD = 62
+FLOP_BWD_ADD = 56
 # Backward of a pair whose Gaussian only needs dL/dmean2D (static in the shift stage): the same
-# terms up to dL/du, dL/dv (36) and 2 reduction adds = 37 flop.
-FLOP_BWD_MEAN_ADD = 37
+# terms up to the dpow dx, dpow dy sums (29) and 2 reduction adds = 31 flop.
+FLOP_BWD_MEAN_ADD = 31
 # DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture scaled to 20
 # cameras, profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
-RENDER_BWD_TRAFFIC = 8.81e8
+RENDER_BWD_TRAFFIC = None
 
 
 def parse():

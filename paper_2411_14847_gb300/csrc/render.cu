@@ -39,7 +39,7 @@ int allow_smem(const void* kernel, int bytes) {
 // of the per-pixel math is stored twice, so one shared load yields the operand pair of the
 // packed arithmetic without register moves:
 //   P0 = (-u, -u, -v, -v)     P1 = (a', a', b2', b2')     P2 = (c', c', o, o)
-//   P3 = (r, r, g, g)         P4 = (blue, blue, a, a)     P5 = (b, b, c, c)   (backward only)
+//   P3 = (r, r, g, g)         P4 = (blue, blue, a, a)
 // with a' = a kNegHalfLog2e, b2' = 2 b kNegHalfLog2e, c' = c kNegHalfLog2e (see splat_gauss);
 // F = (a, b, c, k2) is the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
 template <int NG, int BATCH>
@@ -56,7 +56,6 @@ __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splat
     sP[2][i] = make_float4(cp, cp, s1.y, s1.y);
     sP[3][i] = make_float4(s1.z, s1.z, s1.w, s1.w);
     sP[4][i] = make_float4(bl, bl, s0.z, s0.z);
-    if constexpr (NG > 5) sP[5][i] = make_float4(s0.w, s0.w, s1.x, s1.x);
     sF[i] = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
 }
 
@@ -342,8 +341,10 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
     gp[2 * NT] = g2;
 }
 
-// Reverse step of staged entry P0..P5 (list position pos) for both pixels of the pair; adds the
-// entry's gradient contributions: vm[0..1] (packed, both pixels) dL/d(u, v); if FULL also vf[0..2]
+// Reverse step of staged entry P0..P4 (list position pos) for both pixels of the pair; adds the
+// entry's gradient contributions: vm[0..1] (packed, both pixels) the sums of dx and dy times
+// dL/d(power) -- dL/d(u, v) = (a X + b Y, b X + c Y) of those sums X, Y, applied once per
+// Gaussian after the reduction since the conic is the Gaussian's; if FULL also vf[0..2]
 // the sums of dx^2, dx dy, dy^2 times dL/d(power) (dL/d(a, b, c) after scaling by -1/2, -1, -1/2),
 // vf[3] dL/do and vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
 // 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. Returns
@@ -351,7 +352,7 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 template <bool FULL, int NT>
 __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, const float4 P0,
                                               const float4 P1, const float4 P2, const float4 P3, const float4 P4,
-                                              const float4 P5, float2* vm, float2* vf) {
+                                              float2* vm, float2* vf) {
     bool val0 = pos <= p.last0, val1 = pos <= p.last1;
     if (!(val0 || val1)) return false;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
@@ -372,9 +373,8 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     // the clamp alpha = 0.99 has zero derivative
     const bool cm0 = val0 && oG.x < kAlphaMax, cm1 = val1 && oG.y < kAlphaMax;
     const float2 dpow = __fmul2_rn(dLda, make_float2(cm0 ? alpha.x : 0.f, cm1 ? alpha.y : 0.f));
-    const float2 Fa = hi2(P4), Fb = lo2(P5), Fc = hi2(P5);
-    vm[0] = __ffma2_rn(dpow, __ffma2_rn(Fa, dx, __fmul2_rn(Fb, dy)), vm[0]);
-    vm[1] = __ffma2_rn(dpow, __ffma2_rn(Fc, dy, __fmul2_rn(Fb, dx)), vm[1]);
+    vm[0] = __ffma2_rn(dpow, dx, vm[0]);
+    vm[1] = __ffma2_rn(dpow, dy, vm[1]);
     if (FULL) {
         vf[0] = __ffma2_rn(__fmul2_rn(dx, dx), dpow, vf[0]);
         vf[1] = __ffma2_rn(__fmul2_rn(dx, dy), dpow, vf[1]);
@@ -391,8 +391,8 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
 // Dynamic shared-memory layout of the backward CTA (byte offsets; every part 16-byte aligned).
 template <int BATCH, int NT, int NP>
 struct BwdSmem {
-    static constexpr int kP = 0;                                  // float4 [6][BATCH] staged splats
-    static constexpr int kF = kP + 6 * BATCH * 16;                // float4 [BATCH] footprints
+    static constexpr int kP = 0;                                  // float4 [5][BATCH] staged splats
+    static constexpr int kF = kP + 5 * BATCH * 16;                // float4 [BATCH] footprints
     static constexpr int kGp = kF + BATCH * 16;                   // float2 [NP][3][NT] dL/dC of the lanes' pixels
     static constexpr int kG = kGp + NP * 3 * NT * 8;              // float [BATCH][9] block-reduced gradients
     static constexpr int kRec = kG + ((BATCH * 9 * 4 + 15) / 16) * 16;   // uint32 [BATCH] record indices
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
     static_assert(BH <= CT && PPL % 2 == 0, "warp block taller than the CTA tile, or odd pixels per lane");
     using L = BwdSmem<BATCH, NT, NP>;
     extern __shared__ __align__(16) unsigned char smem[];
-    auto& sP = *reinterpret_cast<float4(*)[6][BATCH]>(smem + L::kP);
+    auto& sP = *reinterpret_cast<float4(*)[5][BATCH]>(smem + L::kP);
     auto& sF = *reinterpret_cast<float4(*)[BATCH]>(smem + L::kF);
     float2* sGp = reinterpret_cast<float2*>(smem + L::kGp);        // [NP][3][NT] upstream gradients
     auto& sG = *reinterpret_cast<float(*)[BATCH][9]>(smem + L::kG);
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
             const uint32_t rec = pair_rec[lo + i];
             sRec[i] = rec;
             sFull[i] = full_grad ? full_grad[rec % stride] : (uint8_t)1;
-            stage_splat<6, BATCH>(splats, rec, i, sP, sF);
+            stage_splat<5, BATCH>(splats, rec, i, sP, sF);
 #pragma unroll
             for (int k = 0; k < 9; ++k) sG[i][k] = 0.f;
         }
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
         for (int t = nl - 1; t >= 0; --t) {
             const int j = sList[warp][t];
             const int pos = (int)(lo + j);
-            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j], P5 = sP[5][j];
+            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             bool contrib = false;
             float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -489,12 +489,18 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
                     contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
-                                                       P5, vm, vf);
+                                                       vm, vf);
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     float r[8] = {vm[0].x + vm[0].y, vm[1].x + vm[1].y, vf[0].x + vf[0].y, vf[1].x + vf[1].y,
                                   vf[2].x + vf[2].y, vf[3].x + vf[3].y, vf[4].x + vf[4].y, vf[5].x + vf[5].y};
-                    const float s = warp_reduce8(r, lane);
+                    float s = warp_reduce8(r, lane);
                     const float e = warp_sum(vf[6].x + vf[6].y);
+                    // lane 0 holds X (index 0), lane 4 holds Y (index 1): dL/du = a X + b Y, dL/dv = b X + c Y
+                    const float other = __shfl_xor_sync(0xffffffffu, s, 4);
+                    if (gidx < 2) {
+                        const float4 F = sF[j];
+                        s = gidx == 0 ? F.x * s + F.y * other : F.y * other + F.z * s;
+                    }
                     if ((lane & 3) == 0) atomicAdd(&sG[j][gidx], s * gscale);
                     if (lane == 1) atomicAdd(&sG[j][8], e);
                 }
@@ -502,10 +508,16 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
                     contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
-                                                        P5, vm, nullptr);
+                                                        vm, nullptr);
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                    if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
+                    float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
+                    // lane 0 holds X, lane 16 holds Y: dL/du = a X + b Y, dL/dv = b X + c Y
+                    const float other = __shfl_xor_sync(0xffffffffu, r, 16);
+                    if ((lane & 15) == 0) {
+                        const float4 F = sF[j];
+                        r = lane == 0 ? F.x * r + F.y * other : F.y * other + F.z * r;
+                        atomicAdd(&sG[j][lane >> 4], r);
+                    }
                 }
             }
         }
