@@ -159,8 +159,7 @@ __device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 dx, co
     p.C0 = __ffma2_rn(lo2(P3), w, p.C0);
     p.C1 = __ffma2_rn(hi2(P3), w, p.C1);
     p.C2 = __ffma2_rn(blue, w, p.C2);
-    p.T.x = ok0 ? test.x : p.T.x;
-    p.T.y = ok1 ? test.y : p.T.y;
+    p.T = __fmul2_rn(p.T, one_minus2(alpha));   // = test where the pixel blends, T where alpha = 0
     p.last0 = ok0 ? pos : p.last0;
     p.last1 = ok1 ? pos : p.last1;
 }
@@ -232,6 +231,7 @@ __global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat
         __syncthreads();
         if (__all_sync(0xffffffffu, p.done0 && p.done1)) continue;
         const int nl = warp_compact<8, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
+#pragma unroll 8
         for (int t = 0; t < nl; ++t) {
             if (p.done0 && p.done1) break;
             const int j = sList[warp][t];
