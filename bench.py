@@ -28,6 +28,17 @@ import time
 
 import numpy as np
 
+# Algorithmic bytes of the HBM-bound stages. bin_sort per record: count pass 48 B read + 12 B
+# written, 4 depth-digit passes x 20 B (histogram read 4, scatter read 8 + write 8), pair-count
+# gather 12 B, scan 12 B, duplication reads 56 B (order, offset, record) = 220 B; per pair:
+# duplication writes 8 B, 2 tile-digit passes x 20 B, ranges 4 B = 52 B. loss per pixel-channel:
+# SSIM forward reads image and target (8 B) and writes 3 maps (12 B), backward reads the maps,
+# image and target (20 B) and writes dL/dimage (4 B) = 44 B. preprocess: the Gaussian's
+# parameters once + a 48-byte record per (camera, Gaussian).
+SORT_REC_BYTES = 220
+SORT_PAIR_BYTES = 52
+LOSS_PIX_BYTES = 44
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -52,6 +63,15 @@ FLOP_BWD_MEAN_ADD = 31
 RENDER_BWD_TRAFFIC = None
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this GPU type (MEASURED_PEAKS.json beside this file), else None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -69,7 +89,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--render-reps", type=int, default=50)
     ap.add_argument("--cpu-pixels", type=int, default=384)
-    ap.add_argument("--serve-rates", default="500,1000", help="Poisson request rates (req/s) of the serving run")
+    ap.add_argument("--serve-rates", default="200,500,1000,2000",
+                    help="Poisson request rates (req/s) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -402,13 +423,26 @@ def main():
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)",
                 "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
+    # HBM-bound stages against the measured copy bandwidth (algorithmic bytes, see SORT_REC_BYTES etc.)
+    hbm_peak = measured_hbm_gbs()
+    n_rec = sfr.n * len(cams)
+    deg_bytes = 4 * (3 + 3 + 4 + 1 + 3 * stage.g["sh"].shape[1])
+    n_px = sum(c.width * c.height for c in cams)
+    hbm = {}
+    for name, nbytes, ms_ in (("bin_sort", SORT_REC_BYTES * n_rec + SORT_PAIR_BYTES * n_pairs, sort_ms),
+                              ("loss", LOSS_PIX_BYTES * 3 * n_px, loss_ms),
+                              ("preprocess", deg_bytes * sfr.n + 48 * n_rec, pre_ms)):
+        gbs = nbytes / (ms_ * 1e-3) / 1e9
+        hbm[name] = {"bytes": int(nbytes), "ms": round(ms_, 3), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / hbm_peak, 4) if hbm_peak else None}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
                "preprocess_ms": round(pre_ms, 3), "loss_ms": round(loss_ms, 3),
                "preprocess_bwd_dyn_ms": round(pbwd_ms, 3), "densify_stats_ms": round(stats_ms, 3),
                "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
                "pairs_evaluated_fwd": n_eval, "pairs_added": n_add, "pairs_added_dynamic": n_add_dyn,
                "list_prefix_bwd": n_bwd,
-               "bin_sort_bytes_per_pair": None}
+               "bin_sort_bytes_per_pair": round(hbm["bin_sort"]["bytes"] / max(1, n_pairs), 1),
+               "hbm": hbm, "hbm_peak_gbs": hbm_peak}
 
     # ---------------- plain form (one launch per camera, no graph) vs batched, per iteration
     plain_st = ShiftStage(ts.view(), cams, targets, dyn_t, off_t.clone(), tile=tile, batch=batch, lambda_dssim=0.2)
@@ -427,6 +461,24 @@ def main():
     plain = {"ms_per_iter": round(plain_ms, 3), "batched_ms_per_iter": round(batched_ms, 3),
              "s_per_timestep": round(plain_ms * 1e-3 * args.iters + overhead_s, 4), "extrapolated": True,
              "speedup_batched": round(plain_ms / batched_ms, 3)}
+
+    # ---------------- selective-inheritance stage (Sec. 3.2): s1 = 20 iterations learning the mask of the
+    # var rows the timesteps above spawned, on the final G_t against the last targets (graph-replayed)
+    from paper_2411_14847_gb300.timestep import InheritStage
+    inh = None
+    isv = ts.is_var[ts.cur][:ts.n]
+    if int(isv.sum()) > 0:
+        ist = InheritStage(ts.view(), isv, cams, targets, tile=tile, batch=batch, lambda_dssim=0.2)
+        ist.run(2)                                 # eager iteration + capture
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ea.record()
+        ist.run(20)
+        eb.record()
+        torch.cuda.synchronize()
+        inh = {"iters": 20, "ms": round(ea.elapsed_time(eb), 3), "ms_per_iter": round(ea.elapsed_time(eb) / 20, 3),
+               "var_rows": ist.n_var, "kept": int(((ist.m[:ts.n] > 0) & (isv > 0)).sum())}
+        del ist
 
     # ---------------- render latency: one novel 1352x1014 view, forward only, p50/p99
     rfr = raster.Frame(cams[:1], ts.n, tile=tile, batch=batch)
@@ -493,7 +545,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
-                "plain": plain, "render_latency": {"single_view": render, "under_load": serve},
+                "plain": plain, "inherit_stage": inh, "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "cpu_baseline": cpu}
         print(json.dumps(line))

@@ -237,7 +237,30 @@ int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, const floa
                         float* d_means, float* d_log_scales, float* d_quats,
                         float* d_opacity_logit, float* d_sh, void* stream);
 
+/* dL/dkeep of the inheritance mask (Sec. 3.2, Eq. 1: the mask multiplies the activated opacity
+ * and scale, so dL/dkeep = o dL/do_r + sum_j s_j dL/ds_r,j with o = sigmoid(logit), s_j =
+ * exp(log_scale_j)), summed over cameras, at the mask `keep` the splats were rendered with.
+ * Same inputs and row selection as dass_preprocess_bwd; d_keep is [n_rows] (rows given) or [n].
+ * A row rendered with keep = 0 has no footprint and gets 0. */
+int dass_keep_grad(int64_t n, int sh_degree, const float* means, const float* log_scales,
+                   const float* quats, const float* opacity_logit, const float* sh,
+                   const uint8_t* keep, const dass_camera* cams /* host */, int n_cams,
+                   const dass_splat* splats, const dass_splat_grad* splat_grads,
+                   const int32_t* rows, int64_t n_rows, float* d_keep, void* stream);
+
 /* ------------------------------------------------------------------ DASS stages */
+
+/* Rendering mask of the selective-inheritance stage (Sec. 3.2, Eq. 1): keep[g] =
+ * Quant(sigmoid(m[g])) = [m[g] > 0] for var rows (is_var[g] != 0), 1 for base rows. */
+int dass_inherit_keep(int64_t n, const uint8_t* is_var, const float* m, uint8_t* keep, void* stream);
+
+/* Straight-through gradient of the inheritance logits (App. B.2 STE applied to the loss of
+ * Eq. 2): for r < n_rows, g = rows[r] (rows == NULL: g = r),
+ * grad[g] = (d_keep[r] + lambda_inher) * sigmoid(m[g]) (1 - sigmoid(m[g])), where d_keep[r] is
+ * dL/dkeep from dass_keep_grad. loss (optional, device double) accumulates the mask loss
+ * lambda_inher * sum_r sigmoid(m[rows[r]]). grad rows outside `rows` are not written. */
+int dass_inherit_mask_grad(int64_t n_rows, const int32_t* rows, const float* m, const float* d_keep,
+                           float lambda_inher, float* grad, double* loss, void* stream);
 
 /* Dynamics-aware shift (Sec. 3.3), dynamic rows only: for d < n_dyn with n = dyn_idx[d],
  * out_means[n] = means[n] + dmu_d and out_quats[n] = norm(quats[n]) x norm(sigma_d)

@@ -120,3 +120,47 @@ def loss_grads(arrays, cams, sh_degree, targets, lam, dyn_idx=None, offsets=None
     res["images"] = images
     res["dimages"] = dimg
     return res
+
+
+# ------------------------------------------------------------ Sec. 3.2: learned inheritance mask
+
+def ste_keep(m, is_var):
+    """Rendering mask of Eq. 1 under the straight-through estimator of App. B.2.
+
+    On var rows m_op = detach(Quant(sigmoid(m)) - sigmoid(m)) + sigmoid(m): its value is
+    Quant(sigmoid(m)) (read as [sigmoid(m) > 1/2], i.e. m > 0) and its derivative is that of
+    sigmoid(m). Base rows are always rendered (mask 1)."""
+    m = t64(m)
+    sg = torch.sigmoid(m)
+    q = (m > 0).to(DT)
+    m_op = (q - sg).detach() + sg
+    isv = torch.as_tensor(np.asarray(is_var, dtype=bool))
+    return torch.where(isv, m_op, torch.ones_like(m_op))
+
+
+def inherit_mask_grads(arrays, cams, sh_degree, targets, lam, m, is_var, lam_inher, bg=None):
+    """Loss of Eq. 2 and its gradients for the selective-inheritance stage (Sec. 3.2, App. B.2).
+
+    L = (1 - lam) L1 + lam D-SSIM (Eq. 3 over all cameras) + lam_inher * sum_var sigmoid(m).
+    The render uses o_r = m_op o and s_r = m_op s (Eq. 1) with m_op from ste_keep. Returns
+    loss, d_keep (dL_fidelity/d(mask value) per Gaussian, the derivative of the fidelity loss
+    w.r.t. the multiplier of Eq. 1 at its current value) and dm (dL/dm through the STE,
+    mask loss included; 0 on base rows)."""
+    m_leaf = t64(np.asarray(m, dtype=np.float64)).clone().requires_grad_(True)
+    keep = ste_keep(m_leaf, is_var)
+    keep.retain_grad()
+    imgs = render(arrays, cams, sh_degree, keep=keep.detach(), bg=bg)
+    images = [r["image"] for r in imgs]
+    fid, dimg = loss_and_image_grad(images, [t64(t) for t in targets], lam)
+    pg = []
+    for cam, gi in zip(cams, dimg):
+        px, py = comp.pixel_grid(cam.width, cam.height)
+        pg.append((px, py, gi.reshape(3, -1).T))
+    image_vjp(arrays, cams, sh_degree, pg, keep=keep, bg=bg)
+    d_keep = keep.grad.detach().clone() if keep.grad is not None else torch.zeros_like(keep)
+    isv = torch.as_tensor(np.asarray(is_var, dtype=bool))
+    reg = lam_inher * torch.sigmoid(m_leaf[isv]).sum()
+    reg.backward()
+    dm = m_leaf.grad.detach().clone()
+    return {"loss": float(fid) + float(reg.detach()), "fidelity": float(fid), "d_keep": d_keep, "dm": dm,
+            "images": images}

@@ -19,7 +19,7 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
                           const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                           const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
                           unsigned flags, int accumulate, float* d_means, float* d_log_scales, float* d_quats,
-                          float* d_opacity_logit, float* d_sh, cudaStream_t st);
+                          float* d_opacity_logit, float* d_sh, float* d_keep, cudaStream_t st);
 int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
                          float* accum, int* count, cudaStream_t st);
 size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
@@ -47,6 +47,9 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
                    const float* sh, const uint8_t* is_var, const float* m, int erase, float* om, float* ols, float* oq,
                    float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
                    cudaStream_t st);
+int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st);
+int inherit_mask_grad_launch(long long n_rows, const int* rows, const float* m, const float* d_keep, float lambda,
+                             float* grad, double* loss, cudaStream_t st);
 size_t error_pass_workspace_bytes(const CamTable& ct);
 int error_pass_launch(const float* img, const float* tgt, const CamTable& ct, double quantile, long long n,
                       const float* means, const uint8_t* is_var, float* error_map, float* gamma, uint8_t* s_err,
@@ -277,7 +280,24 @@ DASS_API int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, c
     if (!make_cam_table(cams, n_cams, 8, n, &ct)) return DASS_ERR_INVALID_ARG;
     return preprocess_bwd_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, keep, ct, splats,
                                  splat_grads, rows, nr, grad_flags, accumulate, d_means, d_log_scales, d_quats,
-                                 d_opacity_logit, d_sh, as_stream(stream));
+                                 d_opacity_logit, d_sh, nullptr, as_stream(stream));
+}
+
+DASS_API int dass_keep_grad(int64_t n, int sh_degree, const float* means, const float* log_scales, const float* quats,
+                            const float* opacity_logit, const float* sh, const uint8_t* keep,
+                            const dass_camera* cams, int n_cams, const dass_splat* splats,
+                            const dass_splat_grad* splat_grads, const int32_t* rows, int64_t n_rows, float* d_keep,
+                            void* stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3) return DASS_ERR_INVALID_ARG;
+    long long nr = rows ? n_rows : n;
+    if (nr < 0) return DASS_ERR_INVALID_ARG;
+    if (nr > 0 && (!means || !log_scales || !quats || !opacity_logit || !sh || !splats || !splat_grads || !d_keep))
+        return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 8, n, &ct)) return DASS_ERR_INVALID_ARG;
+    return preprocess_bwd_launch(n, sh_degree, means, log_scales, quats, opacity_logit, sh, keep, ct, splats,
+                                 splat_grads, rows, nr, 0u, 0, nullptr, nullptr, nullptr, nullptr, nullptr, d_keep,
+                                 as_stream(stream));
 }
 
 DASS_API int dass_densify_stats(int64_t n, const dass_splat* splats, const dass_splat_grad* splat_grads,
@@ -336,6 +356,17 @@ DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
     if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     *bytes = inherit_workspace_bytes(n);
     return DASS_OK;
+}
+
+DASS_API int dass_inherit_keep(int64_t n, const uint8_t* is_var, const float* m, uint8_t* keep, void* stream) {
+    if (n < 0 || (n > 0 && (!is_var || !m || !keep))) return DASS_ERR_INVALID_ARG;
+    return inherit_keep_launch(n, is_var, m, keep, as_stream(stream));
+}
+
+DASS_API int dass_inherit_mask_grad(int64_t n_rows, const int32_t* rows, const float* m, const float* d_keep,
+                                    float lambda_inher, float* grad, double* loss, void* stream) {
+    if (n_rows < 0 || (n_rows > 0 && (!m || !d_keep || !grad))) return DASS_ERR_INVALID_ARG;
+    return inherit_mask_grad_launch(n_rows, rows, m, d_keep, lambda_inher, grad, loss, as_stream(stream));
 }
 
 DASS_API int dass_inherit(int64_t n, int sh_degree, const float* means, const float* log_scales, const float* quats,
@@ -455,7 +486,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
         rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
                                    d->opacity_logit, d->sh, nullptr, ct, d->splats, d->splat_grads, d->dyn_idx,
                                    d->n_dyn, DASS_GRAD_MEANS | DASS_GRAD_QUATS, 0, d->d_means_dyn, nullptr,
-                                   d->d_quats_dyn, nullptr, nullptr, st);
+                                   d->d_quats_dyn, nullptr, nullptr, nullptr, st);
         if (rc) return rc;
         if (d->stat_accum && d->stat_count) {
             rc = densify_stats_launch(d->n, ct, d->splats, d->splat_grads, d->stat_accum, d->stat_count, st);
@@ -488,7 +519,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
             rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
                                        d->opacity_logit, d->sh, nullptr, ct, sp, gs, d->dyn_idx, d->n_dyn,
                                        DASS_GRAD_MEANS | DASS_GRAD_QUATS, c > 0, d->d_means_dyn, nullptr,
-                                       d->d_quats_dyn, nullptr, nullptr, st);
+                                       d->d_quats_dyn, nullptr, nullptr, nullptr, st);
             if (rc) return rc;
             if (d->stat_accum && d->stat_count) {
                 rc = densify_stats_launch(d->n, ct, sp, gs, d->stat_accum, d->stat_count, st);

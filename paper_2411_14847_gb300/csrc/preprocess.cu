@@ -200,12 +200,16 @@ __global__ void __launch_bounds__(128) preprocess_scenes_kernel(int deg, SceneTa
     write_record<K>(cam, ct.tile, deg, p, o, Sig, coef, rec);
 }
 
+// Internal gradient flag (beyond the public DASS_GRAD_* set): dL/dkeep of the inheritance mask.
+constexpr unsigned kGradKeep = 1u << 8;
+
 struct Grads {
     float* d_means;
     float* d_log_scales;
     float* d_quats;
     float* d_opacity_logit;
     float* d_sh;
+    float* d_keep;
 };
 
 template <int K>
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
     Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
     const bool want_sh = (flags & DASS_GRAD_SH) && out.d_sh;
-    const bool want_geo = (flags & (DASS_GRAD_MEANS | DASS_GRAD_SCALES | DASS_GRAD_QUATS)) != 0;
+    const bool want_geo = (flags & (DASS_GRAD_MEANS | DASS_GRAD_SCALES | DASS_GRAD_QUATS | kGradKeep)) != 0;
     float coef[3 * K];
     load_sh<K>(prm.sh, g, coef);
     float dcoef[3 * K];
@@ -376,7 +380,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
 #pragma unroll
         for (int i = 0; i < 3; ++i) d[i] = accumulate ? d[i] + dp[i] : dp[i];
     }
-    if (flags & (DASS_GRAD_SCALES | DASS_GRAD_QUATS)) {
+    // dL/dkeep of the inheritance mask (Eq. 1: o_r = keep o, s_r = keep s) at the current keep
+    float d_keep = d_o * o_raw;
+    if (flags & (DASS_GRAD_SCALES | DASS_GRAD_QUATS | kGradKeep)) {
         // Sigma = M M^T: dM = 2 dSigmaFull M with dSigmaFull the symmetric matrix whose
         // off-diagonals are half the accumulated (once-counted) values.
         float D[9] = {dSig[0], 0.5f * dSig[1], 0.5f * dSig[2], 0.5f * dSig[1], dSig[3], 0.5f * dSig[4],
@@ -395,6 +401,11 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
                 float v = ds * s[j];   // s already includes the keep mask: d s_r / d log s = s_r
                 d[j] = accumulate ? d[j] + v : v;
             }
+        }
+        if (flags & kGradKeep) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                d_keep += (dM[j] * R[j] + dM[3 + j] * R[3 + j] + dM[6 + j] * R[6 + j]) * __expf(ls[j]);
         }
         if (flags & DASS_GRAD_QUATS && out.d_quats) {
             float G[9];
@@ -419,6 +430,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
             for (int i = 0; i < 4; ++i) d[i] = accumulate ? d[i] + v[i] : v[i];
         }
     }
+    if ((flags & kGradKeep) && out.d_keep) out.d_keep[orow] = accumulate ? out.d_keep[orow] + d_keep : d_keep;
 }
 
 __global__ void densify_stats_kernel(long long n, CamTable ct, const dass_splat* __restrict__ splats,
@@ -510,9 +522,10 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
                           const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                           const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
                           unsigned flags, int accumulate, float* d_means, float* d_log_scales, float* d_quats,
-                          float* d_opacity_logit, float* d_sh, cudaStream_t st) {
+                          float* d_opacity_logit, float* d_sh, float* d_keep, cudaStream_t st) {
     Params prm{means, log_scales, quats, opacity_logit, sh, keep};
-    Grads gr{d_means, d_log_scales, d_quats, d_opacity_logit, d_sh};
+    Grads gr{d_means, d_log_scales, d_quats, d_opacity_logit, d_sh, d_keep};
+    if (d_keep) flags |= kGradKeep;
     if (n_rows <= 0) return DASS_OK;
     switch (deg) {
         case 0: return launch_pre_bwd<1>(n, deg, prm, ct, splats, gsp, rows, n_rows, flags, accumulate, gr, st);

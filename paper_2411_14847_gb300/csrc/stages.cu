@@ -110,6 +110,36 @@ __global__ void inherit_flags_kernel(long long n, const uint8_t* __restrict__ is
     fv[i] = (var && !erase && (m == nullptr || m[i] > 0.f)) ? 1u : 0u;
 }
 
+// Rendering mask of the inheritance stage: keep = Quant(sigmoid(m)) = [m > 0] on var rows, 1 on
+// base rows (Eq. 1).
+__global__ void inherit_keep_kernel(long long n, const uint8_t* __restrict__ is_var, const float* __restrict__ m,
+                                    uint8_t* __restrict__ keep) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keep[i] = (is_var[i] == 0 || m[i] > 0.f) ? 1 : 0;
+}
+
+// Straight-through gradient of the inheritance logits (App. B.2 STE on Eq. 2): the rendering
+// uses m_op = Quant(sigmoid(m)) whose surrogate derivative is sigmoid'(m), and the mask loss
+// lambda sum sigmoid(m) adds lambda sigmoid'(m); grad[rows[r]] = (d_keep[r] + lambda) s (1 - s).
+// loss (optional) accumulates lambda * sum sigmoid(m) over the rows.
+__global__ void inherit_mask_grad_kernel(long long n_rows, const int* __restrict__ rows, const float* __restrict__ m,
+                                         const float* __restrict__ d_keep, float lambda, float* __restrict__ grad,
+                                         double* loss) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float reg = 0.f;
+    if (r < n_rows) {
+        const long long g = rows ? (long long)rows[r] : r;
+        const float sg = 1.f / (1.f + __expf(-m[g]));
+        grad[g] = (d_keep[r] + lambda) * sg * (1.f - sg);
+        reg = lambda * sg;
+    }
+    if (loss) {
+        for (int o = 16; o > 0; o >>= 1) reg += __shfl_xor_sync(0xffffffffu, reg, o);
+        if ((threadIdx.x & 31) == 0 && reg != 0.f) atomicAdd(loss, (double)reg);
+    }
+}
+
 __global__ void inherit_scatter_kernel(long long n, int K3, const uint32_t* __restrict__ fb,
                                        const uint32_t* __restrict__ fv, const uint32_t* __restrict__ sb,
                                        const uint32_t* __restrict__ sv, const long long* __restrict__ totals,
@@ -379,6 +409,20 @@ size_t inherit_workspace_bytes(long long n) {
     c.take<long long>(4);
     c.take<unsigned long long>((long long)(scan_partials_bytes(n) / 8 + 1));
     return c.used;
+}
+
+int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st) {
+    if (n <= 0) return DASS_OK;
+    inherit_keep_kernel<<<div_up(n, 256), 256, 0, st>>>(n, is_var, m, keep); count_launch();
+    return check_launch("inherit_keep_kernel");
+}
+
+int inherit_mask_grad_launch(long long n_rows, const int* rows, const float* m, const float* d_keep, float lambda,
+                             float* grad, double* loss, cudaStream_t st) {
+    if (n_rows <= 0) return DASS_OK;
+    inherit_mask_grad_kernel<<<div_up(n_rows, 256), 256, 0, st>>>(n_rows, rows, m, d_keep, lambda, grad, loss);
+    count_launch();
+    return check_launch("inherit_mask_grad_kernel");
 }
 
 int inherit_launch(long long n, int deg, const float* means, const float* ls, const float* quats, const float* logit,

@@ -89,7 +89,11 @@ _SIGS = {
                                   _P, _P]),
     "dass_preprocess_bwd": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P,
                                       C.c_int64, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dass_keep_grad": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int64,
+                                 _P, _P]),
     "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
+    "dass_inherit_keep": (C.c_int, [C.c_int64, _P, _P, _P, _P]),
+    "dass_inherit_mask_grad": (C.c_int, [C.c_int64, _P, _P, _P, C.c_float, _P, _P, _P]),
     "dass_shift": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "dass_shift_bwd": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "dass_adam": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_float, C.c_float,
@@ -266,6 +270,27 @@ def dass_preprocess_bwd(g, cams, splats, splat_grads, out, grad_flags=GRAD_ALL, 
           _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, grad_flags, int(bool(accumulate)),
           _ptr(out.get("d_means"), F32), _ptr(out.get("d_log_scales"), F32), _ptr(out.get("d_quats"), F32),
           _ptr(out.get("d_opacity_logit"), F32), _ptr(out.get("d_sh"), F32), _stream(stream))
+
+
+def dass_keep_grad(g, cams, splats, splat_grads, d_keep, keep=None, rows=None, stream=None):
+    """dL/dkeep of the inheritance mask per row (compact [n_rows] when rows is given)."""
+    n = g["means"].shape[0]
+    deg = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    arr = cameras(cams)
+    n_rows = rows.numel() if rows is not None else n
+    _call("dass_keep_grad", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
+          _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), _ptr(splats, F32),
+          _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, _ptr(d_keep, F32), _stream(stream))
+
+
+def dass_inherit_keep(is_var, m, keep, stream=None):
+    _call("dass_inherit_keep", is_var.numel(), _ptr(is_var, U8), _ptr(m, F32), _ptr(keep, U8), _stream(stream))
+
+
+def dass_inherit_mask_grad(rows, m, d_keep, lambda_inher, grad, loss=None, stream=None):
+    n_rows = rows.numel() if rows is not None else m.numel()
+    _call("dass_inherit_mask_grad", n_rows, _ptr(rows, I32), _ptr(m, F32), _ptr(d_keep, F32), float(lambda_inher),
+          _ptr(grad, F32), _ptr(loss, F64), _stream(stream))
 
 
 def dass_densify_stats(n, splats, splat_grads, cams, accum, count, stream=None):

@@ -1,7 +1,9 @@
 """Per-timestep driver of the streaming reconstruction on top of libdass.
 
 A timestep (Sec. 3.1) turns G_{t-1} into G_t with the multi-view images of timestep t:
-  1. selective inheritance copy (Sec. 3.2)                  -> dass_inherit
+  1. selective inheritance (Sec. 3.2): s1 iterations learning the var-row mask (InheritStage:
+     dass_inherit_keep, dass_keep_grad, dass_inherit_mask_grad, dass_adam), then the copy
+                                                           -> dass_inherit
   2. dynamics-aware shift stage, n_shift iterations (Sec. 3.3) -> dass_step (graph replay)
   3. error pass on the last shift render, Eq. 4 selection and spawn (Sec. 3.4)
                                                            -> dass_error_pass, dass_densify_select, dass_spawn
@@ -125,13 +127,105 @@ class ShiftStage:
         raise D.DassError("dass_step", D.ERR_CAPACITY)
 
 
+class InheritStage:
+    """Selective-inheritance stage (Sec. 3.2, App. B.2): learns one logit m per var Gaussian of
+    G_{t-1} against the images of timestep t, every other parameter fixed.
+
+    One iteration: keep = Quant(sigmoid(m)) on var rows (dass_inherit_keep) -> projection with
+    opacity and scale multiplied by keep (Eq. 1) -> bin/sort -> forward -> loss of Eq. 3 ->
+    backward (full splat gradients for var rows only) -> dL/dkeep (dass_keep_grad) -> the
+    straight-through gradient with the mask loss of Eq. 2 (dass_inherit_mask_grad) -> Adam on m.
+    The first iteration runs eagerly (it sizes the pair buffer with every var row rendered, the
+    most the stage can render since a masked row only receives the mask loss); the others replay
+    it as one captured CUDA graph.
+
+    The paper fixes neither lambda_inher, the initial logit nor the optimiser of m: m starts at
+    m0 > 0 (every var row inherited unless the stage learns otherwise) and takes Adam steps.
+    """
+
+    def __init__(self, g, is_var, cams, targets, tile=16, batch=128, lambda_dssim=0.2, lambda_inher=1e-6, m0=0.5,
+                 lr=0.05, beta1=0.9, beta2=0.999, eps=1e-15):
+        self.g = {k: g[k].contiguous() for k in PARAM_NAMES}
+        self.cams = list(cams)
+        self.n = int(self.g["means"].shape[0])
+        dev = self.g["means"].device
+        self.is_var = is_var[:self.n].contiguous()
+        self.var_rows = torch.nonzero(self.is_var).flatten().to(torch.int32).contiguous()
+        self.n_var = int(self.var_rows.numel())
+        self.targets = targets.contiguous()
+        self.lam, self.lam_inher = float(lambda_dssim), float(lambda_inher)
+        self.lr, self.betas, self.eps = float(lr), (float(beta1), float(beta2)), float(eps)
+        self.m = torch.full((max(1, self.n),), float(m0), device=dev)
+        self.keep = torch.ones(max(1, self.n), dtype=torch.uint8, device=dev)
+        self.grad = torch.zeros(max(1, self.n), device=dev)
+        self.adam_m = torch.zeros(max(1, self.n), device=dev)
+        self.adam_v = torch.zeros(max(1, self.n), device=dev)
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.d_keep = torch.zeros(max(1, self.n_var), device=dev)
+        self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
+        self.dL_dimage = torch.zeros_like(self.frame.image)
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _iteration(self, eager=False):
+        fr = self.frame
+        D.dass_inherit_keep(self.is_var, self.m, self.keep)
+        fr.project(self.g, keep=self.keep)
+        if eager:
+            fr.bin_sort()
+        else:
+            fr.bin_sort(grow=False)
+            torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
+        fr.render_fwd()
+        self.loss_buf.zero_()
+        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
+                          fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.is_var, rec_stride=self.n)
+        if self.n_var:
+            D.dass_keep_grad(self.g, self.cams, fr.splats, fr.splat_grads, self.d_keep, keep=self.keep,
+                             rows=self.var_rows)
+            D.dass_inherit_mask_grad(self.var_rows, self.m, self.d_keep, self.lam_inher, self.grad, self.loss_buf)
+            D.dass_adam(self.m.view(-1, 1), self.grad.view(-1, 1), self.adam_m.view(-1, 1), self.adam_v.view(-1, 1),
+                        self.step, [self.lr], self.betas[0], self.betas[1], self.eps, rows=self.var_rows)
+
+    @property
+    def loss(self):
+        return float(self.loss_buf.item())
+
+    def run(self, n_iters):
+        """n_iters iterations; returns the learned logits m (var rows meaningful)."""
+        if n_iters <= 0 or self.n == 0:
+            return self.m
+        replays = n_iters
+        if self.graph is None:
+            self._iteration(eager=True)
+            replays -= 1
+            if replays > 0:
+                # the pair buffer now holds the exact count with every var row rendered (+ margin)
+                m_pairs = int(self.frame.counters[0].item())
+                if self.frame.pair_capacity < m_pairs * 1.05 + 1024:
+                    self.frame._alloc_pairs(int(m_pairs * 1.1) + 1024)
+                torch.cuda.synchronize()
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self._iteration()
+        for _ in range(replays):
+            self.graph.replay()
+        if replays > 0 and int(self.overflow.item()):
+            raise D.DassError("inherit stage bin_sort", D.ERR_CAPACITY)
+        return self.m
+
+
 class Timestep:
     """One full timestep t of the streaming pipeline over resident device buffers.
 
     Scene arrays are allocated with room for `n_max` rows; `n` tracks the live count."""
 
     def __init__(self, cams, n_max, sh_degree, tile=16, batch=128, lambda_dssim=0.2, n_shift=100,
-                 quantile=0.95, tau_pos=2e-4, tau_err=1e-4, k_max=5000, erase_every=20, device="cuda"):
+                 quantile=0.95, tau_pos=2e-4, tau_err=1e-4, k_max=5000, erase_every=20, n_inherit=0,
+                 lambda_inher=1e-6, device="cuda"):
         self.cams = list(cams)
         self.n_max = int(n_max)
         self.deg = sh_degree
@@ -140,6 +234,7 @@ class Timestep:
         self.n_shift = n_shift
         self.quantile, self.tau_pos, self.tau_err, self.k_max = quantile, tau_pos, tau_err, k_max
         self.erase_every = erase_every
+        self.n_inherit, self.lambda_inher = int(n_inherit), float(lambda_inher)   # s1 of the inheritance stage
         self.device = device
         K = (sh_degree + 1) ** 2
         shapes = dict(means=(3,), log_scales=(3,), quats=(4,), opacity_logit=(), sh=(K, 3))
@@ -167,13 +262,19 @@ class Timestep:
         dev = self.device
         src, dst = self.cur, 1 - self.cur
         n = self.n
-        # 1) selective inheritance copy (Sec. 3.2)
+        # 1) selective inheritance (Sec. 3.2): learn the mask over the var rows (s1 iterations),
+        #    unless the logits are given or this timestep erases every var row (App. B.2)
+        erase = t % self.erase_every == 0
+        if inherit_logits is None and self.n_inherit > 0 and not erase and n > 0 and bool(self.is_var[src][:n].any()):
+            stage1 = InheritStage(self.view(src), self.is_var[src][:n], self.cams, targets, tile=self.tile,
+                                  batch=self.batch, lambda_dssim=self.lambda_dssim, lambda_inher=self.lambda_inher)
+            inherit_logits = stage1.run(self.n_inherit)[:n]
         m = inherit_logits if inherit_logits is not None else torch.ones(n, device=dev)
         ws = torch.empty(max(1, D.dass_inherit_workspace(n)), dtype=torch.uint8, device=dev)
         remap = torch.empty(max(1, n), dtype=torch.int32, device=dev)
         n_out = torch.zeros(1, dtype=torch.int64, device=dev)
         out = {k: v for k, v in self.bufs[dst].items()}
-        D.dass_inherit(self.view(src), self.is_var[src][:n], m[:n].contiguous(), t % self.erase_every == 0, out,
+        D.dass_inherit(self.view(src), self.is_var[src][:n], m[:n].contiguous(), erase, out,
                        self.is_var[dst], remap, n_out, ws)
         self.cur = dst
         self.n = int(n_out.item())
