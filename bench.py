@@ -60,7 +60,7 @@ FLOP_BWD_ADD = 56
 FLOP_BWD_MEAN_ADD = 31
 # DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture scaled to 20
 # cameras, profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
-RENDER_BWD_TRAFFIC = None
+RENDER_BWD_TRAFFIC = 8.80e8
 
 
 def measured_hbm_gbs():
