@@ -178,24 +178,29 @@ __device__ __forceinline__ void pix_fwd_store(float T, float C0, float C1, float
     n_last[cam.pix_base + pix] = last;
 }
 
-// One CTA per CT x CT part of a tile with CT*CT/2 threads: warp w owns the 8 x 8 block
-// (w % (CT/8), w / (CT/8)) and each lane the two pixels (x, y) and (x, y + 4) of it.
-// COUNT = true is a separate instantiation used only to measure the work of a render (pairs
-// evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false instantiations.
-template <int TILE, int BATCH, bool COUNT, int CT = TILE>
-__global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat* __restrict__ splats,
-                                                                   const uint32_t* __restrict__ pair_rec,
-                                                                   const uint32_t* __restrict__ ranges, CamTable ct,
-                                                                   float3 bg, float* __restrict__ image,
-                                                                   float* __restrict__ T_final,
-                                                                   int* __restrict__ n_last,
-                                                                   unsigned long long* __restrict__ work,
-                                                                   const uint8_t* __restrict__ full_grad,
-                                                                   long long rec_stride) {
-    constexpr int NT = CT * CT / 2;
+// One CTA per CT x CT part of a tile with CT*CT/PPL threads: warp w owns the 8 x 4*PPL block
+// (w % (CT/8), w / (CT/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, as PPL/2
+// packed pixel pairs. COUNT = true is a separate instantiation used only to measure the work of a
+// render (pairs evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false
+// instantiations.
+template <int TILE, int BATCH, bool COUNT, int CT = TILE, int PPL = 2>
+__global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_splat* __restrict__ splats,
+                                                                     const uint32_t* __restrict__ pair_rec,
+                                                                     const uint32_t* __restrict__ ranges,
+                                                                     CamTable ct, float3 bg,
+                                                                     float* __restrict__ image,
+                                                                     float* __restrict__ T_final,
+                                                                     int* __restrict__ n_last,
+                                                                     unsigned long long* __restrict__ work,
+                                                                     const uint8_t* __restrict__ full_grad,
+                                                                     long long rec_stride) {
+    constexpr int NT = CT * CT / PPL;
     constexpr int NW = NT / 32;
     constexpr int WX = CT / 8;
+    constexpr int BH = 4 * PPL;
+    constexpr int NP = PPL / 2;       // pixel pairs per lane
     constexpr int S = TILE / CT;      // CTAs per tile side
+    static_assert(BH <= CT && PPL % 2 == 0, "warp block taller than the CTA tile, or odd pixels per lane");
     __shared__ float4 sP[5][BATCH];
     __shared__ float4 sF[BATCH];
     __shared__ unsigned short sList[NW][BATCH];
@@ -206,22 +211,32 @@ __global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
     const int tx0 = (local % cam.tiles_x) * TILE + (sub % S) * CT, ty0 = (local / cam.tiles_x) * TILE + (sub / S) * CT;
-    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * 8;
+    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * BH;
     const int px = bxi + (lane & 7);
     const int py = byi + (lane >> 3);
     const float bx = (float)bxi, by = (float)byi;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const float2 fx2 = make_float2((float)px, (float)px);
-    PixFwd2 p;
-    p.fy = make_float2((float)py, (float)(py + 4));
-    p.T = make_float2(1.f, 1.f);
-    p.C0 = p.C1 = p.C2 = make_float2(0.f, 0.f);
-    p.last0 = p.last1 = -1;
-    p.done0 = !(px < cam.W && py < cam.H);
-    p.done1 = !(px < cam.W && py + 4 < cam.H);
-    p.n_eval = p.n_add = p.n_full = 0ull;
+    PixFwd2 pp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int y0 = py + 8 * k;
+        pp[k].fy = make_float2((float)y0, (float)(y0 + 4));
+        pp[k].T = make_float2(1.f, 1.f);
+        pp[k].C0 = pp[k].C1 = pp[k].C2 = make_float2(0.f, 0.f);
+        pp[k].last0 = pp[k].last1 = -1;
+        pp[k].done0 = !(px < cam.W && y0 < cam.H);
+        pp[k].done1 = !(px < cam.W && y0 + 4 < cam.H);
+        pp[k].n_eval = pp[k].n_add = pp[k].n_full = 0ull;
+    }
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) d = d && pp[k].done0 && pp[k].done1;
+        return d;
+    };
     for (uint32_t base = start; base < end; base += BATCH) {
-        if (__syncthreads_count(p.done0 && p.done1) == NT) break;
+        if (__syncthreads_count(all_done()) == NT) break;
         const int cnt = min((uint32_t)BATCH, end - base);
         for (int i = tid; i < cnt; i += NT) {
             const uint32_t rec = pair_rec[base + i];
@@ -229,29 +244,36 @@ __global__ void __launch_bounds__(CT* CT / 2) render_fwd_kernel(const dass_splat
             if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
         }
         __syncthreads();
-        if (__all_sync(0xffffffffu, p.done0 && p.done1)) continue;
-        const int nl = warp_compact<8, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
+        if (__all_sync(0xffffffffu, all_done())) continue;
+        const int nl = warp_compact<BH, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
 #pragma unroll 8
         for (int t = 0; t < nl; ++t) {
-            if (p.done0 && p.done1) break;
+            if (all_done()) break;
             const int j = sList[warp][t];
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
             const float2 blue = lo2(sP[4][j]);
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
-            pix_fwd_step2<COUNT>(p, (int)(base + j), dx, P0, P1, P2, P3, blue, full);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), dx, P0, P1, P2, P3, blue, full);
         }
     }
-    pix_fwd_store(p.T.x, p.C0.x, p.C1.x, p.C2.x, p.last0, cam, px, py, bg, image, T_final, n_last);
-    pix_fwd_store(p.T.y, p.C0.y, p.C1.y, p.C2.y, p.last1, cam, px, py + 4, bg, image, T_final, n_last);
-    if (COUNT) {
-        unsigned long long n_bwd = (p.last0 >= 0 ? (unsigned long long)(p.last0 - (int)start + 1) : 0ull) +
-                                   (p.last1 >= 0 ? (unsigned long long)(p.last1 - (int)start + 1) : 0ull);
-        atomicAdd(work + 0, p.n_eval);
-        atomicAdd(work + 1, p.n_add);
-        atomicAdd(work + 2, n_bwd);
-        atomicAdd(work + 3, (unsigned long long)((px < cam.W && py < cam.H) + (px < cam.W && py + 4 < cam.H)));
-        atomicAdd(work + 4, p.n_full);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const PixFwd2& p = pp[k];
+        const int y0 = py + 8 * k;
+        pix_fwd_store(p.T.x, p.C0.x, p.C1.x, p.C2.x, p.last0, cam, px, y0, bg, image, T_final, n_last);
+        pix_fwd_store(p.T.y, p.C0.y, p.C1.y, p.C2.y, p.last1, cam, px, y0 + 4, bg, image, T_final, n_last);
+        if (COUNT) {
+            unsigned long long n_bwd = (p.last0 >= 0 ? (unsigned long long)(p.last0 - (int)start + 1) : 0ull) +
+                                       (p.last1 >= 0 ? (unsigned long long)(p.last1 - (int)start + 1) : 0ull);
+            atomicAdd(work + 0, p.n_eval);
+            atomicAdd(work + 1, p.n_add);
+            atomicAdd(work + 2, n_bwd);
+            atomicAdd(work + 3,
+                      (unsigned long long)((px < cam.W && y0 < cam.H) + (px < cam.W && y0 + 4 < cam.H)));
+            atomicAdd(work + 4, p.n_full);
+        }
     }
 }
 
@@ -534,12 +556,15 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 3 : 1) render_bwd_ker
     }
 }
 
-// CTA side of the compositing kernels for a binning tile: a tile's list can be composited by
-// (TILE/CT)^2 independent CTAs, each covering a CT x CT part of the tile. Measured on the 300k x
-// 20-view workload: 32-pixel bins are composited fastest by 16 x 16 forward CTAs (fewer warps
-// wait at each staged batch) and by whole-tile backward CTAs.
+// CTA side and pixels per lane of the compositing kernels for a binning tile: a tile's list can
+// be composited by (TILE/CT)^2 independent CTAs, each covering a CT x CT part of the tile, and a
+// lane owns PPL pixels of a column. Measured on the 300k x 20-view workload: 32-pixel bins are
+// composited fastest by whole-tile CTAs with 4 pixels per lane (8 x 16 warp blocks) in both
+// passes; 16 x 16 forward CTAs were best with 2 pixels per lane (2.76 vs 2.69 ms).
 template <int TILE>
-constexpr int fwd_cta() { return TILE == 32 ? 16 : TILE; }
+constexpr int fwd_cta() { return TILE; }
+template <int TILE>
+constexpr int fwd_ppl() { return TILE == 32 ? 4 : 2; }
 template <int TILE>
 constexpr int bwd_cta() { return TILE; }
 
@@ -549,12 +574,13 @@ int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
                cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int CT = fwd_cta<TILE>();
+    constexpr int PPL = fwd_ppl<TILE>();
     constexpr int NB = (TILE / CT) * (TILE / CT);
     if (work)
-        render_fwd_kernel<TILE, BATCH, true, CT><<<ct.tiles_total * NB, CT * CT / 2, 0, st>>>(sp, pr, rg, ct, bg, img,
-                                                                                             tf, nl, work, full, stride);
+        render_fwd_kernel<TILE, BATCH, true, CT, PPL><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(
+            sp, pr, rg, ct, bg, img, tf, nl, work, full, stride);
     else
-        render_fwd_kernel<TILE, BATCH, false, CT><<<ct.tiles_total * NB, CT * CT / 2, 0, st>>>(
+        render_fwd_kernel<TILE, BATCH, false, CT, PPL><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(
             sp, pr, rg, ct, bg, img, tf, nl, nullptr, nullptr, 1);
     count_launch();
     return check_launch("render_fwd_kernel");
