@@ -480,6 +480,31 @@ def main():
                "var_rows": ist.n_var, "kept": int(((ist.m[:ts.n] > 0) & (isv > 0)).sum())}
         del ist
 
+    # ---------------- densification-stage training (Sec. 3.4): s3 = 60 iterations over every parameter of
+    # the var rows (the contiguous tail of G_t), base rows fixed (graph-replayed)
+    from paper_2411_14847_gb300.timestep import DensifyStage
+    den = None
+    n_base = int((isv == 0).sum().item())
+    if ts.n > n_base:
+        dst = DensifyStage(ts.view(), n_base, cams, targets, tile=tile, batch=batch, lambda_dssim=0.2)
+        dst.run(2)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ea.record()
+        dst.run(60)
+        eb.record()
+        torch.cuda.synchronize()
+        den = {"iters": 60, "ms": round(ea.elapsed_time(eb), 3), "ms_per_iter": round(ea.elapsed_time(eb) / 60, 3),
+               "var_rows": dst.n_var}
+        del dst
+    stages = None
+    if inh is not None and den is not None:
+        # the paper's schedule per timestep: s1 = 20 inheritance, s2 = 100 shift, s3 = 60 densification
+        # iterations (Sec. 4.1), from the per-iteration costs measured above
+        stages = {"s1_s2_s3": [20, 100, 60],
+                  "estimated_s_per_timestep": round((20 * inh["ms_per_iter"] + 100 * batched_ms
+                                                     + 60 * den["ms_per_iter"]) / 1e3, 4)}
+
     # ---------------- render latency: one novel 1352x1014 view, forward only, p50/p99
     rfr = raster.Frame(cams[:1], ts.n, tile=tile, batch=batch)
     gv = ts.view()
@@ -545,7 +570,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
-                "plain": plain, "inherit_stage": inh, "render_latency": {"single_view": render, "under_load": serve},
+                "plain": plain, "inherit_stage": inh, "densify_stage": den, "paper_schedule": stages,
+                "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "cpu_baseline": cpu}
         print(json.dumps(line))

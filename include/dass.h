@@ -250,6 +250,13 @@ int dass_keep_grad(int64_t n, int sh_degree, const float* means, const float* lo
 
 /* ------------------------------------------------------------------ DASS stages */
 
+/* Low-opacity pruning of the densification stage (Sec. 3.4: var Gaussians of very low opacity
+ * are eliminated) expressed as keep logits for dass_inherit: m[g] = opacity_logit[g] -
+ * logit(min_opacity), positive iff sigmoid(opacity_logit[g]) > min_opacity. Passing m to
+ * dass_inherit (erase = 0) keeps every base row and the var rows above the threshold, in order.
+ * min_opacity in (0, 1). */
+int dass_prune_logits(int64_t n, const float* opacity_logit, float min_opacity, float* m, void* stream);
+
 /* Rendering mask of the selective-inheritance stage (Sec. 3.2, Eq. 1): keep[g] =
  * Quant(sigmoid(m[g])) = [m[g] > 0] for var rows (is_var[g] != 0), 1 for base rows. */
 int dass_inherit_keep(int64_t n, const uint8_t* is_var, const float* m, uint8_t* keep, void* stream);

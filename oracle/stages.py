@@ -68,6 +68,19 @@ def inherit(arrays: dict, is_var, m, t, erase_every=20):
     return out, new_var, remap
 
 
+def prune_low_opacity(arrays: dict, is_var, min_opacity):
+    """Low-opacity pruning of the densification stage (Sec. 3.4): every base row is kept, a var row
+    only if its opacity sigmoid(logit) exceeds min_opacity; base rows first, then the kept var rows,
+    each group in its original order (the layout of the inheritance copy)."""
+    is_var = np.asarray(is_var, dtype=bool)
+    o = 1.0 / (1.0 + np.exp(-np.asarray(arrays["opacity_logit"], dtype=np.float64)))
+    keep_var = is_var & (o > min_opacity)
+    rows = np.concatenate([np.nonzero(~is_var)[0], np.nonzero(keep_var)[0]])
+    out = {k: np.asarray(v)[rows].copy() for k, v in arrays.items()}
+    new_var = np.concatenate([np.zeros(int((~is_var).sum()), bool), np.ones(int(keep_var.sum()), bool)])
+    return out, new_var
+
+
 # ------------------------------------------------------------ optimiser
 
 def adam(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, rows=None):

@@ -48,6 +48,7 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
                    float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
                    cudaStream_t st);
 int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st);
+int prune_logits_launch(long long n, const float* logit, float min_opacity, float* m, cudaStream_t st);
 int inherit_mask_grad_launch(long long n_rows, const int* rows, const float* m, const float* d_keep, float lambda,
                              float* grad, double* loss, cudaStream_t st);
 size_t error_pass_workspace_bytes(const CamTable& ct);
@@ -356,6 +357,12 @@ DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
     if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     *bytes = inherit_workspace_bytes(n);
     return DASS_OK;
+}
+
+DASS_API int dass_prune_logits(int64_t n, const float* opacity_logit, float min_opacity, float* m, void* stream) {
+    if (n < 0 || (n > 0 && (!opacity_logit || !m)) || !(min_opacity > 0.f && min_opacity < 1.f))
+        return DASS_ERR_INVALID_ARG;
+    return prune_logits_launch(n, opacity_logit, min_opacity, m, as_stream(stream));
 }
 
 DASS_API int dass_inherit_keep(int64_t n, const uint8_t* is_var, const float* m, uint8_t* keep, void* stream) {

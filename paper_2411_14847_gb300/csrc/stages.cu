@@ -411,6 +411,21 @@ size_t inherit_workspace_bytes(long long n) {
     return c.used;
 }
 
+// Keep logits of the low-opacity pruning (Sec. 3.4): m[g] = opacity_logit[g] - logit(min_opacity),
+// positive iff sigmoid(opacity_logit[g]) > min_opacity, for the inheritance copy to keep or drop
+// var rows by.
+__global__ void prune_logits_kernel(long long n, const float* __restrict__ logit, float thr, float* __restrict__ m) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) m[i] = logit[i] - thr;
+}
+
+int prune_logits_launch(long long n, const float* logit, float min_opacity, float* m, cudaStream_t st) {
+    if (n <= 0) return DASS_OK;
+    const float thr = logf(min_opacity / (1.f - min_opacity));
+    prune_logits_kernel<<<div_up(n, 256), 256, 0, st>>>(n, logit, thr, m); count_launch();
+    return check_launch("prune_logits_kernel");
+}
+
 int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st) {
     if (n <= 0) return DASS_OK;
     inherit_keep_kernel<<<div_up(n, 256), 256, 0, st>>>(n, is_var, m, keep); count_launch();

@@ -93,6 +93,7 @@ _SIGS = {
                                  _P, _P]),
     "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
     "dass_inherit_keep": (C.c_int, [C.c_int64, _P, _P, _P, _P]),
+    "dass_prune_logits": (C.c_int, [C.c_int64, _P, C.c_float, _P, _P]),
     "dass_inherit_mask_grad": (C.c_int, [C.c_int64, _P, _P, _P, C.c_float, _P, _P, _P]),
     "dass_shift": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "dass_shift_bwd": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
@@ -281,6 +282,11 @@ def dass_keep_grad(g, cams, splats, splat_grads, d_keep, keep=None, rows=None, s
     _call("dass_keep_grad", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
           _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), _ptr(splats, F32),
           _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, _ptr(d_keep, F32), _stream(stream))
+
+
+def dass_prune_logits(opacity_logit, min_opacity, m, stream=None):
+    _call("dass_prune_logits", opacity_logit.numel(), _ptr(opacity_logit, F32), float(min_opacity), _ptr(m, F32),
+          _stream(stream))
 
 
 def dass_inherit_keep(is_var, m, keep, stream=None):

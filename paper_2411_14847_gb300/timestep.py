@@ -7,6 +7,8 @@ A timestep (Sec. 3.1) turns G_{t-1} into G_t with the multi-view images of times
   2. dynamics-aware shift stage, n_shift iterations (Sec. 3.3) -> dass_step (graph replay)
   3. error pass on the last shift render, Eq. 4 selection and spawn (Sec. 3.4)
                                                            -> dass_error_pass, dass_densify_select, dass_spawn
+  4. densification-stage training of the var rows, s3 iterations (DensifyStage: dass_preprocess_bwd
+     over the var tail, dass_adam), then low-opacity pruning -> dass_prune_logits, dass_inherit
 This module only allocates buffers (PyTorch) and sequences the calls.
 """
 from __future__ import annotations
@@ -218,6 +220,134 @@ class InheritStage:
         return self.m
 
 
+class DensifyStage:
+    """Densification-stage training (Sec. 3.4): s3 iterations of the fidelity loss (Eq. 3) over every
+    parameter of the var Gaussians (the new spawns and the inherited var rows), base rows fixed.
+
+    The var rows must be the contiguous tail [n_base, n) of the arrays (the layout dass_inherit and
+    dass_spawn produce), so each parameter's var part is a slice: the backward runs full splat
+    gradients for var rows only (dass_render_bwd full_grad), dass_preprocess_bwd with rows = the
+    tail gives compact gradients of exactly those slices, and dass_adam updates the slices. One
+    iteration runs eagerly, the rest replay it as a captured CUDA graph.
+
+    The paper trains these Gaussians as vanilla 3DGS does and states no learning rates; the 3DGS
+    ones are used (positions 1.6e-4 per unit of scene extent, log-scales 5e-3, rotations 1e-3,
+    opacity logits 5e-2, SH DC 2.5e-3 and higher bands 2.5e-3 / 20)."""
+
+    def __init__(self, g, n_base, cams, targets, tile=16, batch=128, lambda_dssim=0.2, extent=3.0, lr=None,
+                 beta1=0.9, beta2=0.999, eps=1e-15):
+        self.g = {k: g[k] for k in PARAM_NAMES}
+        for k in PARAM_NAMES:
+            assert self.g[k].is_contiguous()
+        self.cams = list(cams)
+        self.n = int(self.g["means"].shape[0])
+        self.n_base = int(n_base)
+        self.n_var = self.n - self.n_base
+        dev = self.g["means"].device
+        self.K = int(self.g["sh"].shape[1])
+        self.targets = targets.contiguous()
+        self.lam = float(lambda_dssim)
+        lr = dict(lr or {})
+        self.lr = dict(means=lr.get("means", 1.6e-4 * extent), log_scales=lr.get("log_scales", 5e-3),
+                       quats=lr.get("quats", 1e-3), opacity_logit=lr.get("opacity_logit", 5e-2),
+                       sh_dc=lr.get("sh_dc", 2.5e-3), sh_rest=lr.get("sh_rest", 2.5e-3 / 20))
+        self.betas, self.eps = (float(beta1), float(beta2)), float(eps)
+        self.rows = torch.arange(self.n_base, self.n, dtype=torch.int32, device=dev)
+        self.full = torch.zeros(max(1, self.n), dtype=torch.uint8, device=dev)
+        self.full[self.n_base:self.n] = 1
+        nv = max(1, self.n_var)
+        widths = dict(means=3, log_scales=3, quats=4, opacity_logit=1, sh=3 * self.K)
+        self.grads = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
+        self.adam_m = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
+        self.adam_v = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
+        self.dL_dimage = torch.zeros_like(self.frame.image)
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _slice(self, k):
+        return self.g[k][self.n_base:self.n].reshape(self.n_var, -1)
+
+    def _iteration(self, eager=False):
+        fr = self.frame
+        fr.project(self.g)
+        if eager:
+            fr.bin_sort()
+        else:
+            fr.bin_sort(grow=False)
+            torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
+        fr.render_fwd()
+        self.loss_buf.zero_()
+        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
+                          fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.full, rec_stride=self.n)
+        if self.n_var == 0:
+            return
+        out = {"d_means": self.grads["means"], "d_log_scales": self.grads["log_scales"],
+               "d_quats": self.grads["quats"], "d_opacity_logit": self.grads["opacity_logit"],
+               "d_sh": self.grads["sh"]}
+        D.dass_preprocess_bwd(self.g, self.cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL, rows=self.rows)
+        b1, b2 = self.betas
+        names = ("means", "log_scales", "quats", "opacity_logit", "sh")
+        for i, k in enumerate(names):
+            if k == "sh":
+                lr = [self.lr["sh_dc"]] * 3 + [self.lr["sh_rest"]] * (3 * (self.K - 1))
+            else:
+                lr = [self.lr[k]] * self.grads[k].shape[1]
+            D.dass_adam(self._slice(k), self.grads[k], self.adam_m[k], self.adam_v[k], self.step, lr, b1, b2,
+                        self.eps, increment_step=(i == len(names) - 1))
+
+    @property
+    def loss(self):
+        return float(self.loss_buf.item())
+
+    def run(self, n_iters, max_regrow=2):
+        """n_iters iterations; on pair-buffer overflow the var rows and optimiser state are restored
+        and the stage reruns with twice the pair capacity."""
+        snap = [self._slice(k).clone() for k in PARAM_NAMES]
+        for _ in range(max_regrow + 1):
+            try:
+                self._run(n_iters)
+                return
+            except D.DassError as e:
+                if e.status != D.ERR_CAPACITY:
+                    raise
+                for k, v in zip(PARAM_NAMES, snap):
+                    self._slice(k).copy_(v)
+                for d in (self.adam_m, self.adam_v):
+                    for t in d.values():
+                        t.zero_()
+                self.step.zero_()
+                self.overflow.zero_()
+                self.frame._alloc_pairs(2 * self.frame.pair_capacity)
+                self.graph = None
+        raise D.DassError("densify stage bin_sort", D.ERR_CAPACITY)
+
+    def _run(self, n_iters):
+        if n_iters <= 0 or self.n == 0:
+            return
+        replays = n_iters
+        if self.graph is None:
+            self._iteration(eager=True)
+            replays -= 1
+            if replays > 0:
+                m_pairs = int(self.frame.counters[0].item())
+                # the var rows move and change size: keep 50% headroom over the pairs of the first render
+                if self.frame.pair_capacity < int(m_pairs * 1.5) + 4096:
+                    self.frame._alloc_pairs(int(m_pairs * 1.5) + 4096)
+                torch.cuda.synchronize()
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self._iteration()
+        for _ in range(replays):
+            self.graph.replay()
+        if replays > 0 and int(self.overflow.item()):
+            raise D.DassError("densify stage bin_sort", D.ERR_CAPACITY)
+
+
 class Timestep:
     """One full timestep t of the streaming pipeline over resident device buffers.
 
@@ -225,7 +355,7 @@ class Timestep:
 
     def __init__(self, cams, n_max, sh_degree, tile=16, batch=128, lambda_dssim=0.2, n_shift=100,
                  quantile=0.95, tau_pos=2e-4, tau_err=1e-4, k_max=5000, erase_every=20, n_inherit=0,
-                 lambda_inher=1e-6, device="cuda"):
+                 lambda_inher=1e-6, n_densify=0, prune_opacity=0.005, device="cuda"):
         self.cams = list(cams)
         self.n_max = int(n_max)
         self.deg = sh_degree
@@ -235,6 +365,7 @@ class Timestep:
         self.quantile, self.tau_pos, self.tau_err, self.k_max = quantile, tau_pos, tau_err, k_max
         self.erase_every = erase_every
         self.n_inherit, self.lambda_inher = int(n_inherit), float(lambda_inher)   # s1 of the inheritance stage
+        self.n_densify, self.prune_opacity = int(n_densify), float(prune_opacity)  # s3 of the densification stage
         self.device = device
         K = (sh_degree + 1) ** 2
         shapes = dict(means=(3,), log_scales=(3,), quats=(4,), opacity_logit=(), sh=(K, 3))
@@ -304,4 +435,34 @@ class Timestep:
         D.dass_spawn({k: v for k, v in self.bufs[self.cur].items()}, n, self.is_var[self.cur], sel, nsel,
                      self.k_max, z[:n].contiguous(), n_total)
         self.n = int(n_total.item())
-        return dict(loss=stage.loss, n=self.n, spawned=int(nsel.item()), stage=stage)
+        spawned = int(nsel.item())
+        out = dict(loss=stage.loss, n=self.n, spawned=spawned, stage=stage)
+        # 4) densification-stage training of the var rows (Sec. 3.4, s3 iterations), then the
+        #    low-opacity pruning of the var rows
+        if self.n_densify > 0:
+            out.update(self._densify(targets))
+        return out
+
+    def _densify(self, targets):
+        n = self.n
+        isv = self.is_var[self.cur][:n]
+        n_base = int((isv == 0).sum().item())
+        if n == n_base:
+            return dict(densify_loss=None, pruned=0)
+        if bool(isv[:n_base].any()) or not bool(isv[n_base:].all()):
+            raise ValueError("densification stage needs the var rows as the contiguous tail of the arrays")
+        stage3 = DensifyStage(self.view(), n_base, self.cams, targets, tile=self.tile, batch=self.batch,
+                              lambda_dssim=self.lambda_dssim)
+        stage3.run(self.n_densify)
+        dev = self.device
+        g = self.view()
+        m = torch.empty(n, device=dev)
+        D.dass_prune_logits(g["opacity_logit"], self.prune_opacity, m)
+        src, dst = self.cur, 1 - self.cur
+        ws = torch.empty(max(1, D.dass_inherit_workspace(n)), dtype=torch.uint8, device=dev)
+        remap = torch.empty(n, dtype=torch.int32, device=dev)
+        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+        D.dass_inherit(g, isv, m, False, {k: v for k, v in self.bufs[dst].items()}, self.is_var[dst], remap, n_out, ws)
+        self.cur = dst
+        self.n = int(n_out.item())
+        return dict(densify_loss=stage3.loss, pruned=n - self.n, n=self.n, densify_stage=stage3)

@@ -466,3 +466,16 @@ def test_spawn_rule():
 def test_mean_grad_and_ndc_norm():
     assert S.mean_grad_f32([3.0, 1.0], [2, 0]).tolist() == [1.5, 0.0]
     assert float(S.ndc_grad_norm(torch.tensor([[3.0 / 50, 4.0 / 20]]), 100, 40)[0]) == pytest.approx(5.0)
+
+
+def test_prune_low_opacity_closed_form():
+    """Sec. 3.4 pruning: base rows always kept; var rows kept iff opacity > threshold; layout
+    base-then-var with each group's order preserved."""
+    from oracle.stages import prune_low_opacity
+    logit = np.array([-9.0, 2.0, -6.0, -4.0, 0.0, -5.5])     # opacities ~1.2e-4, .88, 2.5e-3, .018, .5, 4.1e-3
+    is_var = np.array([0, 1, 1, 0, 1, 1], dtype=bool)
+    arrays = {"opacity_logit": logit, "means": np.arange(18.0).reshape(6, 3)}
+    out, new_var = prune_low_opacity(arrays, is_var, 0.005)
+    assert out["opacity_logit"].tolist() == [-9.0, -4.0, 2.0, 0.0]
+    assert out["means"][:, 0].tolist() == [0.0, 9.0, 3.0, 12.0]
+    assert new_var.tolist() == [False, False, True, True]
