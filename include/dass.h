@@ -278,10 +278,13 @@ int dass_shift(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, cons
 
 /* Backward of dass_shift: from compact d_out_means[n_dyn][3], d_out_quats[n_dyn][4] (the
  * gradients of the shifted rows, e.g. from dass_preprocess_bwd with rows = dyn_idx) to
- * d_offsets[n_dyn][7]. Only dynamic Gaussians receive gradients (Sec. 3.3). */
+ * d_offsets[n_dyn][7]. Only dynamic Gaussians receive gradients (Sec. 3.3). d_quats (optional,
+ * compact [n_dyn][4], NULL = not computed) receives the gradient w.r.t. the input quaternion
+ * quats[dyn_idx[d]] through norm(q) x norm(sigma); the input means' gradient equals d_out_means
+ * (the shift adds dmu). */
 int dass_shift_bwd(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* quats,
                    const float* d_out_means, const float* d_out_quats, float* d_offsets,
-                   void* stream);
+                   float* d_quats, void* stream);
 
 /* Masked Adam step (optimiser not named by the paper; the 3DGS family uses Adam):
  * for each selected row r (rows == NULL: all n_rows rows) and k < row_width:

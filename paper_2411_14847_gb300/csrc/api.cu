@@ -39,7 +39,7 @@ int loss_launch(const float* image, const float* target, const CamTable& ct, flo
 int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats, float* om,
                  float* oq, cudaStream_t st);
 int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
-                     const float* dq, float* doff, cudaStream_t st);
+                     const float* dq, float* doff, float* dqin, cudaStream_t st);
 int adam_launch(long long n_sel, int width, const int* rows, float* p, const float* g, float* m, float* v,
                 int* step_dev, const float* lr, float b1, float b2, float eps, int inc, cudaStream_t st);
 size_t inherit_workspace_bytes(long long n);
@@ -318,11 +318,13 @@ DASS_API int dass_shift(int64_t n_dyn, const int32_t* dyn_idx, const float* offs
 }
 
 DASS_API int dass_shift_bwd(int64_t n_dyn, const int32_t* dyn_idx, const float* offsets, const float* quats,
-                            const float* d_out_means, const float* d_out_quats, float* d_offsets, void* stream) {
+                            const float* d_out_means, const float* d_out_quats, float* d_offsets, float* d_quats,
+                            void* stream) {
     if (n_dyn < 0) return DASS_ERR_INVALID_ARG;
     if (n_dyn > 0 && (!dyn_idx || !offsets || !quats || !d_out_means || !d_out_quats || !d_offsets))
         return DASS_ERR_INVALID_ARG;
-    return shift_bwd_launch(n_dyn, dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, as_stream(stream));
+    return shift_bwd_launch(n_dyn, dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, d_quats,
+                            as_stream(stream));
 }
 
 DASS_API int dass_adam(int64_t n_rows, int row_width, const int32_t* rows, int64_t n_sel, float* param,
@@ -535,7 +537,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
         }
     }
     rc = shift_bwd_launch(d->n_dyn, d->dyn_idx, d->offsets, d->quats, d->d_means_dyn, d->d_quats_dyn, d->offset_grad,
-                          st);
+                          nullptr, st);
     if (rc) return rc;
     float lr[7] = {d->lr_mu, d->lr_mu, d->lr_mu, d->lr_sigma, d->lr_sigma, d->lr_sigma, d->lr_sigma};
     return adam_launch(d->n_dyn, 7, nullptr, d->offsets, d->offset_grad, d->adam_m, d->adam_v, d->adam_step, lr,

@@ -45,7 +45,7 @@ __global__ void shift_fwd_kernel(long long n_dyn, const int* __restrict__ idx, c
 
 __global__ void shift_bwd_kernel(long long n_dyn, const int* __restrict__ idx, const float* __restrict__ off,
                                  const float* __restrict__ quats, const float* __restrict__ dm,
-                                 const float* __restrict__ dq, float* __restrict__ doff) {
+                                 const float* __restrict__ dq, float* __restrict__ doff, float* __restrict__ dqin) {
     long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= n_dyn) return;
     long long n = idx[d];
@@ -69,6 +69,19 @@ __global__ void shift_bwd_kernel(long long n_dyn, const int* __restrict__ idx, c
     float dot = gs[0] * sh[0] + gs[1] * sh[1] + gs[2] * sh[2] + gs[3] * sh[3];
 #pragma unroll
     for (int k = 0; k < 4; ++k) g[3 + k] = (gs[k] - dot * sh[k]) / len;
+    if (dqin) {
+        // q' = q_hat x sigma_hat = R(sigma_hat) q_hat: dL/dq_hat = R(sigma_hat)^T dL/dq', then through
+        // q_hat = q / |q|
+        float gh[4];
+        gh[0] = sh[0] * gq[0] + sh[1] * gq[1] + sh[2] * gq[2] + sh[3] * gq[3];
+        gh[1] = -sh[1] * gq[0] + sh[0] * gq[1] - sh[3] * gq[2] + sh[2] * gq[3];
+        gh[2] = -sh[2] * gq[0] + sh[3] * gq[1] + sh[0] * gq[2] - sh[1] * gq[3];
+        gh[3] = -sh[3] * gq[0] - sh[2] * gq[1] + sh[1] * gq[2] + sh[0] * gq[3];
+        float d2 = gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z;
+        float qh[4] = {w, x, y, z};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dqin[4 * d + k] = (gh[k] - d2 * qh[k]) * qn;
+    }
 }
 
 // ----------------------------------------------------------------- masked Adam
@@ -379,9 +392,9 @@ int shift_launch(long long n_dyn, const int* idx, const float* off, const float*
 }
 
 int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
-                     const float* dq, float* doff, cudaStream_t st) {
+                     const float* dq, float* doff, float* dqin, cudaStream_t st) {
     if (n_dyn <= 0) return DASS_OK;
-    shift_bwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, quats, dm, dq, doff); count_launch();
+    shift_bwd_kernel<<<div_up(n_dyn, 256), 256, 0, st>>>(n_dyn, idx, off, quats, dm, dq, doff, dqin); count_launch();
     return check_launch("shift_bwd_kernel");
 }
 

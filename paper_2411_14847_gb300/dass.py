@@ -96,7 +96,7 @@ _SIGS = {
     "dass_prune_logits": (C.c_int, [C.c_int64, _P, C.c_float, _P, _P]),
     "dass_inherit_mask_grad": (C.c_int, [C.c_int64, _P, _P, _P, C.c_float, _P, _P, _P]),
     "dass_shift": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
-    "dass_shift_bwd": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
+    "dass_shift_bwd": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dass_adam": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_float, C.c_float,
                             C.c_float, C.c_int, _P]),
     "dass_loss_workspace": (C.c_int, [_P, C.c_int, _P]),
@@ -310,9 +310,9 @@ def dass_shift(dyn_idx, offsets, means, quats, out_means, out_quats, stream=None
           _ptr(out_means, F32), _ptr(out_quats, F32), _stream(stream))
 
 
-def dass_shift_bwd(dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, stream=None):
+def dass_shift_bwd(dyn_idx, offsets, quats, d_out_means, d_out_quats, d_offsets, d_quats=None, stream=None):
     _call("dass_shift_bwd", dyn_idx.numel(), _ptr(dyn_idx, I32), _ptr(offsets, F32), _ptr(quats, F32),
-          _ptr(d_out_means, F32), _ptr(d_out_quats, F32), _ptr(d_offsets, F32), _stream(stream))
+          _ptr(d_out_means, F32), _ptr(d_out_quats, F32), _ptr(d_offsets, F32), _ptr(d_quats, F32), _stream(stream))
 
 
 def dass_adam(param, grad, m, v, step_dev, lr, beta1=0.9, beta2=0.999, eps=1e-15, rows=None, increment_step=True,

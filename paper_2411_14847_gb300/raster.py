@@ -93,35 +93,58 @@ class Frame:
 
 
 class DassRender(torch.autograd.Function):
-    """Differentiable multi-camera render: forward = preprocess -> bin/sort -> composite,
-    backward = reverse-order composite backward -> preprocess backward. Returns the planar
-    image buffer (all cameras concatenated)."""
+    """Differentiable multi-camera render: forward = [shift] -> preprocess -> bin/sort -> composite,
+    backward = reverse-order composite backward -> preprocess backward -> [shift backward]. Returns
+    the planar image buffer (all cameras concatenated).
+
+    With dyn_idx and offsets ([n_dyn][7] = (dmu, sigma)) the dynamics-aware shift of Sec. 3.3 is
+    applied to the dynamic rows before the projection (dass_shift): the offsets receive their
+    gradient from dass_shift_bwd, and the means and quaternions of the dynamic rows receive the
+    gradient w.r.t. their unshifted values (the mean's is the shifted one's, the quaternion's goes
+    through norm(q) x norm(sigma))."""
 
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logit, sh, frame: Frame, bg=None):
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, offsets, frame: Frame, dyn_idx=None, bg=None):
         g = dict(means=means.detach().contiguous(), log_scales=log_scales.detach().contiguous(),
                  quats=quats.detach().contiguous(), opacity_logit=opacity_logit.detach().contiguous(),
                  sh=sh.detach().contiguous())
-        frame.project(g)
+        gr = g
+        off = None
+        if offsets is not None:
+            off = offsets.detach().contiguous()
+            rm, rq = g["means"].clone(), g["quats"].clone()
+            D.dass_shift(dyn_idx, off, g["means"], g["quats"], rm, rq)
+            gr = dict(g, means=rm, quats=rq)
+        frame.project(gr)
         frame.bin_sort()
         frame.render_fwd(bg)
-        ctx.frame = frame
-        ctx.bg = bg
-        ctx.g = g
+        ctx.frame, ctx.bg, ctx.g, ctx.gr, ctx.off, ctx.dyn_idx = frame, bg, g, gr, off, dyn_idx
         return frame.image.clone()
 
     @staticmethod
     def backward(ctx, dimage):
         fr = ctx.frame
         fr.render_bwd(dimage.contiguous(), bg=ctx.bg)
-        g = ctx.g
+        g, gr = ctx.g, ctx.gr
         out = {"d_means": torch.empty_like(g["means"]), "d_log_scales": torch.empty_like(g["log_scales"]),
                "d_quats": torch.empty_like(g["quats"]), "d_opacity_logit": torch.empty_like(g["opacity_logit"]),
                "d_sh": torch.empty_like(g["sh"])}
-        D.dass_preprocess_bwd(g, fr.cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL)
-        return out["d_means"], out["d_log_scales"], out["d_quats"], out["d_opacity_logit"], out["d_sh"], None, None
+        D.dass_preprocess_bwd(gr, fr.cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL)
+        d_off = None
+        if ctx.off is not None:
+            idx = ctx.dyn_idx.long()
+            dm = out["d_means"][idx].contiguous()
+            dq = out["d_quats"][idx].contiguous()
+            d_off = torch.empty_like(ctx.off)
+            dq_in = torch.empty_like(dq)
+            D.dass_shift_bwd(ctx.dyn_idx, ctx.off, g["quats"], dm, dq, d_off, dq_in)
+            out["d_quats"][idx] = dq_in
+        return (out["d_means"], out["d_log_scales"], out["d_quats"], out["d_opacity_logit"], out["d_sh"], d_off, None,
+                None, None)
 
 
-def render_autograd(params: dict, frame: Frame, bg=None):
+def render_autograd(params: dict, frame: Frame, bg=None, dyn_idx=None, offsets=None):
+    """Differentiable render of params (dict of tensors) into the frame's cameras; with dyn_idx and
+    offsets, through the dynamics-aware shift of the dynamic rows."""
     return DassRender.apply(params["means"], params["log_scales"], params["quats"], params["opacity_logit"],
-                            params["sh"], frame, bg)
+                            params["sh"], offsets, frame, dyn_idx, bg)

@@ -282,3 +282,35 @@ def test_backward_mean_only_for_unmasked_gaussians(dass):
     assert rel_l2(part[:, ~m, 0:2].cpu().numpy(), ref[:, ~m, 0:2].cpu().numpy()) < 1e-5
     assert float(part[:, ~m, 2:].abs().max()) == 0.0
     assert float(ref[:, ~m, 2:9].abs().max()) > 0.0
+
+
+def test_autograd_gradients_with_shift_offsets(dass):
+    """The autograd Function through the dynamics-aware shift (Sec. 3.3): gradients of all six
+    inputs -- means, log-scales, quaternions, opacity logits, SH and the dynamic rows' offsets --
+    against the oracle's analytic (autodiff) gradients, which are pinned by finite differences."""
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene, cams = _small_multicam(n=1500, w=64, h=48, deg=1)
+    deg = 1
+    rng = np.random.default_rng(12)
+    dyn = np.sort(rng.choice(scene.n, 150, replace=False)).astype(np.int32)
+    off = np.zeros((150, 7))
+    off[:, :3] = rng.normal(0, 0.02, (150, 3))
+    off[:, 3:] = np.array([1.0, 0, 0, 0]) + rng.normal(0, 0.05, (150, 4))
+    targets = [t["image"] for t in og.render(synth.perturbed(scene, 2001).arrays(), cams, deg)]
+    ref = og.loss_grads(scene.arrays(), cams, deg, targets, 0.2, dyn_idx=dyn, offsets=off)
+    params = {k: v.clone().requires_grad_(True) for k, v in raster.to_device(scene.arrays()).items()}
+    off_t = torch.tensor(off, dtype=torch.float32, device="cuda", requires_grad=True)
+    dyn_t = torch.as_tensor(dyn, device="cuda")
+    fr = _frame(dass, cams, scene.n)
+    img = raster.render_autograd(params, fr, dyn_idx=dyn_t, offsets=off_t)
+    tgt = torch.cat([t.reshape(-1) for t in targets]).float().cuda()
+    dimg = torch.empty_like(img)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(1, D.dass_loss_workspace(cams)), dtype=torch.uint8, device="cuda")
+    D.dass_loss(img.detach(), tgt, cams, 0.2, dimg, loss, ws)
+    img.backward(dimg)
+    torch.cuda.synchronize()
+    assert float(loss) == pytest.approx(ref["loss"], rel=1e-4)
+    for k in og.PARAMS:
+        assert rel_l2(params[k].grad.cpu().numpy(), ref[k].numpy()) < 1e-3, k
+    assert rel_l2(off_t.grad.cpu().numpy(), ref["offsets"].numpy()) < 1e-3
