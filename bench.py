@@ -497,6 +497,21 @@ def main():
         den = {"iters": 60, "ms": round(ea.elapsed_time(eb), 3), "ms_per_iter": round(ea.elapsed_time(eb) / 60, 3),
                "var_rows": dst.n_var}
         del dst
+    # ---------------- shift stage with the paper's hash-encoding deformation fields (Sec. 3.3):
+    # H_dyn (2^16 x 4) on the dynamic group and H_st (2^14 x 2) on the static group, every Gaussian
+    # shifted and back-propagated (graph-replayed)
+    from paper_2411_14847_gb300.timestep import FieldShiftStage
+    fst = FieldShiftStage(ts.view(), cams, targets, dyn_t, tile=tile, batch=batch, lambda_dssim=0.2)
+    fst.run(2)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ea.record()
+    fst.run(20)
+    eb.record()
+    torch.cuda.synchronize()
+    field_shift = {"iters": 20, "ms_per_iter": round(ea.elapsed_time(eb) / 20, 3),
+                   "groups": [g_["n"] for g_ in fst.groups], "loss_last": fst.loss}
+    del fst
     stages = None
     if inh is not None and den is not None:
         # the paper's schedule per timestep: s1 = 20 inheritance, s2 = 100 shift, s3 = 60 densification
@@ -570,7 +585,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
-                "plain": plain, "inherit_stage": inh, "densify_stage": den, "paper_schedule": stages,
+                "plain": plain, "inherit_stage": inh, "densify_stage": den, "field_shift_stage": field_shift,
+                "paper_schedule": stages,
                 "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "cpu_baseline": cpu}

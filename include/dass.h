@@ -248,6 +248,48 @@ int dass_keep_grad(int64_t n, int sh_degree, const float* means, const float* lo
                    const dass_splat* splats, const dass_splat_grad* splat_grads,
                    const int32_t* rows, int64_t n_rows, float* d_keep, void* stream);
 
+/* ------------------------------------------------------------------ deformation fields (Sec. 3.3) */
+
+/* Hash-encoding deformation field (Sec. 3.3, App. B.2: multiresolution hash encoding of I-NGP
+ * followed by a small MLP). For a Gaussian at position p:
+ *   x = clamp((p - bbox_min) / (bbox_max - bbox_min), 0, 1)^3;
+ *   level l < levels: N_l = res[l] cells per axis, vertices 0..N_l; the 8 vertices of x's cell
+ *   are looked up in table[l][T][features] (T = 2^log2_table) at index
+ *   i + j (N_l + 1) + k (N_l + 1)^2 when (N_l + 1)^3 <= T, else the spatial hash
+ *   (i * 1 ^ j * 2654435761 ^ k * 805459861) mod T (uint32 arithmetic), and trilinearly
+ *   interpolated: enc = concat_l interp_l  (levels * features values);
+ *   h = relu(w1 enc + b1) (hidden units), out = w2 h + b2 (7 values);
+ *   offsets = (out[0..2], 1 + out[3], out[4], out[5], out[6]) = (dmu, sigma) for dass_shift.
+ * All arrays are FP32 device memory: table [levels][T][features], w1 [hidden][levels*features],
+ * b1 [hidden], w2 [7][hidden], b2 [7]. Limits: levels <= 16, features in {2, 4},
+ * levels * features <= 64, hidden == 64. */
+typedef struct dass_field {
+    int32_t levels;
+    int32_t features;
+    int32_t log2_table;
+    int32_t hidden;
+    int32_t res[16];          /* N_l per level */
+    float bbox_min[3];
+    float bbox_max[3];
+    const float* table;
+    const float* w1;
+    const float* b1;
+    const float* w2;
+    const float* b2;
+} dass_field;
+
+/* offsets[r][7] of rows r < n_rows (row g = rows[r], or r if rows == NULL) at positions
+ * means[g] (n x 3). */
+int dass_field_fwd(const dass_field* field, int64_t n_rows, const int32_t* rows, const float* means,
+                   float* offsets, void* stream);
+
+/* Gradients of the field's parameters from d_offsets[n_rows][7] (e.g. dass_shift_bwd's
+ * d_offsets): ADDED to d_table, d_w1, d_b1, d_w2, d_b2 (same shapes as the parameters; the
+ * caller zeroes them). The forward is recomputed; table gradients are scattered with atomics. */
+int dass_field_bwd(const dass_field* field, int64_t n_rows, const int32_t* rows, const float* means,
+                   const float* d_offsets, float* d_table, float* d_w1, float* d_b1, float* d_w2,
+                   float* d_b2, void* stream);
+
 /* ------------------------------------------------------------------ DASS stages */
 
 /* Low-opacity pruning of the densification stage (Sec. 3.4: var Gaussians of very low opacity

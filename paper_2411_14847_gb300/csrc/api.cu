@@ -5,6 +5,10 @@
 #include <cstring>
 #include <vector>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 
 namespace dass {
@@ -48,6 +52,10 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
                    float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
                    cudaStream_t st);
 int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st);
+int field_fwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, float* out,
+                     cudaStream_t st);
+int field_bwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, const float* dof,
+                     float* dt, float* dw1, float* db1, float* dw2, float* db2, cudaStream_t st);
 int prune_logits_launch(long long n, const float* logit, float min_opacity, float* m, cudaStream_t st);
 int inherit_mask_grad_launch(long long n_rows, const int* rows, const float* m, const float* d_keep, float lambda,
                              float* grad, double* loss, cudaStream_t st);
@@ -74,6 +82,19 @@ void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", m
 
 void set_last_error(const char* what, cudaError_t e) {
     snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+int allow_dynamic_smem(const void* kernel, int bytes) {
+    if (bytes <= 48 * 1024) return DASS_OK;
+    int dev = 0;
+    DASS_CHECK_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return DASS_OK;
+    DASS_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.insert({kernel, dev});
+    return DASS_OK;
 }
 
 int check_launch(const char* what) {
@@ -359,6 +380,21 @@ DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
     if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     *bytes = inherit_workspace_bytes(n);
     return DASS_OK;
+}
+
+DASS_API int dass_field_fwd(const dass_field* field, int64_t n_rows, const int32_t* rows, const float* means,
+                            float* offsets, void* stream) {
+    if (n_rows < 0 || (n_rows > 0 && (!means || !offsets))) return DASS_ERR_INVALID_ARG;
+    return field_fwd_launch(field, n_rows, rows, means, offsets, as_stream(stream));
+}
+
+DASS_API int dass_field_bwd(const dass_field* field, int64_t n_rows, const int32_t* rows, const float* means,
+                            const float* d_offsets, float* d_table, float* d_w1, float* d_b1, float* d_w2,
+                            float* d_b2, void* stream) {
+    if (n_rows < 0 || (n_rows > 0 && (!means || !d_offsets || !d_table || !d_w1 || !d_b1 || !d_w2 || !d_b2)))
+        return DASS_ERR_INVALID_ARG;
+    return field_bwd_launch(field, n_rows, rows, means, d_offsets, d_table, d_w1, d_b1, d_w2, d_b2,
+                            as_stream(stream));
 }
 
 DASS_API int dass_prune_logits(int64_t n, const float* opacity_logit, float min_opacity, float* m, void* stream) {

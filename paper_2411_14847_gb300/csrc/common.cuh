@@ -19,6 +19,9 @@ int check_launch(const char* what);   // returns DASS_OK or DASS_ERR_CUDA
 void count_launch(long long k = 1);
 long long launches_so_far();
 void set_launches(long long v);
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device (once per kernel and
+// device; a no-op up to the default 48 KB). Not to be first called under stream capture.
+int allow_dynamic_smem(const void* kernel, int bytes);
 
 #define DASS_CHECK_CUDA(call)                                              \
     do {                                                                   \

@@ -10,30 +10,11 @@
 // T_j = T_{j+1}/(1-alpha_j) from the saved T_final, and reduces per-Gaussian gradients
 // warp-wide (shuffles), then block-wide (shared-memory atomics), then into global memory
 // (vector atomics).
-#include <mutex>
-#include <set>
-#include <utility>
-
 #include "common.cuh"
 
 namespace dass {
 
 namespace {
-
-// Opt a kernel in to `bytes` of dynamic shared memory on the current device (once per kernel and
-// device; a no-op up to the default 48 KB).
-int allow_smem(const void* kernel, int bytes) {
-    if (bytes <= 48 * 1024) return DASS_OK;
-    int dev = 0;
-    DASS_CHECK_CUDA(cudaGetDevice(&dev));
-    static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done.count({kernel, dev})) return DASS_OK;
-    DASS_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    done.insert({kernel, dev});
-    return DASS_OK;
-}
 
 // Staged form of a splat: NG float4 groups in structure-of-arrays shared memory. Every scalar
 // of the per-pixel math is stored twice, so one shared load yields the operand pair of the
@@ -597,7 +578,7 @@ int prepare_bwd() {
     constexpr int PPL = bwd_ppl<TILE>();
     constexpr int CT = bwd_cta<TILE>();
     constexpr int bytes = BwdSmem<BATCH, CT * CT / PPL, PPL / 2>::kBytes;
-    return allow_smem(reinterpret_cast<const void*>(render_bwd_kernel<TILE, BATCH, PPL, CT>), bytes);
+    return allow_dynamic_smem(reinterpret_cast<const void*>(render_bwd_kernel<TILE, BATCH, PPL, CT>), bytes);
 }
 
 template <int TILE, int BATCH>

@@ -93,6 +93,8 @@ _SIGS = {
                                  _P, _P]),
     "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
     "dass_inherit_keep": (C.c_int, [C.c_int64, _P, _P, _P, _P]),
+    "dass_field_fwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "dass_field_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dass_prune_logits": (C.c_int, [C.c_int64, _P, C.c_float, _P, _P]),
     "dass_inherit_mask_grad": (C.c_int, [C.c_int64, _P, _P, _P, C.c_float, _P, _P, _P]),
     "dass_shift": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
@@ -282,6 +284,42 @@ def dass_keep_grad(g, cams, splats, splat_grads, d_keep, keep=None, rows=None, s
     _call("dass_keep_grad", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
           _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), _ptr(splats, F32),
           _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, _ptr(d_keep, F32), _stream(stream))
+
+
+class dass_field(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("features", C.c_int32), ("log2_table", C.c_int32), ("hidden", C.c_int32),
+                ("res", C.c_int32 * 16), ("bbox_min", C.c_float * 3), ("bbox_max", C.c_float * 3),
+                ("table", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p),
+                ("b2", C.c_void_p)]
+
+
+def field_struct(p: dict, res, log2_table, bbox_min, bbox_max):
+    """dass_field over parameter tensors p = {table [L][T][F], w1 [H][L*F], b1 [H], w2 [7][H], b2 [7]}."""
+    f = dass_field()
+    f.levels, f.features = int(p["table"].shape[0]), int(p["table"].shape[2])
+    f.log2_table, f.hidden = int(log2_table), int(p["w1"].shape[0])
+    for i, r in enumerate(res):
+        f.res[i] = int(r)
+    for d in range(3):
+        f.bbox_min[d], f.bbox_max[d] = float(bbox_min[d]), float(bbox_max[d])
+    for k in ("table", "w1", "b1", "w2", "b2"):
+        assert p[k].is_cuda and p[k].dtype == torch.float32 and p[k].is_contiguous(), k
+        setattr(f, k, p[k].data_ptr())
+    return f
+
+
+def dass_field_fwd(field, means, offsets, rows=None, stream=None):
+    n_rows = rows.numel() if rows is not None else means.shape[0]
+    _call("dass_field_fwd", C.byref(field), n_rows, _ptr(rows, I32), _ptr(means, F32), _ptr(offsets, F32),
+          _stream(stream))
+
+
+def dass_field_bwd(field, means, d_offsets, grads, rows=None, stream=None):
+    """grads: dict of tensors table, w1, b1, w2, b2 (accumulated into)."""
+    n_rows = rows.numel() if rows is not None else means.shape[0]
+    _call("dass_field_bwd", C.byref(field), n_rows, _ptr(rows, I32), _ptr(means, F32), _ptr(d_offsets, F32),
+          _ptr(grads["table"], F32), _ptr(grads["w1"], F32), _ptr(grads["b1"], F32), _ptr(grads["w2"], F32),
+          _ptr(grads["b2"], F32), _stream(stream))
 
 
 def dass_prune_logits(opacity_logit, min_opacity, m, stream=None):

@@ -348,6 +348,150 @@ class DensifyStage:
             raise D.DassError("densify stage bin_sort", D.ERR_CAPACITY)
 
 
+def level_resolutions(levels, n_min=16, n_max=2048):
+    """Cells per axis of each hash-grid level: floor(n_min * b^l), b = (n_max / n_min)^(1/(levels-1))."""
+    if levels == 1:
+        return [int(n_min)]
+    b = math.exp((math.log(n_max) - math.log(n_min)) / (levels - 1))
+    return [int(math.floor(n_min * b ** l)) for l in range(levels)]
+
+
+def init_field(levels, features, log2_table, hidden=64, seed=0, device="cuda"):
+    """Parameters of a hash-encoding deformation field: table U(-1e-4, 1e-4) (the I-NGP
+    initialisation), w1 He-normal, b1 = 0, and a zero output layer so that the field starts as the
+    identity deformation (dmu = 0, sigma = (1, 0, 0, 0))."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    T = 1 << log2_table
+    n_in = levels * features
+    p = {"table": (torch.rand((levels, T, features), generator=gen) * 2e-4 - 1e-4),
+         "w1": torch.randn((hidden, n_in), generator=gen) * math.sqrt(2.0 / n_in),
+         "b1": torch.zeros(hidden), "w2": torch.zeros((7, hidden)), "b2": torch.zeros(7)}
+    return {k: v.to(device=device, dtype=torch.float32).contiguous() for k, v in p.items()}
+
+
+class FieldShiftStage:
+    """Dynamics-aware shift with the paper's hash-encoding deformation fields (Sec. 3.3, App. B.2):
+    H_dyn (T = 2^16, F = 4) deforms the dynamic group and the lighter H_st (T = 2^14, F = 2) the
+    static group; both are trained with the fidelity loss of Eq. 3.
+
+    One iteration: offsets of both groups (dass_field_fwd) -> shift of every row (dass_shift) ->
+    projection -> bin/sort -> forward -> loss -> backward (full splat gradients for every row) ->
+    gradients of the shifted means and quaternions per group (dass_preprocess_bwd) -> offset
+    gradients (dass_shift_bwd) -> field gradients (dass_field_bwd) -> Adam on every field tensor.
+    The first iteration runs eagerly, the rest replay it as a captured CUDA graph. The paper names
+    the table sizes and feature widths only; levels (16, resolutions 16..2048), the 64-unit hidden
+    layer, the identity initialisation and the Adam learning rate are readings."""
+
+    def __init__(self, g, cams, targets, dyn_idx, tile=16, batch=128, lambda_dssim=0.2, levels=16, bbox=None,
+                 lr=1e-3, dyn_spec=(4, 16), st_spec=(2, 14), beta1=0.9, beta2=0.999, eps=1e-15, seed=0):
+        self.g = {k: g[k].contiguous() for k in PARAM_NAMES}
+        self.cams = list(cams)
+        self.n = int(self.g["means"].shape[0])
+        dev = self.g["means"].device
+        self.targets = targets.contiguous()
+        self.lam = float(lambda_dssim)
+        self.lr, self.betas, self.eps = float(lr), (float(beta1), float(beta2)), float(eps)
+        mask = torch.zeros(self.n, dtype=torch.bool, device=dev)
+        mask[dyn_idx.long()] = True
+        self.groups = []
+        if bbox is None:
+            lo = self.g["means"].min(0).values.cpu().numpy() - 1e-3
+            hi = self.g["means"].max(0).values.cpu().numpy() + 1e-3
+        else:
+            lo, hi = bbox
+        for gi, (rows, (feats, log2t)) in enumerate(((torch.nonzero(mask).flatten(), dyn_spec),
+                                                     (torch.nonzero(~mask).flatten(), st_spec))):
+            rows = rows.to(torch.int32).contiguous()
+            nr = int(rows.numel())
+            prm = init_field(levels, feats, log2t, seed=seed + gi, device=dev)
+            res = level_resolutions(levels)
+            grp = {"rows": rows, "n": nr, "params": prm, "res": res, "log2t": log2t,
+                   "field": D.field_struct(prm, res, log2t, lo, hi),
+                   "grads": {k: torch.zeros_like(v) for k, v in prm.items()},
+                   "m": {k: torch.zeros_like(v) for k, v in prm.items()},
+                   "v": {k: torch.zeros_like(v) for k, v in prm.items()},
+                   "offsets": torch.zeros((max(1, nr), 7), device=dev),
+                   "d_offsets": torch.zeros((max(1, nr), 7), device=dev),
+                   "d_means": torch.zeros((max(1, nr), 3), device=dev),
+                   "d_quats": torch.zeros((max(1, nr), 4), device=dev)}
+            self.groups.append(grp)
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.render_means = self.g["means"].clone()
+        self.render_quats = self.g["quats"].clone()
+        self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
+        self.dL_dimage = torch.zeros_like(self.frame.image)
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _render_g(self):
+        return dict(self.g, means=self.render_means, quats=self.render_quats)
+
+    def _iteration(self, eager=False):
+        fr = self.frame
+        for grp in self.groups:
+            if grp["n"]:
+                D.dass_field_fwd(grp["field"], self.g["means"], grp["offsets"], rows=grp["rows"])
+                D.dass_shift(grp["rows"], grp["offsets"], self.g["means"], self.g["quats"], self.render_means,
+                             self.render_quats)
+        gr = self._render_g()
+        fr.project(gr)
+        if eager:
+            fr.bin_sort()
+        else:
+            fr.bin_sort(grow=False)
+            torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
+        fr.render_fwd()
+        self.loss_buf.zero_()
+        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        fr.render_bwd(self.dL_dimage)
+        b1, b2 = self.betas
+        last = max(i for i, grp in enumerate(self.groups) if grp["n"]) if any(g_["n"] for g_ in self.groups) else -1
+        for gi, grp in enumerate(self.groups):
+            if not grp["n"]:
+                continue
+            D.dass_preprocess_bwd(gr, self.cams, fr.splats, fr.splat_grads,
+                                  {"d_means": grp["d_means"], "d_quats": grp["d_quats"]},
+                                  D.GRAD_MEANS | D.GRAD_QUATS, rows=grp["rows"])
+            D.dass_shift_bwd(grp["rows"], grp["offsets"], self.g["quats"], grp["d_means"], grp["d_quats"],
+                             grp["d_offsets"])
+            for t in grp["grads"].values():
+                t.zero_()
+            D.dass_field_bwd(grp["field"], self.g["means"], grp["d_offsets"], grp["grads"], rows=grp["rows"])
+            names = list(grp["params"].keys())
+            for i, k in enumerate(names):
+                p_, g_ = grp["params"][k], grp["grads"][k]
+                w = 16 if p_.numel() % 16 == 0 else 1
+                D.dass_adam(p_.view(-1, w), g_.view(-1, w), grp["m"][k].view(-1, w), grp["v"][k].view(-1, w),
+                            self.step, [self.lr] * w, b1, b2, self.eps,
+                            increment_step=(gi == last and i == len(names) - 1))
+
+    @property
+    def loss(self):
+        return float(self.loss_buf.item())
+
+    def run(self, n_iters):
+        if n_iters <= 0 or self.n == 0:
+            return
+        replays = n_iters
+        if self.graph is None:
+            self._iteration(eager=True)
+            replays -= 1
+            if replays > 0:
+                m_pairs = int(self.frame.counters[0].item())
+                if self.frame.pair_capacity < int(m_pairs * 1.25) + 4096:
+                    self.frame._alloc_pairs(int(m_pairs * 1.25) + 4096)
+                torch.cuda.synchronize()
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self._iteration()
+        for _ in range(replays):
+            self.graph.replay()
+        if replays > 0 and int(self.overflow.item()):
+            raise D.DassError("field shift stage bin_sort", D.ERR_CAPACITY)
+
+
 class Timestep:
     """One full timestep t of the streaming pipeline over resident device buffers.
 
