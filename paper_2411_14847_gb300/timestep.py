@@ -261,6 +261,9 @@ class DensifyStage:
         self.adam_m = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
         self.adam_v = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
         self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        band = torch.arange(max(1, self.n_var) * self.K, device=dev) % self.K
+        self.sh_dc_rows = torch.nonzero(band == 0).flatten().to(torch.int32).contiguous()
+        self.sh_rest_rows = torch.nonzero(band > 0).flatten().to(torch.int32).contiguous()
         self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -291,14 +294,17 @@ class DensifyStage:
                "d_sh": self.grads["sh"]}
         D.dass_preprocess_bwd(self.g, self.cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL, rows=self.rows)
         b1, b2 = self.betas
-        names = ("means", "log_scales", "quats", "opacity_logit", "sh")
-        for i, k in enumerate(names):
-            if k == "sh":
-                lr = [self.lr["sh_dc"]] * 3 + [self.lr["sh_rest"]] * (3 * (self.K - 1))
-            else:
-                lr = [self.lr[k]] * self.grads[k].shape[1]
-            D.dass_adam(self._slice(k), self.grads[k], self.adam_m[k], self.adam_v[k], self.step, lr, b1, b2,
-                        self.eps, increment_step=(i == len(names) - 1))
+        for k in ("means", "log_scales", "quats", "opacity_logit"):
+            D.dass_adam(self._slice(k), self.grads[k], self.adam_m[k], self.adam_v[k], self.step,
+                        [self.lr[k]] * self.grads[k].shape[1], b1, b2, self.eps, increment_step=False)
+        # SH as [rows * K, 3]: the DC band and the higher bands take their own learning rates
+        sh = self.g["sh"][self.n_base:self.n].reshape(-1, 3)
+        gs, ms, vs = (t.view(-1, 3) for t in (self.grads["sh"], self.adam_m["sh"], self.adam_v["sh"]))
+        D.dass_adam(sh, gs, ms, vs, self.step, [self.lr["sh_dc"]] * 3, b1, b2, self.eps, rows=self.sh_dc_rows,
+                    increment_step=self.K == 1)
+        if self.K > 1:
+            D.dass_adam(sh, gs, ms, vs, self.step, [self.lr["sh_rest"]] * 3, b1, b2, self.eps,
+                        rows=self.sh_rest_rows, increment_step=True)
 
     @property
     def loss(self):

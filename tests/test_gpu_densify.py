@@ -41,11 +41,13 @@ def test_densify_stage_gradients_of_var_rows(dass, lam):
         assert rel_l2(got, want) < 1e-3, k
 
 
-def test_densify_stage_trains_only_var_rows(dass):
-    """The stage lowers the loss, moves var rows and leaves every base row bit-identical."""
+@pytest.mark.parametrize("deg", [1, 3])
+def test_densify_stage_trains_only_var_rows(dass, deg):
+    """The stage lowers the loss, moves var rows and leaves every base row bit-identical (SH degree
+    3 takes the per-band learning rates through row-selected updates)."""
     from paper_2411_14847_gb300 import raster
     from paper_2411_14847_gb300.timestep import DensifyStage
-    arrays, cams, deg, n_base, targets = _case(seed=32)
+    arrays, cams, deg, n_base, targets = _case(seed=32, deg=deg)
     tgt = torch.cat([t.reshape(-1) for t in targets]).float().cuda()
     g = raster.to_device(arrays)
     before = {k: v.clone() for k, v in g.items()}
