@@ -512,6 +512,28 @@ def main():
     field_shift = {"iters": 20, "ms_per_iter": round(ea.elapsed_time(eb) / 20, 3),
                    "groups": [g_["n"] for g_ in fst.groups], "loss_last": fst.loss}
     del fst
+    # ---------------- dynamics query (Sec. 3.3): 16-dim identity features rendered for all 20 views,
+    # per-pixel object IDs over 64 classes, dynamic objects inside a dynamic area, per-Gaussian mask
+    qn = ts.n
+    qfeat = torch.randn((qn, 16), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    qW = torch.randn((64, 16), device=dev, generator=torch.Generator(device=dev).manual_seed(8))
+    qb = torch.zeros(64, device=dev)
+    qfr = sfr
+    qout = torch.empty((qfr.pixels, 16), device=dev)
+    qids = torch.empty(qfr.pixels, dtype=torch.int32, device=dev)
+    qarea = (torch.rand(qfr.pixels, device=dev) < 0.1).to(torch.uint8)
+    qobj = torch.empty(64, dtype=torch.uint8, device=dev)
+    qhist = torch.empty(64, dtype=torch.int32, device=dev)
+    qmask = torch.empty(max(1, qn), dtype=torch.uint8, device=dev)
+
+    def dyn_query():
+        D.dass_render_features(qfr.splats, qfr.pair_rec, qfr.tile_ranges, cams, tile, qfeat[:qfr.n], qfr.n, qout)
+        D.dass_object_ids(qout, qW, qb, qids)
+        D.dass_dynamic_objects(qids, qarea, 64, 50, qobj, qhist)
+        D.dass_dynamic_gaussians(qfeat[:qfr.n], qW, qb, qobj, qmask[:qfr.n])
+
+    dyn_query_ms = timed(dyn_query, reps=5)
+    del qout
     stages = None
     if inh is not None and den is not None:
         # the paper's schedule per timestep: s1 = 20 inheritance, s2 = 100 shift, s3 = 60 densification
@@ -586,6 +608,7 @@ def main():
                            "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
                 "plain": plain, "inherit_stage": inh, "densify_stage": den, "field_shift_stage": field_shift,
+                "dynamics_query_ms": round(dyn_query_ms, 3),
                 "paper_schedule": stages,
                 "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -290,6 +290,38 @@ int dass_field_bwd(const dass_field* field, int64_t n_rows, const int32_t* rows,
                    const float* d_offsets, float* d_table, float* d_w1, float* d_b1, float* d_w2,
                    float* d_b2, void* stream);
 
+/* ------------------------------------------------------------------ dynamics mask (Sec. 3.3) */
+
+/* Identity-feature rendering (Sec. 3.3: Gaussian Grouping object features, rendered like colour
+ * to query object IDs in any view): the lists, alpha, skip and stop rules of dass_render_fwd
+ * (no background) compositing per-Gaussian feature vectors features[g][n_features], g = record
+ * % rec_stride. n_features in {4, 8, 16, 32}. out: pixel-major [pixels_total][n_features]. */
+int dass_render_features(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                         const dass_camera* cams /* host */, int n_cams, int tile, const float* features,
+                         int n_features, int64_t rec_stride, float* out, void* stream);
+
+/* Object IDs of feature rows (the linear classifier of Gaussian Grouping):
+ * ids[i] = argmax_k (W x_i + b)_k over n_classes (ties to the lower k), W [n_classes][n_features]. */
+int dass_object_ids(const float* x, int64_t n, int n_features, const float* W, const float* b, int n_classes,
+                    int32_t* ids, void* stream);
+
+/* Dynamic objects (Sec. 3.3: the IDs rendered inside the dynamic image areas): obj_mask[k] = 1 iff
+ * at least min_pixels pixels i with dyn_area[i] != 0 have ids[i] == k. hist: device scratch
+ * [n_classes] uint32. The dynamic areas (optical flow above a threshold) are an input. */
+int dass_dynamic_objects(const int32_t* ids, const uint8_t* dyn_area, int64_t n, int n_classes,
+                         uint32_t min_pixels, uint8_t* obj_mask, uint32_t* hist, void* stream);
+
+/* Per-Gaussian dynamics mask (Sec. 3.3): dyn_mask[g] = obj_mask[argmax_k (W f_g + b)_k] for the
+ * Gaussians' own identity features f_g. */
+int dass_dynamic_gaussians(const float* features, int64_t n, int n_features, const float* W, const float* b,
+                           int n_classes, const uint8_t* obj_mask, uint8_t* dyn_mask, void* stream);
+
+/* Stable compaction of a byte mask: rows[0..*count) = the indices i with mask[i] != 0, ascending
+ * (count: device int64), e.g. the dyn_idx of the shift stage from dass_dynamic_gaussians. */
+int dass_mask_rows_workspace(int64_t n, size_t* bytes);
+int dass_mask_rows(const uint8_t* mask, int64_t n, int32_t* rows, int64_t* count, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------ DASS stages */
 
 /* Low-opacity pruning of the densification stage (Sec. 3.4: var Gaussians of very low opacity

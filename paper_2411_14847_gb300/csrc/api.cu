@@ -52,6 +52,17 @@ int inherit_launch(long long n, int deg, const float* means, const float* ls, co
                    float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
                    cudaStream_t st);
 int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st);
+int render_features_launch(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct,
+                           const float* feats, int F, long long stride, float* out, cudaStream_t st);
+int object_ids_launch(const float* x, long long n, int F, const float* W, const float* b, int K, int* ids,
+                      cudaStream_t st);
+int dynamic_objects_launch(const int* ids, const uint8_t* dyn_area, long long n, int K, unsigned int min_pixels,
+                           uint8_t* obj_mask, unsigned int* hist, cudaStream_t st);
+int dynamic_gaussians_launch(const float* feats, long long n, int F, const float* W, const float* b, int K,
+                             const uint8_t* obj_mask, uint8_t* dyn_mask, cudaStream_t st);
+size_t mask_rows_workspace_bytes(long long n);
+int mask_rows_launch(const uint8_t* mask, long long n, int* rows, long long* count, void* ws, size_t ws_bytes,
+                     cudaStream_t st);
 int field_fwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, float* out,
                      cudaStream_t st);
 int field_bwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, const float* dof,
@@ -380,6 +391,49 @@ DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
     if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     *bytes = inherit_workspace_bytes(n);
     return DASS_OK;
+}
+
+DASS_API int dass_render_features(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
+                                  const dass_camera* cams, int n_cams, int tile, const float* features,
+                                  int n_features, int64_t rec_stride, float* out, void* stream) {
+    if (rec_stride <= 0 || !features || !out || !pair_rec || !tile_ranges || !splats) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
+    return render_features_launch(splats, pair_rec, tile_ranges, ct, features, n_features, rec_stride, out,
+                                  as_stream(stream));
+}
+
+DASS_API int dass_object_ids(const float* x, int64_t n, int n_features, const float* W, const float* b,
+                             int n_classes, int32_t* ids, void* stream) {
+    if (n < 0 || n_classes < 1 || (n > 0 && (!x || !W || !b || !ids))) return DASS_ERR_INVALID_ARG;
+    return object_ids_launch(x, n, n_features, W, b, n_classes, ids, as_stream(stream));
+}
+
+DASS_API int dass_dynamic_objects(const int32_t* ids, const uint8_t* dyn_area, int64_t n, int n_classes,
+                                  uint32_t min_pixels, uint8_t* obj_mask, uint32_t* hist, void* stream) {
+    if (n < 0 || n_classes < 1 || !obj_mask || !hist || (n > 0 && (!ids || !dyn_area))) return DASS_ERR_INVALID_ARG;
+    return dynamic_objects_launch(ids, dyn_area, n, n_classes, min_pixels, obj_mask, hist, as_stream(stream));
+}
+
+DASS_API int dass_dynamic_gaussians(const float* features, int64_t n, int n_features, const float* W,
+                                    const float* b, int n_classes, const uint8_t* obj_mask, uint8_t* dyn_mask,
+                                    void* stream) {
+    if (n < 0 || n_classes < 1 || (n > 0 && (!features || !W || !b || !obj_mask || !dyn_mask)))
+        return DASS_ERR_INVALID_ARG;
+    return dynamic_gaussians_launch(features, n, n_features, W, b, n_classes, obj_mask, dyn_mask, as_stream(stream));
+}
+
+DASS_API int dass_mask_rows_workspace(int64_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
+    *bytes = mask_rows_workspace_bytes(n);
+    return DASS_OK;
+}
+
+DASS_API int dass_mask_rows(const uint8_t* mask, int64_t n, int32_t* rows, int64_t* count, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    if (n < 0 || !count || (n > 0 && (!mask || !rows || !workspace))) return DASS_ERR_INVALID_ARG;
+    return mask_rows_launch(mask, n, rows, reinterpret_cast<long long*>(count), workspace, workspace_bytes,
+                            as_stream(stream));
 }
 
 DASS_API int dass_field_fwd(const dass_field* field, int64_t n_rows, const int32_t* rows, const float* means,

@@ -94,6 +94,12 @@ _SIGS = {
     "dass_densify_stats": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, _P, _P, _P]),
     "dass_inherit_keep": (C.c_int, [C.c_int64, _P, _P, _P, _P]),
     "dass_field_fwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "dass_render_features": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int64, _P, _P]),
+    "dass_object_ids": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, C.c_int, _P, _P]),
+    "dass_dynamic_objects": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_uint32, _P, _P, _P]),
+    "dass_dynamic_gaussians": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, C.c_int, _P, _P, _P]),
+    "dass_mask_rows_workspace": (C.c_int, [C.c_int64, _P]),
+    "dass_mask_rows": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_field_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dass_prune_logits": (C.c_int, [C.c_int64, _P, C.c_float, _P, _P]),
     "dass_inherit_mask_grad": (C.c_int, [C.c_int64, _P, _P, _P, C.c_float, _P, _P, _P]),
@@ -284,6 +290,39 @@ def dass_keep_grad(g, cams, splats, splat_grads, d_keep, keep=None, rows=None, s
     _call("dass_keep_grad", n, deg, _ptr(g["means"], F32), _ptr(g["log_scales"], F32), _ptr(g["quats"], F32),
           _ptr(g["opacity_logit"], F32), _ptr(g["sh"], F32), _ptr(keep, U8), arr, len(cams), _ptr(splats, F32),
           _ptr(splat_grads, F32), _ptr(rows, I32), n_rows, _ptr(d_keep, F32), _stream(stream))
+
+
+def dass_render_features(splats, pair_rec, tile_ranges, cams, tile, features, rec_stride, out, stream=None):
+    """features: [n, F] per Gaussian (F in 4, 8, 16, 32); out: [pixels_total, F]."""
+    arr = cameras(cams)
+    _call("dass_render_features", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams),
+          tile, _ptr(features, F32), int(features.shape[1]), rec_stride, _ptr(out, F32), _stream(stream))
+
+
+def dass_object_ids(x, W, b, ids, stream=None):
+    _call("dass_object_ids", _ptr(x, F32), x.shape[0], int(x.shape[1]), _ptr(W, F32), _ptr(b, F32), int(W.shape[0]),
+          _ptr(ids, I32), _stream(stream))
+
+
+def dass_dynamic_objects(ids, dyn_area, n_classes, min_pixels, obj_mask, hist, stream=None):
+    _call("dass_dynamic_objects", _ptr(ids, I32), _ptr(dyn_area, U8), ids.numel(), int(n_classes), int(min_pixels),
+          _ptr(obj_mask, U8), _ptr(hist, I32), _stream(stream))
+
+
+def dass_dynamic_gaussians(features, W, b, obj_mask, dyn_mask, stream=None):
+    _call("dass_dynamic_gaussians", _ptr(features, F32), features.shape[0], int(features.shape[1]), _ptr(W, F32),
+          _ptr(b, F32), int(W.shape[0]), _ptr(obj_mask, U8), _ptr(dyn_mask, U8), _stream(stream))
+
+
+def dass_mask_rows_workspace(n):
+    b = C.c_size_t()
+    _call("dass_mask_rows_workspace", n, C.byref(b))
+    return b.value
+
+
+def dass_mask_rows(mask, rows, count, workspace, stream=None):
+    _call("dass_mask_rows", _ptr(mask, U8), mask.numel(), _ptr(rows, I32), _ptr(count, I64), _ptr(workspace, U8),
+          workspace.numel(), _stream(stream))
 
 
 class dass_field(C.Structure):
