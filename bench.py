@@ -289,7 +289,7 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_2411_14847_gb300 import build, dass as D, raster, synth
+    from paper_2411_14847_gb300 import build, dass as D, raster, replicas, synth
     from paper_2411_14847_gb300.autotune import autotune
     from paper_2411_14847_gb300.timestep import ShiftStage, Timestep
 
@@ -304,7 +304,7 @@ def main():
     dev = "cuda"
 
     # ---------------- workload (replicas: every rank runs its own timestep stream)
-    scene, cams, dyn_idx, offsets0 = synth.config_c(seed=1003 + rank, n=args.n, n_cams=args.cams,
+    scene, cams, dyn_idx, offsets0 = synth.config_c(seed=replicas.replica_seed(1003, rank), n=args.n, n_cams=args.cams,
                                                      width=args.width, height=args.height)
     g0 = raster.to_device(scene.arrays())
     fr = raster.Frame(cams, scene.n, tile=16, batch=128)
@@ -358,11 +358,8 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = D.dass_kernel_launches() - l0
     clk = clocks.stop()
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = ms_max / 1e3 / (args.steps * world)
+    ms_max = replicas.max_over_ranks(ms, dist if world > 1 else None, device=dev)
+    value = replicas.seconds_per_timestep(ms_max, args.steps, world)
 
     # ---------------- dominant kernels, timed standalone on the last iteration's buffers
     stage = results[-1]["stage"]
