@@ -382,6 +382,21 @@ int dass_loss(const float* image, const float* target, const dass_camera* cams /
               int n_cams, float lambda, float* dL_dimage, double* loss, void* workspace,
               size_t workspace_bytes, void* stream);
 
+/* Window statistics of a target for the SSIM term of Eq. 3, computed once per fixed target set:
+ * stats[0 .. 3P) = w * y (the window mean) and stats[3P .. 6P) = w * y^2 (its second moment),
+ * P = sum of W*H over cams, planar like the image, w the 11x11 window of dass_loss with zero
+ * padding. stats: device, 6P floats, caller-owned. */
+int dass_loss_target_stats(const float* target, const dass_camera* cams /* host */, int n_cams,
+                           float* stats, void* stream);
+
+/* dass_loss with the target's window statistics taken from dass_loss_target_stats (same cams,
+ * same target) instead of filtered again: same loss and gradient up to FP32 rounding order.
+ * The workspace is dass_loss_workspace's. */
+int dass_loss_cached(const float* image, const float* target, const float* target_stats,
+                     const dass_camera* cams /* host */, int n_cams, float lambda,
+                     float* dL_dimage, double* loss, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
 /* Per-iteration statistics of error-guided densification (Sec. 3.4): for every Gaussian g
  * and camera c with a visible record (radius > 0 and the square of half-side radius around
  * mean2d overlapping the image), accum[g] += |(dL/du W/2, dL/dv H/2)| (the view-space
@@ -494,7 +509,10 @@ int dass_step_workspace(const dass_step_desc* d, size_t* bytes);
  * -> forward -> loss -> backward -> preprocess backward (dynamic rows) -> shift backward ->
  * [statistics] -> masked Adam on the offsets. mode DASS_STEP_BATCHED captures one iteration
  * into a CUDA graph on `stream` (which must not be the legacy default stream) and replays it
- * n_iters times; DASS_STEP_PLAIN launches per camera without a graph. render_means/quats
+ * n_iters times; DASS_STEP_PLAIN launches per camera without a graph. With lambda_dssim > 0 the
+ * call first computes the targets' SSIM window statistics into the workspace once
+ * (dass_loss_target_stats) and every iteration's loss reads them (dass_loss_cached).
+ * render_means/quats
  * must hold a copy of means/quats before the first call. The call ends with one stream
  * synchronisation and a read of the pair-overflow flag: it returns DASS_ERR_CAPACITY if any
  * iteration overflowed pair_capacity (results of the stage are then unreliable). */

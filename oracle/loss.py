@@ -36,6 +36,11 @@ def _filter(img):
     return F.conv2d(img[None], w2, padding=WINDOW // 2, groups=img.shape[0])[0]
 
 
+def window_moments(y):
+    """The window statistics of one image that SSIM needs from it alone: (w * y, w * y^2)."""
+    return _filter(y), _filter(y * y)
+
+
 def ssim_map(x, y):
     """Per-pixel, per-channel SSIM of images x, y [3,H,W]."""
     mx, my = _filter(x), _filter(y)

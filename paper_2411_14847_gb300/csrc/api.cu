@@ -39,7 +39,9 @@ int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
 size_t loss_workspace_bytes(const CamTable& ct);
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
-                double* loss, void* ws, size_t ws_bytes, cudaStream_t st);
+                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr,
+                long long stats_stride = 0);
+int target_stats_launch(const float* target, const CamTable& ct, float* stats, cudaStream_t st);
 int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats, float* om,
                  float* oq, cudaStream_t st);
 int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
@@ -387,6 +389,26 @@ DASS_API int dass_loss(const float* image, const float* target, const dass_camer
                        as_stream(stream));
 }
 
+DASS_API int dass_loss_target_stats(const float* target, const dass_camera* cams, int n_cams, float* stats,
+                                   void* stream) {
+    if (!target || !stats) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    return target_stats_launch(target, ct, stats, as_stream(stream));
+}
+
+DASS_API int dass_loss_cached(const float* image, const float* target, const float* target_stats,
+                              const dass_camera* cams, int n_cams, float lambda, float* dL_dimage, double* loss,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+    if (!image || !target || !target_stats || !dL_dimage || !loss || !(lambda >= 0.f && lambda <= 1.f))
+        return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
+    if (lambda > 0.f && workspace_bytes < loss_workspace_bytes(ct)) return DASS_ERR_OOM;
+    return loss_launch(image, target, ct, lambda, 1.f / (float)n_cams, dL_dimage, loss, workspace, workspace_bytes,
+                       as_stream(stream), target_stats, 3 * ct.pixels_total);
+}
+
 DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
     if (n < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     *bytes = inherit_workspace_bytes(n);
@@ -534,6 +556,8 @@ struct StepPlan {
     CamTable all;
     std::vector<CamTable> per;   // one-camera tables (plain mode)
     size_t bin_ws = 0, loss_ws = 0;
+    size_t stats_bytes = 0;      // cached target statistics of the SSIM term (2 maps)
+    size_t total() const;
 };
 
 bool plan_step(const dass_step_desc* d, StepPlan& p, int mode) {
@@ -541,6 +565,7 @@ bool plan_step(const dass_step_desc* d, StepPlan& p, int mode) {
     long long n_rec = (long long)d->n_cams * d->n;
     p.bin_ws = bin_sort_workspace_bytes(mode == DASS_STEP_PLAIN ? d->n : n_rec, d->pair_capacity);
     p.loss_ws = loss_workspace_bytes(p.all);
+    p.stats_bytes = d->lambda_dssim > 0.f ? sizeof(float) * 6 * (size_t)p.all.pixels_total : 0;
     if (mode == DASS_STEP_PLAIN) {
         p.per.resize(d->n_cams);
         for (int c = 0; c < d->n_cams; ++c)
@@ -551,12 +576,21 @@ bool plan_step(const dass_step_desc* d, StepPlan& p, int mode) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+size_t StepPlan::total() const { return align256(bin_ws) + align256(loss_ws) + align256(stats_bytes); }
+
+float* target_stats_ptr(const dass_step_desc* d, const StepPlan& p) {
+    if (!p.stats_bytes) return nullptr;
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(d->workspace) + align256(p.bin_ws) + align256(p.loss_ws));
+}
+
 __global__ void or_flag_kernel(long long* counters) { counters[3] |= counters[1]; }
 
 int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStream_t st) {
     char* ws = reinterpret_cast<char*>(d->workspace);
     void* bin_ws = ws;
     void* loss_ws = ws + align256(p.bin_ws);
+    const float* ystats = target_stats_ptr(d, p);
+    const long long ystride = 3 * p.all.pixels_total;
     const float3 bg = make_float3(0.f, 0.f, 0.f);
     int rc = shift_launch(d->n_dyn, d->dyn_idx, d->offsets, d->means, d->quats, d->render_means, d->render_quats, st);
     if (rc) return rc;
@@ -576,7 +610,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
                                d->n_last, st);
         if (rc) return rc;
         rc = loss_launch(d->image, d->targets, ct, d->lambda_dssim, inv_cams, d->dL_dimage, d->loss, loss_ws,
-                         p.loss_ws, st);
+                         p.loss_ws, st, ystats, ystride);
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemsetAsync(d->splat_grads, 0, sizeof(dass_splat_grad) * n_rec, st));
         rc = render_bwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final, d->n_last,
@@ -609,7 +643,8 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
                                    d->T_final + pb, d->n_last + pb, st);
             if (rc) return rc;
             rc = loss_launch(d->image + 3 * pb, d->targets + 3 * pb, ct, d->lambda_dssim, inv_cams,
-                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st);
+                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st, ystats ? ystats + 3 * pb : nullptr,
+                             ystride);
             if (rc) return rc;
             DASS_CHECK_CUDA(cudaMemsetAsync(gs, 0, sizeof(dass_splat_grad) * d->n, st));
             rc = render_bwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final + pb, d->n_last + pb,
@@ -653,7 +688,7 @@ DASS_API int dass_step_workspace(const dass_step_desc* d, size_t* bytes) {
     if (!d || !bytes) return DASS_ERR_INVALID_ARG;
     StepPlan p;
     if (!plan_step(d, p, DASS_STEP_BATCHED)) return DASS_ERR_INVALID_ARG;
-    *bytes = align256(p.bin_ws) + align256(p.loss_ws);
+    *bytes = p.total();
     return DASS_OK;
 }
 
@@ -662,10 +697,12 @@ DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* str
         return DASS_ERR_INVALID_ARG;
     StepPlan p;
     if (!plan_step(d, p, mode)) return DASS_ERR_INVALID_ARG;
-    if (d->workspace_bytes < align256(p.bin_ws) + align256(p.loss_ws)) return DASS_ERR_OOM;
+    if (d->workspace_bytes < p.total()) return DASS_ERR_OOM;
     cudaStream_t st = as_stream(stream);
     DASS_CHECK_CUDA(cudaMemsetAsync(d->counters, 0, sizeof(int64_t) * 4, st));
     if (n_iters == 0) return DASS_OK;
+    if (float* ys = target_stats_ptr(d, p))   // the targets are fixed for the whole call
+        if (int rc = target_stats_launch(d->targets, p.all, ys, st)) return rc;
     if (mode == DASS_STEP_BATCHED) {
         if (st == nullptr) return DASS_ERR_INVALID_ARG;   // the legacy stream cannot be captured
         cudaGraph_t graph = nullptr;

@@ -31,9 +31,11 @@ struct LossArgs {
     float* dx;            // dL/dimage
     float* g;             // 3 maps, each 3 * pixels_total
     double* loss;
+    const float* ystats;  // optional cached target statistics (2 maps, ystride apart)
     float lambda;
     float inv_cams;
     long long map_stride;  // 3 * pixels_total
+    long long ystride;
 };
 
 __device__ __forceinline__ void plane_of(const CamTable& ct, int z, const CamInfo*& cam, long long& off) {
@@ -92,9 +94,14 @@ struct HorB {
     float s[kI][kHP];
 };
 
-// SQUARES: the staged pair is (x, y) and the quantities are (x, y), (x^2, y^2), x*y; otherwise
-// the staged pair and scalar are filtered as they are (q unused).
-template <bool SQUARES, class Tile, class Hor>
+// Quantities filtered by the passes, from the staged pair (and scalar):
+//   kPairScalar: the staged pair and the staged scalar as they are;
+//   kSquares:    staged (x, y) -> the pairs (x, y), (x^2, y^2) and the scalar x*y;
+//   kCached:     staged (x, y) -> the pair (x, x^2) and the scalar x*y (the target's window
+//                statistics come from a cache).
+enum Mode { kPairScalar = 0, kSquares = 1, kCached = 2 };
+
+template <int MODE, class Tile, class Hor>
 __device__ __forceinline__ void hpass2(const Tile& src, Hor& dst, const Window2& win) {
     for (int job = threadIdx.x; job < kI * (kO / 4); job += 256) {
         const int r = job % kI, c0 = (job / kI) * 4;
@@ -108,21 +115,24 @@ __device__ __forceinline__ void hpass2(const Tile& src, Hor& dst, const Window2&
         }
 #pragma unroll
         for (int k = 0; k < 14; ++k) {
-            const float2 in = src.p[r][c0 + k];
-            float2 sq;
-            float sc;
-            if (SQUARES) {
-                sq = __fmul2_rn(in, in);
-                sc = in.x * in.y;
+            const float2 xy = src.p[r][c0 + k];
+            float2 in = xy, sq = make_float2(0.f, 0.f);
+            float sc = 0.f;
+            if constexpr (MODE == kSquares) {
+                sq = __fmul2_rn(xy, xy);
+                sc = xy.x * xy.y;
+            } else if constexpr (MODE == kCached) {
+                in = make_float2(xy.x, xy.x * xy.x);
+                sc = xy.x * xy.y;
             } else {
-                if constexpr (!SQUARES) sc = src.s[r][c0 + k];
+                sc = src.s[r][c0 + k];
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int t = k - o;
                 if (t >= 0 && t < 11) {
                     a[o] = __ffma2_rn(win.w[t], in, a[o]);
-                    if (SQUARES) b[o] = __ffma2_rn(win.w[t], sq, b[o]);
+                    if constexpr (MODE == kSquares) b[o] = __ffma2_rn(win.w[t], sq, b[o]);
                     c[o] = fmaf(win.w[t].x, sc, c[o]);
                 }
             }
@@ -130,7 +140,7 @@ __device__ __forceinline__ void hpass2(const Tile& src, Hor& dst, const Window2&
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             dst.p[r][c0 + o] = a[o];
-            if constexpr (SQUARES) dst.q[r][c0 + o] = b[o];
+            if constexpr (MODE == kSquares) dst.q[r][c0 + o] = b[o];
             dst.s[r][c0 + o] = c[o];
         }
     }
@@ -195,7 +205,11 @@ __device__ __forceinline__ void stage2(Tile& dst, const float* p0, const float* 
     }
 }
 
+// Forward SSIM of one 32 x 32 output tile. CACHED: the target's window mean and second moment
+// come from a_.ystats (dass_loss_target_stats) and only x, x^2 and x*y are filtered here.
+template <bool CACHED>
 __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 win, LossArgs a) {
+    using Hor = std::conditional_t<CACHED, HorB, HorF>;
     const CamInfo* cam;
     long long off;
     plane_of(ct, blockIdx.z, cam, off);
@@ -203,15 +217,38 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
     const int ox = blockIdx.x * kO, oy = blockIdx.y * kO;
     if (ox >= W || oy >= H) return;
     __shared__ TileF sin;
-    __shared__ HorF sh;
+    __shared__ Hor sh;
+    const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
+    float ym[4], y2[4];
+    if constexpr (CACHED) {      // requested before the stencil work
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int gx = ox + col, gy = oy + r0 + o;
+            const bool in = gx < W && gy < H;
+            const long long idx = off + (long long)gy * W + gx;
+            ym[o] = in ? __ldg(a.ystats + idx) : 0.f;
+            y2[o] = in ? __ldg(a.ystats + a.ystride + idx) : 0.f;
+        }
+    }
     stage2(sin, a.x, a.y, nullptr, off, W, H, ox, oy);
     __syncthreads();
-    hpass2<true>(sin, sh, win);
-    __syncthreads();
-    const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
     float2 m[4], e[4];
     float exy[4];
-    vpass2<true>(sh, win, col, r0, m, e, exy);
+    if constexpr (CACHED) {
+        hpass2<kCached>(sin, sh, win);
+        __syncthreads();
+        float2 unused[4];
+        vpass2<false>(sh, win, col, r0, m, unused, exy);   // m = (mean x, mean x^2)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            e[o] = make_float2(m[o].y, y2[o]);
+            m[o] = make_float2(m[o].x, ym[o]);
+        }
+    } else {
+        hpass2<kSquares>(sin, sh, win);
+        __syncthreads();
+        vpass2<true>(sh, win, col, r0, m, e, exy);
+    }
     const float inv_n = a.inv_cams / (3.f * (float)W * (float)H);
     float contrib = 0.f;
 #pragma unroll
@@ -262,7 +299,7 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
     }
     stage2(sin, a.g, a.g + a.map_stride, a.g + 2 * a.map_stride, off, W, H, ox, oy);
     __syncthreads();
-    hpass2<false>(sin, sh, win);
+    hpass2<kPairScalar>(sin, sh, win);
     __syncthreads();
     float2 c12[4], unused[4];
     float c3[4];
@@ -277,6 +314,36 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
         const float d = xv[o] - yv[o];
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
         a.dx[idx] = inv_n * ((1.f - a.lambda) * sgn - a.lambda * dS);
+    }
+}
+
+// Window statistics of the target (cached across the iterations of a stage): ystats[0] = w * y,
+// ystats[1] = w * y^2, per plane, planar like the image.
+__global__ void __launch_bounds__(256, 4) ssim_target_stats_kernel(CamTable ct, Window2 win, const float* y,
+                                                                   float* ystats, long long map_stride) {
+    const CamInfo* cam;
+    long long off;
+    plane_of(ct, blockIdx.z, cam, off);
+    const int W = cam->W, H = cam->H;
+    const int ox = blockIdx.x * kO, oy = blockIdx.y * kO;
+    if (ox >= W || oy >= H) return;
+    __shared__ TileF sin;
+    __shared__ HorB sh;
+    stage2(sin, y, y, nullptr, off, W, H, ox, oy);
+    __syncthreads();
+    hpass2<kCached>(sin, sh, win);      // staged (y, y): pair (y, y^2)
+    __syncthreads();
+    const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
+    float2 m[4], unused[4];
+    float c[4];
+    vpass2<false>(sh, win, col, r0, m, unused, c);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int gx = ox + col, gy = oy + r0 + o;
+        if (gx >= W || gy >= H) continue;
+        const long long idx = off + (long long)gy * W + gx;
+        ystats[idx] = m[o].x;
+        ystats[map_stride + idx] = m[o].y;
     }
 }
 
@@ -314,8 +381,11 @@ Window make_window() {
 size_t loss_workspace_bytes(const CamTable& ct) { return sizeof(float) * 9 * (size_t)ct.pixels_total; }
 
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
-                double* loss, void* ws, size_t ws_bytes, cudaStream_t st) {
+                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats,
+                long long stats_stride) {
     LossArgs a;
+    a.ystats = target_stats;
+    a.ystride = stats_stride;
     a.x = image;
     a.y = target;
     a.dx = dL;
@@ -342,11 +412,30 @@ int loss_launch(const float* image, const float* target, const CamTable& ct, flo
     Window2 w2;
     for (int t = 0; t < 11; ++t) w2.w[t] = make_float2(w.w[t], w.w[t]);
     dim3 grid(div_up(maxW, kO), div_up(maxH, kO), 3 * ct.n);
-    ssim_fwd_kernel<<<grid, 256, 0, st>>>(ct, w2, a); count_launch();
+    if (target_stats)
+        ssim_fwd_kernel<true><<<grid, 256, 0, st>>>(ct, w2, a);
+    else
+        ssim_fwd_kernel<false><<<grid, 256, 0, st>>>(ct, w2, a);
+    count_launch();
     int rc = check_launch("ssim_fwd_kernel");
     if (rc) return rc;
     ssim_bwd_kernel<<<grid, 256, 0, st>>>(ct, w2, a); count_launch();
     return check_launch("ssim_bwd_kernel");
+}
+
+int target_stats_launch(const float* target, const CamTable& ct, float* stats, cudaStream_t st) {
+    int maxW = 0, maxH = 0;
+    for (int i = 0; i < ct.n; ++i) {
+        maxW = ct.c[i].W > maxW ? ct.c[i].W : maxW;
+        maxH = ct.c[i].H > maxH ? ct.c[i].H : maxH;
+    }
+    Window w = make_window();
+    Window2 w2;
+    for (int t = 0; t < 11; ++t) w2.w[t] = make_float2(w.w[t], w.w[t]);
+    dim3 grid(div_up(maxW, kO), div_up(maxH, kO), 3 * ct.n);
+    ssim_target_stats_kernel<<<grid, 256, 0, st>>>(ct, w2, target, stats, 3 * ct.pixels_total);
+    count_launch();
+    return check_launch("ssim_target_stats_kernel");
 }
 
 }  // namespace dass

@@ -109,6 +109,8 @@ _SIGS = {
                             C.c_float, C.c_int, _P]),
     "dass_loss_workspace": (C.c_int, [_P, C.c_int, _P]),
     "dass_loss": (C.c_int, [_P, _P, _P, C.c_int, C.c_float, _P, _P, _P, C.c_size_t, _P]),
+    "dass_loss_target_stats": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "dass_loss_cached": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_float, _P, _P, _P, C.c_size_t, _P]),
     "dass_inherit_workspace": (C.c_int, [C.c_int64, _P]),
     "dass_inherit": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                _P, _P, _P, C.c_size_t, _P]),
@@ -413,6 +415,18 @@ def dass_loss(image, target, cams, lam, dL_dimage, loss, workspace, stream=None)
     arr = cameras(cams)
     _call("dass_loss", _ptr(image, F32), _ptr(target, F32), arr, len(cams), lam, _ptr(dL_dimage, F32),
           _ptr(loss, F64), _ptr(workspace, U8), workspace.numel() if workspace is not None else 0, _stream(stream))
+
+
+def dass_loss_target_stats(target, cams, stats, stream=None):
+    arr = cameras(cams)
+    _call("dass_loss_target_stats", _ptr(target, F32), arr, len(cams), _ptr(stats, F32), _stream(stream))
+
+
+def dass_loss_cached(image, target, target_stats, cams, lam, dL_dimage, loss, workspace, stream=None):
+    arr = cameras(cams)
+    _call("dass_loss_cached", _ptr(image, F32), _ptr(target, F32), _ptr(target_stats, F32), arr, len(cams), lam,
+          _ptr(dL_dimage, F32), _ptr(loss, F64), _ptr(workspace, U8), workspace.numel() if workspace is not None else 0,
+          _stream(stream))
 
 
 def dass_inherit_workspace(n):

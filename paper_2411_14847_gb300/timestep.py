@@ -26,6 +26,25 @@ def _vp(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+class _FidelityLoss:
+    """Eq. 3 over a fixed target set: the targets' SSIM window statistics are computed once
+    (dass_loss_target_stats) and every iteration's loss reads them (dass_loss_cached)."""
+
+    def __init__(self, targets, cams, lam):
+        self.targets, self.cams, self.lam = targets, cams, lam
+        self.ws = torch.empty(max(1, D.dass_loss_workspace(cams)), dtype=torch.uint8, device=targets.device)
+        self.stats = None
+        if lam > 0:
+            self.stats = torch.empty(2 * targets.numel(), device=targets.device)
+            D.dass_loss_target_stats(targets, cams, self.stats)
+
+    def __call__(self, image, dL_dimage, loss):
+        if self.stats is None:
+            D.dass_loss(image, self.targets, self.cams, self.lam, dL_dimage, loss, self.ws)
+        else:
+            D.dass_loss_cached(image, self.targets, self.stats, self.cams, self.lam, dL_dimage, loss, self.ws)
+
+
 class ShiftStage:
     """Buffers and descriptor of one shift-stage optimisation over a fixed Gaussian set."""
 
@@ -168,7 +187,7 @@ class InheritStage:
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
         self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.fidelity = _FidelityLoss(self.targets, self.cams, self.lam)
         self.graph = None
 
     def _iteration(self, eager=False):
@@ -182,7 +201,7 @@ class InheritStage:
             torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
         fr.render_fwd()
         self.loss_buf.zero_()
-        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        self.fidelity(fr.image, self.dL_dimage, self.loss_buf)
         D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
                           fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.is_var, rec_stride=self.n)
         if self.n_var:
@@ -268,7 +287,7 @@ class DensifyStage:
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
         self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.fidelity = _FidelityLoss(self.targets, self.cams, self.lam)
         self.graph = None
 
     def _slice(self, k):
@@ -284,7 +303,7 @@ class DensifyStage:
             torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
         fr.render_fwd()
         self.loss_buf.zero_()
-        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        self.fidelity(fr.image, self.dL_dimage, self.loss_buf)
         D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
                           fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.full, rec_stride=self.n)
         if self.n_var == 0:
@@ -428,7 +447,7 @@ class FieldShiftStage:
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
         self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.loss_ws = torch.empty(max(1, D.dass_loss_workspace(self.cams)), dtype=torch.uint8, device=dev)
+        self.fidelity = _FidelityLoss(self.targets, self.cams, self.lam)
         self.graph = None
 
     def _render_g(self):
@@ -450,7 +469,7 @@ class FieldShiftStage:
             torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
         fr.render_fwd()
         self.loss_buf.zero_()
-        D.dass_loss(fr.image, self.targets, self.cams, self.lam, self.dL_dimage, self.loss_buf, self.loss_ws)
+        self.fidelity(fr.image, self.dL_dimage, self.loss_buf)
         fr.render_bwd(self.dL_dimage)
         b1, b2 = self.betas
         last = max(i for i, grp in enumerate(self.groups) if grp["n"]) if any(g_["n"] for g_ in self.groups) else -1

@@ -260,6 +260,43 @@ def test_loss_parity(dass):
         assert rel_l2(dx.cpu().numpy(), np.concatenate([g.reshape(-1).numpy() for g in ref_g])) < 1e-4
 
 
+@pytest.mark.parametrize("w,h", [(53, 37), (130, 75)])
+def test_loss_cached_target_stats_parity(dass, w, h):
+    """Target window statistics against the oracle's filter, and the loss that reads them against
+    the oracle and against the uncached loss (same planes, ragged 32 x 32 output tiles)."""
+    from paper_2411_14847_gb300 import dass as D
+    cams = synth.arc_cameras(3, 4.0, w, h)
+    rng = np.random.default_rng(1)
+    imgs = [rng.uniform(0, 1, (3, h, w)) for _ in cams]
+    tgts = [rng.uniform(0, 1, (3, h, w)) for _ in cams]
+    x = torch.tensor(np.concatenate([i.reshape(-1) for i in imgs]), dtype=torch.float32, device="cuda")
+    y = torch.tensor(np.concatenate([i.reshape(-1) for i in tgts]), dtype=torch.float32, device="cuda")
+    stats = torch.empty(2 * y.numel(), device="cuda")
+    D.dass_loss_target_stats(y, cams, stats)
+    torch.cuda.synchronize()
+    mom = [oloss.window_moments(torch.tensor(t).float().double()) for t in tgts]
+    want_m = np.concatenate([m[0].reshape(-1).numpy() for m in mom])
+    want_q = np.concatenate([m[1].reshape(-1).numpy() for m in mom])
+    got = stats.cpu().numpy()
+    assert np.abs(got[:y.numel()] - want_m).max() < 2e-6
+    assert np.abs(got[y.numel():] - want_q).max() < 2e-6
+    ws = torch.empty(D.dass_loss_workspace(cams), dtype=torch.uint8, device="cuda")
+    for lam in (0.2, 1.0):
+        ref_loss, ref_g = oloss.loss_and_image_grad([torch.tensor(i).float().double() for i in imgs],
+                                                    [torch.tensor(t).float().double() for t in tgts], lam)
+        dx, dx0 = torch.empty_like(x), torch.empty_like(x)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        loss0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        D.dass_loss_cached(x, y, stats, cams, lam, dx, loss, ws)
+        D.dass_loss(x, y, cams, lam, dx0, loss0, ws)
+        torch.cuda.synchronize()
+        want_g = np.concatenate([g.reshape(-1).numpy() for g in ref_g])
+        assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+        assert rel_l2(dx.cpu().numpy(), want_g) < 1e-4
+        assert float(loss) == pytest.approx(float(loss0), rel=1e-6)
+        assert rel_l2(dx.cpu().numpy(), dx0.cpu().numpy()) < 1e-5
+
+
 def test_backward_mean_only_for_unmasked_gaussians(dass):
     """With a per-Gaussian mask, unmasked Gaussians receive only dL/dmean2D (same values as the
     full backward); masked ones receive the full splat gradient."""
