@@ -32,12 +32,13 @@ import numpy as np
 # written, 4 depth-digit passes x 20 B (histogram read 4, scatter read 8 + write 8), pair-count
 # gather 12 B, scan 12 B, duplication reads 56 B (order, offset, record) = 220 B; per pair:
 # duplication writes 8 B, 2 tile-digit passes x 20 B, ranges 4 B = 52 B. loss per pixel-channel:
-# SSIM forward reads image and target (8 B) and writes 3 maps (12 B), backward reads the maps,
-# image and target (20 B) and writes dL/dimage (4 B) = 44 B. preprocess: the Gaussian's
+# SSIM forward reads image, target and the target's 2 cached window statistics (16 B) and writes
+# 3 maps (12 B), backward reads the maps, image and target (20 B) and writes dL/dimage (4 B)
+# = 52 B. preprocess: the Gaussian's
 # parameters once + a 48-byte record per (camera, Gaussian).
 SORT_REC_BYTES = 220
 SORT_PAIR_BYTES = 52
-LOSS_PIX_BYTES = 44
+LOSS_PIX_BYTES = 52
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -398,7 +399,10 @@ def main():
     pre_ms = timed(lambda: D.dass_preprocess(gs, cams, tile, sfr.splats), reps=5)
     loss_t = torch.zeros(1, dtype=torch.float64, device=dev)
     lws = torch.empty(D.dass_loss_workspace(cams), dtype=torch.uint8, device=dev)
-    loss_ms = timed(lambda: D.dass_loss(sfr.image, stage.targets, cams, 0.2, stage.dL_dimage, loss_t, lws), reps=5)
+    ystats = torch.empty(2 * stage.targets.numel(), device=dev)
+    D.dass_loss_target_stats(stage.targets, cams, ystats)     # once per stage, as in the step
+    loss_ms = timed(lambda: D.dass_loss_cached(sfr.image, stage.targets, ystats, cams, 0.2, stage.dL_dimage, loss_t,
+                                               lws), reps=5)
     pbwd_ms = timed(lambda: D.dass_preprocess_bwd(gs, cams, sfr.splats, sfr.splat_grads,
                                                   {"d_means": stage.d_means_dyn, "d_quats": stage.d_quats_dyn},
                                                   D.GRAD_MEANS | D.GRAD_QUATS, rows=stage.dyn_idx), reps=5)
