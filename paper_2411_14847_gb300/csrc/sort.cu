@@ -397,15 +397,30 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     }
 }
 
-// [start, end) of every tile's run in the sorted pair list (grid-stride over the pairs).
+// [start, end) of every tile's run in the sorted pair list. Grid-stride over groups of 4
+// consecutive pairs: one 16-byte load per group (the key buffer is 256-byte aligned and its
+// capacity a multiple of 64 keys, so the group never leaves the buffer; keys at or beyond n are
+// ignored) plus the keys just before and after it.
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const long long* n_dev,
                                    uint32_t* __restrict__ ranges) {
     const long long n = *n_dev;
+    const long long nq = (n + 3) / 4;
     const long long step = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
-        const uint32_t t = tiles[i];
-        if (i == 0 || tiles[i - 1] != t) ranges[2 * (long long)t] = (uint32_t)i;
-        if (i == n - 1 || tiles[i + 1] != t) ranges[2 * (long long)t + 1] = (uint32_t)(i + 1);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += step) {
+        const long long i0 = 4 * q;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(tiles + i0));
+        const uint32_t t[4] = {v.x, v.y, v.z, v.w};
+        uint32_t prev = i0 > 0 ? __ldg(tiles + i0 - 1) : 0xffffffffu;
+        const uint32_t after = i0 + 4 < n ? __ldg(tiles + i0 + 4) : 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            if (i >= n) break;
+            const uint32_t next = k < 3 ? (i + 1 < n ? t[k + 1] : 0xffffffffu) : after;
+            if (i == 0 || prev != t[k]) ranges[2 * (long long)t[k]] = (uint32_t)i;
+            if (next != t[k]) ranges[2 * (long long)t[k] + 1] = (uint32_t)(i + 1);
+            prev = t[k];
+        }
     }
 }
 
@@ -555,8 +570,8 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
         rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
     if (rc) return rc;
     // 5) tile ranges
-    tile_ranges_kernel<<<div_up(cap, 256) < 152 * 16 ? div_up(cap, 256) : 152 * 16, 256, 0, st>>>(k_out, m_dev,
-                                                                                                tile_ranges);
+    const int rq = div_up(div_up(cap, 4), 256);
+    tile_ranges_kernel<<<rq < 152 * 8 ? rq : 152 * 8, 256, 0, st>>>(k_out, m_dev, tile_ranges);
     count_launch();
     return check_launch("tile_ranges");
 }
