@@ -330,18 +330,42 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const u
     if (i < n) out[i] = counts[order[i]];
 }
 
-// Emit the pairs of each record (depth order) into its scanned slot range. A warp's 32
-// consecutive records own one contiguous output range: pairs that fall in its first kDupStage
-// slots are staged in shared memory and written by the whole warp in order (coalesced), the
-// rest (records with very large footprints) are written directly.
+// Warp-wide inclusive sum of v (all lanes take part).
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Emit the pairs of each record (depth order) into its scanned slot range. A warp owns 32
+// consecutive records and the contiguous output range their pairs fill. The work is balanced
+// over the lanes in three steps instead of each lane looping over its own record's tiles:
+//   1. each lane computes its record's footprint and tile-row range; a warp scan numbers the
+//      (record, tile row) units;
+//   2. units are dealt to the lanes 32 at a time: a lane finds its unit's record (binary search
+//      over the lanes' first unit), solves that tile row's run of tiles (the same footprint_row
+//      that counted the pairs) and a warp scan gives the run's output offset;
+//   3. output slots are dealt to the lanes in order: a lane finds its slot's unit (binary search
+//      over the staged runs) and writes (tile, record) -- consecutive lanes write consecutive
+//      slots.
+// A warp whose records have more than kDupUnits tile rows (very large footprints) writes its
+// pairs lane by lane instead.
 constexpr int kDupThreads = 256;
-constexpr int kDupStage = 256;
+constexpr int kDupUnits = 128;
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const dass_splat* __restrict__ splats, long long n_rec, CamTable ct, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ offsets, const long long* total, long long capacity,
     uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rec, long long* counters) {
-    __shared__ uint32_t s_tile[kDupThreads / 32][kDupStage];
-    __shared__ uint32_t s_rec[kDupThreads / 32][kDupStage];
+    constexpr int NW = kDupThreads / 32;
+    __shared__ Footprint s_f[kDupThreads];
+    __shared__ int s_y0[kDupThreads];
+    __shared__ int s_cam[kDupThreads];
+    __shared__ uint32_t s_upos[NW][kDupUnits];    // output offset of the unit's run (from the warp's base)
+    __shared__ uint32_t s_utile[NW][kDupUnits];   // first tile of the run
+    __shared__ uint32_t s_urec[NW][kDupUnits];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long m = *total;
@@ -359,40 +383,87 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
         rec = order[k];
         pos = offsets[k];
     }
-    // output range of the warp: [first record's offset, next warp's first offset or the total)
     const long long wbase = __shfl_sync(0xffffffffu, pos, 0);
     const long long wend = k0 + 32 < n_rec ? (long long)offsets[k0 + 32] : m;
+    // 1. footprint and tile rows of this lane's record
     Footprint f;
     float depth;
+    int ci = 0, y0 = 0, y1 = -1;
     if (active && record_footprint(splats, rec, f, depth)) {
-        const int ci = (int)(rec / ct.rec_stride);
+        ci = (int)(rec / ct.rec_stride);
         const CamInfo& cam = ct.c[ci];
-        int x0, x1, y0, y1;
+        int x0, x1;
         footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
-        for (int y = y0; y <= y1; ++y) {
-            int r0, r1;
-            if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
-            for (int x = r0; x <= r1; ++x) {
-                const uint32_t tile = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
-                const long long local = pos - wbase;
-                if (local < kDupStage) {
-                    s_tile[warp][local] = tile;
-                    s_rec[warp][local] = rec;
-                } else if (pos < capacity) {
-                    pair_tile[pos] = tile;
-                    pair_rec[pos] = rec;
-                }
-                ++pos;
+    }
+    const uint32_t nrows = y1 >= y0 ? (uint32_t)(y1 - y0 + 1) : 0u;
+    const uint32_t rows_incl = warp_inclusive_sum(nrows, lane);
+    const uint32_t ubase = rows_incl - nrows;
+    const uint32_t U = __shfl_sync(0xffffffffu, rows_incl, 31);
+    if (U > (uint32_t)kDupUnits) {                    // warp-uniform: lane-by-lane emission
+        if (nrows) {
+            const CamInfo& cam = ct.c[ci];
+            for (int y = y0; y <= y1; ++y) {
+                int r0, r1;
+                if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
+                for (int x = r0; x <= r1; ++x, ++pos)
+                    if (pos < capacity && pos < wend) {
+                        pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
+                        pair_rec[pos] = rec;
+                    }
             }
         }
+        return;
+    }
+    s_f[threadIdx.x] = f;
+    s_y0[threadIdx.x] = y0;
+    s_cam[threadIdx.x] = ci;
+    __syncwarp();
+    // 2. the tile runs of the units, 32 at a time, in (record, row) order
+    uint32_t carry = 0;
+    for (uint32_t u0 = 0; u0 < U; u0 += 32) {
+        const uint32_t u = u0 + lane;
+        int owner = 0;                                  // last lane whose first unit is <= u
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t b = __shfl_sync(0xffffffffu, ubase, owner + step);
+            if (b <= u) owner += step;
+        }
+        const uint32_t orow = __shfl_sync(0xffffffffu, ubase, owner);
+        const uint32_t orec = __shfl_sync(0xffffffffu, rec, owner);
+        uint32_t len = 0, tile0 = 0;
+        if (u < U) {
+            const int src = (warp << 5) + owner;
+            const CamInfo& cam = ct.c[s_cam[src]];
+            const int y = s_y0[src] + (int)(u - orow);
+            int r0, r1;
+            if (footprint_row(s_f[src], y, ct.tile, cam.tiles_x, r0, r1)) {
+                len = (uint32_t)(r1 - r0 + 1);
+                tile0 = (uint32_t)(cam.tile_base + y * cam.tiles_x + r0);
+            }
+        }
+        const uint32_t incl = warp_inclusive_sum(len, lane);
+        if (u < U) {
+            s_upos[warp][u] = carry + incl - len;
+            s_utile[warp][u] = tile0;
+            s_urec[warp][u] = orec;
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
-    const long long staged = wend - wbase < kDupStage ? wend - wbase : kDupStage;
-    for (int i = lane; i < staged; i += 32) {
+    // 3. the pairs, slot by slot (the counted total bounds the warp's range)
+    const long long span = wend - wbase;
+    const uint32_t npairs = (long long)carry < span ? carry : (uint32_t)span;
+    for (uint32_t i = lane; i < npairs; i += 32) {
+        int lo = 0;                                     // last unit whose run starts at or before i
+#pragma unroll
+        for (int step = kDupUnits / 2; step > 0; step >>= 1) {
+            const int c = lo + step;
+            if (c < (int)U && s_upos[warp][c] <= i) lo = c;
+        }
         const long long p = wbase + i;
         if (p < capacity) {
-            pair_tile[p] = s_tile[warp][i];
-            pair_rec[p] = s_rec[warp][i];
+            pair_tile[p] = s_utile[warp][lo] + (i - s_upos[warp][lo]);
+            pair_rec[p] = s_urec[warp][lo];
         }
     }
 }
