@@ -23,7 +23,9 @@ namespace {
 //   P3 = (r, r, g, g)         P4 = (blue, blue, a, a)
 // with a' = a kNegHalfLog2e, b2' = 2 b kNegHalfLog2e, c' = c kNegHalfLog2e (see splat_gauss);
 // F = (a, b, c, k2) is the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
-template <int NG, int BATCH>
+// NEG (forward only): o, r, g and blue are staged negated, so that the forward works with -alpha
+// and forms T - alpha T with one packed FMA (the negations are exact: alpha is unchanged).
+template <int NG, int BATCH, bool NEG = false>
 __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splats, uint32_t rec, int i,
                                             float4 (&sP)[NG][BATCH], float4 (&sF)[BATCH]) {
     const float4* sp = reinterpret_cast<const float4*>(splats + rec);
@@ -32,11 +34,12 @@ __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splat
     const float bl = __ldg(reinterpret_cast<const float*>(sp + 2));
     const float ap = __fmul_rn(s0.z, kNegHalfLog2e), b2p = __fmul_rn(2.f * s0.w, kNegHalfLog2e),
                 cp = __fmul_rn(s1.x, kNegHalfLog2e);
+    const float sg = NEG ? -1.f : 1.f;
     sP[0][i] = make_float4(-s0.x, -s0.x, -s0.y, -s0.y);
     sP[1][i] = make_float4(ap, ap, b2p, b2p);
-    sP[2][i] = make_float4(cp, cp, s1.y, s1.y);
-    sP[3][i] = make_float4(s1.z, s1.z, s1.w, s1.w);
-    sP[4][i] = make_float4(bl, bl, s0.z, s0.z);
+    sP[2][i] = make_float4(cp, cp, sg * s1.y, sg * s1.y);
+    sP[3][i] = make_float4(sg * s1.z, sg * s1.z, sg * s1.w, sg * s1.w);
+    sP[4][i] = make_float4(sg * bl, sg * bl, s0.z, s0.z);
     sF[i] = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
 }
 
@@ -111,18 +114,20 @@ struct PixFwd2 {
 };
 
 // Front-to-back step of staged entry P0..P4 (list position pos) for both pixels: skip alpha <
-// 1/255, stop before T (1 - alpha) < 1e-4, else blend. A pixel that skips or is done gets alpha
-// = 0 in the packed blend, which leaves its colour and transmittance exactly unchanged.
+// 1/255, stop before T (1 - alpha) < 1e-4, else blend. The entry is staged negated (o, r, g,
+// blue), so the step carries na = -alpha and forms T - alpha T = fma(na, T, T) in one rounding. A
+// pixel that skips or is done gets alpha = 0 in the packed blend, which leaves its colour and
+// transmittance exactly unchanged.
 template <bool COUNT>
 __device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 dx, const float4 P0, const float4 P1,
-                                              const float4 P2, const float4 P3, float2 blue, bool full) {
+                                              const float4 P2, const float4 P3, float2 nblue, bool full) {
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
-    const float2 oG = __fmul2_rn(hi2(P2), G);
-    float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
-    const float2 test = __fmul2_rn(p.T, one_minus2(alpha));
-    bool ok0 = !p.done0 && !(alpha.x < kAlphaMin);
-    bool ok1 = !p.done1 && !(alpha.y < kAlphaMin);
+    const float2 noG = __fmul2_rn(hi2(P2), G);                 // -o G
+    float2 na = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
+    const float2 test = __ffma2_rn(na, p.T, p.T);
+    bool ok0 = !p.done0 && !(na.x > -kAlphaMin);
+    bool ok1 = !p.done1 && !(na.y > -kAlphaMin);
     if (COUNT) p.n_eval += (unsigned long long)(!p.done0) + (unsigned long long)(!p.done1);
     const bool stop0 = ok0 && test.x < kTStop, stop1 = ok1 && test.y < kTStop;
     p.done0 = p.done0 || stop0;
@@ -134,13 +139,13 @@ __device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 dx, co
         p.n_add += k;
         p.n_full += full ? k : 0ull;
     }
-    alpha.x = ok0 ? alpha.x : 0.f;
-    alpha.y = ok1 ? alpha.y : 0.f;
-    const float2 w = __fmul2_rn(alpha, p.T);
-    p.C0 = __ffma2_rn(lo2(P3), w, p.C0);
-    p.C1 = __ffma2_rn(hi2(P3), w, p.C1);
-    p.C2 = __ffma2_rn(blue, w, p.C2);
-    p.T = __fmul2_rn(p.T, one_minus2(alpha));   // = test where the pixel blends, T where alpha = 0
+    na.x = ok0 ? na.x : 0.f;
+    na.y = ok1 ? na.y : 0.f;
+    const float2 nw = __fmul2_rn(na, p.T);                     // -alpha T
+    p.C0 = __ffma2_rn(lo2(P3), nw, p.C0);                      // (-r)(-alpha T)
+    p.C1 = __ffma2_rn(hi2(P3), nw, p.C1);
+    p.C2 = __ffma2_rn(nblue, nw, p.C2);
+    p.T = __ffma2_rn(na, p.T, p.T);     // = test where the pixel blends, T where alpha = 0
     p.last0 = ok0 ? pos : p.last0;
     p.last1 = ok1 ? pos : p.last1;
 }
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_spl
         const int cnt = min((uint32_t)BATCH, end - base);
         for (int i = tid; i < cnt; i += NT) {
             const uint32_t rec = pair_rec[base + i];
-            stage_splat<5, BATCH>(splats, rec, i, sP, sF);
+            stage_splat<5, BATCH, true>(splats, rec, i, sP, sF);
             if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
         }
         __syncthreads();
@@ -233,11 +238,11 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_spl
             if ((t & 3) == 0 && __all_sync(0xffffffffu, all_done())) break;
             const int j = sList[warp][t];
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
-            const float2 blue = lo2(sP[4][j]);
+            const float2 nblue = lo2(sP[4][j]);
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), dx, P0, P1, P2, P3, blue, full);
+            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), dx, P0, P1, P2, P3, nblue, full);
         }
     }
 #pragma unroll
