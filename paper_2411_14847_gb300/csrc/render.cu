@@ -376,8 +376,9 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     const float2 Tj = __fmul2_rn(p.T, make_float2(val0 ? rcp_approx(om.x) : 1.f, val1 ? rcp_approx(om.y) : 1.f));
     const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
-    const float2 dLda = __fmul2_rn(Tj, sub2(gc, p.S));
-    p.S = __ffma2_rn(om, p.S, __fmul2_rn(am, gc));
+    const float2 d = sub2(gc, p.S);
+    const float2 dLda = __fmul2_rn(Tj, d);
+    p.S = __ffma2_rn(am, d, p.S);       // alpha gc + (1 - alpha) S = S + alpha (gc - S)
     p.T = Tj;
     // the clamp alpha = 0.99 has zero derivative
     const bool cm0 = val0 && oG.x < kAlphaMax, cm1 = val1 && oG.y < kAlphaMax;
