@@ -96,12 +96,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // Explicit round-to-nearest intrinsics fix the operation sequence (no contraction choices
 // by the compiler), so the same pixel/splat pair yields the same alpha in every kernel.
+// q' is evaluated as dy (c' dy + B) + A with the column terms B = b2' dx and A = (a' dx) dx,
+// which every pixel of a column shares (the compositing kernels compute them once per entry).
 __device__ __forceinline__ float splat_gauss(float ap, float b2p, float cp, float dx, float dy) {
-    float t = __fmul_rn(b2p, dy);
-    float s = __fmaf_rn(ap, dx, t);          // a' dx + b2' dy
-    float cdy = __fmul_rn(cp, dy);
-    float q = __fmaf_rn(dx, s, __fmul_rn(cdy, dy));
-    return ex2_approx(q);
+    const float B = __fmul_rn(b2p, dx);
+    const float A = __fmul_rn(__fmul_rn(ap, dx), dx);
+    return ex2_approx(__fmaf_rn(dy, __fmaf_rn(cp, dy, B), A));
 }
 
 __device__ __forceinline__ float splat_alpha(float o, float G) {
@@ -115,11 +115,13 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, one rou
 }
 __device__ __forceinline__ float2 one_minus2(float2 a) { return sub2(make_float2(1.f, 1.f), a); }
 
-__device__ __forceinline__ float2 splat_gauss2(float2 ap, float2 b2p, float2 cp, float2 dx, float2 dy) {
-    const float2 t = __fmul2_rn(b2p, dy);
-    const float2 s = __ffma2_rn(ap, dx, t);
-    const float2 cdy = __fmul2_rn(cp, dy);
-    const float2 q = __ffma2_rn(dx, s, __fmul2_rn(cdy, dy));
+// Column terms (A, B) of splat_gauss for a packed column pair dx.
+__device__ __forceinline__ void splat_column2(float2 ap, float2 b2p, float2 dx, float2& A, float2& B) {
+    B = __fmul2_rn(b2p, dx);
+    A = __fmul2_rn(__fmul2_rn(ap, dx), dx);
+}
+__device__ __forceinline__ float2 splat_gauss2(float2 cp, float2 dy, float2 A, float2 B) {
+    const float2 q = __ffma2_rn(dy, __ffma2_rn(cp, dy, B), A);
     return make_float2(ex2_approx(q.x), ex2_approx(q.y));
 }
 

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kFeatThreads) render_features_kernel(
             const float dx = __fsub_rn(fx, A.x), dy = __fsub_rn(fy, A.y);
             const float alpha = splat_alpha(B.y, splat_gauss(A.z, A.w, B.x, dx, dy));
             if (alpha < kAlphaMin) continue;
-            const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            const float test = __fmaf_rn(-alpha, T, T);     // T - alpha T, as the colour forward
             if (test < kTStop) {
                 done = true;
                 break;

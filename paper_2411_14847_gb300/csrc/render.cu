@@ -119,10 +119,10 @@ struct PixFwd2 {
 // pixel that skips or is done gets alpha = 0 in the packed blend, which leaves its colour and
 // transmittance exactly unchanged.
 template <bool COUNT>
-__device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 dx, const float4 P0, const float4 P1,
+__device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 A, float2 B, const float4 P0,
                                               const float4 P2, const float4 P3, float2 nblue, bool full) {
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
-    const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
+    const float2 G = splat_gauss2(lo2(P2), dy, A, B);
     const float2 noG = __fmul2_rn(hi2(P2), G);                 // -o G
     float2 na = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
     const float2 test = __ffma2_rn(na, p.T, p.T);
@@ -240,9 +240,11 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_spl
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
             const float2 nblue = lo2(sP[4][j]);
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
+            float2 A, B;
+            splat_column2(lo2(P1), hi2(P1), dx, A, B);
             const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), dx, P0, P1, P2, P3, nblue, full);
+            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), A, B, P0, P2, P3, nblue, full);
         }
     }
 #pragma unroll
@@ -361,19 +363,21 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 // whenever any lane needs it, and the divergent exits cost more than the masked work; measured
 // 5.95 -> 5.31 ms on the 300k x 20-view backward). Returns whether either pixel took part.
 template <bool FULL, int NT>
-__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, const float4 P0,
-                                              const float4 P1, const float4 P2, const float4 P3, const float4 P4,
+__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, float2 A, float2 B,
+                                              const float4 P0, const float4 P2, const float4 P3, const float4 P4,
                                               float2* vm, float2* vf) {
     bool val0 = pos <= p.last0, val1 = pos <= p.last1;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
-    const float2 G = splat_gauss2(lo2(P1), hi2(P1), lo2(P2), dx, dy);
+    const float2 G = splat_gauss2(lo2(P2), dy, A, B);
     const float2 oG = __fmul2_rn(hi2(P2), G);
     const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
     val0 = val0 && !(alpha.x < kAlphaMin);
     val1 = val1 && !(alpha.y < kAlphaMin);
     const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
     const float2 om = one_minus2(am);
-    const float2 Tj = __fmul2_rn(p.T, make_float2(val0 ? rcp_approx(om.x) : 1.f, val1 ? rcp_approx(om.y) : 1.f));
+    // a pixel that takes no part has om = 1 exactly, and rcp.approx(1) = 1 exactly (checked on
+    // sm_103), so its T passes through unchanged without a select
+    const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
     const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
     const float2 d = sub2(gc, p.S);
@@ -491,6 +495,8 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
             const int pos = (int)(lo + j);
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
+            float2 A, B;
+            splat_column2(lo2(P1), hi2(P1), dx, A, B);
             bool contrib = false;
             float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (sFull[j]) {          // warp-uniform: the same Gaussian for every lane
@@ -499,7 +505,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                 for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
+                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
                                                        vm, vf);
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     float r[8] = {vm[0].x + vm[0].y, vm[1].x + vm[1].y, vf[0].x + vf[0].y, vf[1].x + vf[1].y,
@@ -518,7 +524,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
             } else {
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, P0, P1, P2, P3, P4,
+                    contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
                                                         vm, nullptr);
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
