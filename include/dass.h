@@ -55,7 +55,9 @@ typedef enum dass_status {
     DASS_ERR_UNSUPPORTED = -6
 } dass_status;
 
-/* Camera of App. A.1's projection: world->camera viewmat, pinhole intrinsics. 88 bytes. */
+/* Camera of App. A.1's projection: world->camera viewmat, pinhole intrinsics. 88 bytes.
+ * width, height > 0 with (width + 16) * (height + 16) < 2^31 (pixel offsets within a plane
+ * are 32-bit); every entry taking cameras returns DASS_ERR_INVALID_ARG otherwise. */
 typedef struct dass_camera {
     float viewmat[16];
     float fx, fy, cx, cy;

@@ -130,6 +130,7 @@ bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec
     for (int i = 0; i < n_cams; ++i) {
         const dass_camera& c = cams[i];
         if (c.width <= 0 || c.height <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f)) return false;
+        if ((long long)(c.width + 16) * (c.height + 16) >= (1ll << 31)) return false;   // 32-bit pixel offsets
         CamInfo& ci = out->c[i];
         for (int r = 0; r < 3; ++r) {
             for (int k = 0; k < 3; ++k) ci.R[3 * r + k] = c.viewmat[4 * r + k];

@@ -174,33 +174,45 @@ __device__ __forceinline__ void vpass2(const Hor& h, const Window2& win, int col
     }
 }
 
-// Stage the 42 x 42 window of the pair (p0, p1) and the scalar plane ps (if any) with zeros
-// outside the image. Each thread issues all of its global loads before its first shared store,
-// so the block waits for one memory latency, not one per element.
+// Stage the 42 x 42 window of the pair (p0, p1) and the scalar plane ps (if any) of the plane at
+// element offset off, with zeros outside the image. Each thread issues all of its global loads
+// before its first shared store, so the block waits for one memory latency, not one per element.
+// A thread's elements are threadIdx.x + 256 e; their (row, column) advance by (6, 4) per step
+// (256 = 6 * 42 + 4), and the plane offsets are 32-bit (a plane has fewer than 2^31 pixels).
 template <class Tile>
 __device__ __forceinline__ void stage2(Tile& dst, const float* p0, const float* p1, const float* ps, long long off,
                                        int W, int H, int ox, int oy) {
     constexpr int kPer = (kI * kI + 255) / 256;
     constexpr bool kScalar = std::is_same_v<Tile, TileB>;
+    static_assert(256 / kI == 6 && 256 % kI == 4, "element stepping assumes a 42-wide window");
+    const float* __restrict__ b0 = p0 + off;
+    const float* __restrict__ b1 = p1 + off;
+    const float* __restrict__ bs = kScalar ? ps + off : nullptr;
     float2 v[kPer];
     float sv[kPer];
+    int so[kPer];
+    int r = threadIdx.x / kI, c = threadIdx.x % kI;
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
-        const int i = threadIdx.x + e * 256;
-        const int r = i / kI, c = i % kI;
         const int gx = ox + c - kR, gy = oy + r - kR;
-        const bool in = i < kI * kI && gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const long long idx = off + (long long)gy * W + gx;
-        v[e] = in ? make_float2(__ldg(p0 + idx), __ldg(p1 + idx)) : make_float2(0.f, 0.f);
-        if constexpr (kScalar) sv[e] = in ? __ldg(ps + idx) : 0.f;
+        const bool in = r < kI && (unsigned)gx < (unsigned)W && (unsigned)gy < (unsigned)H;
+        const int q = gy * W + gx;
+        v[e] = in ? make_float2(__ldg(b0 + q), __ldg(b1 + q)) : make_float2(0.f, 0.f);
+        if constexpr (kScalar) sv[e] = in ? __ldg(bs + q) : 0.f;
+        so[e] = r < kI ? r * kIP + c : -1;
+        c += 4;
+        r += 6;
+        if (c >= kI) {
+            c -= kI;
+            ++r;
+        }
     }
+    float2* dp = &dst.p[0][0];
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
-        const int i = threadIdx.x + e * 256;
-        if (i < kI * kI) {
-            const int r = i / kI, c = i % kI;
-            dst.p[r][c] = v[e];
-            if constexpr (kScalar) dst.s[r][c] = sv[e];
+        if (so[e] >= 0) {
+            dp[so[e]] = v[e];
+            if constexpr (kScalar) (&dst.s[0][0])[so[e]] = sv[e];
         }
     }
 }
@@ -221,13 +233,15 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
     const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
     float ym[4], y2[4];
     if constexpr (CACHED) {      // requested before the stencil work
+        const float* __restrict__ m1 = a.ystats + off;
+        const float* __restrict__ m2 = a.ystats + a.ystride + off;
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int gx = ox + col, gy = oy + r0 + o;
             const bool in = gx < W && gy < H;
-            const long long idx = off + (long long)gy * W + gx;
-            ym[o] = in ? __ldg(a.ystats + idx) : 0.f;
-            y2[o] = in ? __ldg(a.ystats + a.ystride + idx) : 0.f;
+            const int q = gy * W + gx;
+            ym[o] = in ? __ldg(m1 + q) : 0.f;
+            y2[o] = in ? __ldg(m2 + q) : 0.f;
         }
     }
     stage2(sin, a.x, a.y, nullptr, off, W, H, ox, oy);
@@ -250,6 +264,9 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
         vpass2<true>(sh, win, col, r0, m, e, exy);
     }
     const float inv_n = a.inv_cams / (3.f * (float)W * (float)H);
+    float* __restrict__ g1 = a.g + off;
+    float* __restrict__ g2 = a.g + a.map_stride + off;
+    float* __restrict__ g3 = a.g + 2 * a.map_stride + off;
     float contrib = 0.f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -259,15 +276,15 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
         const float vx = e[o].x - mx * mx, vy = e[o].y - my * my, cxy = exy[o] - mx * my;
         const float A1 = 2.f * mx * my + kC1, B1 = mx * mx + my * my + kC1;
         const float A2 = 2.f * cxy + kC2, B2 = vx + vy + kC2;
-        const float inv = 1.f / (B1 * B2);           // 1/B1 = B2 inv, 1/B2 = B1 inv
+        const float inv = __fdividef(1.f, B1 * B2);  // 1/B1 = B2 inv, 1/B2 = B1 inv (B1 B2 >= C1 C2 > 0)
         const float S = A1 * A2 * inv;
         const float dmu = 2.f * inv * (my * A2 - mx * S * B2);
         const float dvx = -S * B1 * inv;
         const float dcxy = 2.f * A1 * inv;
-        const long long idx = off + (long long)gy * W + gx;
-        a.g[idx] = dmu - 2.f * mx * dvx - my * dcxy;
-        a.g[a.map_stride + idx] = dvx;
-        a.g[2 * a.map_stride + idx] = dcxy;
+        const int q = gy * W + gx;
+        g1[q] = dmu - 2.f * mx * dvx - my * dcxy;
+        g2[q] = dvx;
+        g3[q] = dcxy;
         const float2 c = sin.p[r0 + o + kR][col + kR];
         contrib += inv_n * ((1.f - a.lambda) * fabsf(c.x - c.y) - a.lambda * S);
     }
@@ -289,13 +306,15 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
     const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
     // the image and target values of the epilogue are requested before the stencil work
     float xv[4], yv[4];
+    const float* __restrict__ xb = a.x + off;
+    const float* __restrict__ yb = a.y + off;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const int gx = ox + col, gy = oy + r0 + o;
         const bool in = gx < W && gy < H;
-        const long long idx = off + (long long)gy * W + gx;
-        xv[o] = in ? a.x[idx] : 0.f;
-        yv[o] = in ? a.y[idx] : 0.f;
+        const int q = gy * W + gx;
+        xv[o] = in ? __ldg(xb + q) : 0.f;
+        yv[o] = in ? __ldg(yb + q) : 0.f;
     }
     stage2(sin, a.g, a.g + a.map_stride, a.g + 2 * a.map_stride, off, W, H, ox, oy);
     __syncthreads();
@@ -305,15 +324,15 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
     float c3[4];
     vpass2<false>(sh, win, col, r0, c12, unused, c3);
     const float inv_n = a.inv_cams / (3.f * (float)W * (float)H);
+    float* __restrict__ dxb = a.dx + off;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const int gx = ox + col, gy = oy + r0 + o;
         if (gx >= W || gy >= H) continue;
-        const long long idx = off + (long long)gy * W + gx;
         const float dS = c12[o].x + 2.f * xv[o] * c12[o].y + yv[o] * c3[o];
         const float d = xv[o] - yv[o];
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        a.dx[idx] = inv_n * ((1.f - a.lambda) * sgn - a.lambda * dS);
+        dxb[gy * W + gx] = inv_n * ((1.f - a.lambda) * sgn - a.lambda * dS);
     }
 }
 
@@ -337,13 +356,15 @@ __global__ void __launch_bounds__(256, 4) ssim_target_stats_kernel(CamTable ct, 
     float2 m[4], unused[4];
     float c[4];
     vpass2<false>(sh, win, col, r0, m, unused, c);
+    float* __restrict__ s1 = ystats + off;
+    float* __restrict__ s2 = ystats + map_stride + off;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const int gx = ox + col, gy = oy + r0 + o;
         if (gx >= W || gy >= H) continue;
-        const long long idx = off + (long long)gy * W + gx;
-        ystats[idx] = m[o].x;
-        ystats[map_stride + idx] = m[o].y;
+        const int q = gy * W + gx;
+        s1[q] = m[o].x;
+        s2[q] = m[o].y;
     }
 }
 
