@@ -355,7 +355,8 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 // Reverse step of staged entry P0..P4 (list position pos) for both pixels of the pair; adds the
 // entry's gradient contributions: vm[0..1] (packed, both pixels) the sums of dx and dy times
 // dL/d(power) -- dL/d(u, v) = (a X + b Y, b X + c Y) of those sums X, Y, applied once per
-// Gaussian after the reduction since the conic is the Gaussian's; if FULL also vf[0..2]
+// staged Gaussian when the CTA's block sums are flushed, since the conic is the Gaussian's; if
+// FULL also vf[0..2]
 // the sums of dx^2, dx dy, dy^2 times dL/d(power) (dL/d(a, b, c) after scaling by -1/2, -1, -1/2),
 // vf[3] dL/do and vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
 // 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. The step is
@@ -512,12 +513,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                                   vf[2].x + vf[2].y, vf[3].x + vf[3].y, vf[4].x + vf[4].y, vf[5].x + vf[5].y};
                     float s = warp_reduce8(r, lane);
                     const float e = warp_sum(vf[6].x + vf[6].y);
-                    // lane 0 holds X (index 0), lane 4 holds Y (index 1): dL/du = a X + b Y, dL/dv = b X + c Y
-                    const float other = __shfl_xor_sync(0xffffffffu, s, 4);
-                    if (gidx < 2) {
-                        const float4 F = sF[j];
-                        s = gidx == 0 ? F.x * s + F.y * other : F.y * other + F.z * s;
-                    }
+                    // lanes 0 and 4 hold the moments X and Y (the conic is applied at the flush)
                     if ((lane & 3) == 0) atomicAdd(&sG[j][gidx], s * gscale);
                     if (lane == 1) atomicAdd(&sG[j][8], e);
                 }
@@ -527,20 +523,18 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                     contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
                                                         vm, nullptr);
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                    // lane 0 holds X, lane 16 holds Y: dL/du = a X + b Y, dL/dv = b X + c Y
-                    const float other = __shfl_xor_sync(0xffffffffu, r, 16);
-                    if ((lane & 15) == 0) {
-                        const float4 F = sF[j];
-                        r = lane == 0 ? F.x * r + F.y * other : F.y * other + F.z * r;
-                        atomicAdd(&sG[j][lane >> 4], r);
-                    }
+                    const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
+                    // lane 0 holds X, lane 16 holds Y (the conic is applied at the flush)
+                    if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
                 }
             }
         }
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            float4 a = make_float4(sG[i][0], sG[i][1], sG[i][2], sG[i][3]);
+            // block sums X = sum dpow dx, Y = sum dpow dy -> dL/du = a X + b Y, dL/dv = b X + c Y
+            const float4 F = sF[i];
+            const float X = sG[i][0], Y = sG[i][1];
+            float4 a = make_float4(F.x * X + F.y * Y, F.y * X + F.z * Y, sG[i][2], sG[i][3]);
             float4 b = make_float4(sG[i][4], sG[i][5], sG[i][6], sG[i][7]);
             float c = sG[i][8];
             float4* dst = reinterpret_cast<float4*>(gsplat + sRec[i]);
