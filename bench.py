@@ -59,8 +59,9 @@ FLOP_BWD_ADD = 56
 # Backward of a pair whose Gaussian only needs dL/dmean2D (static in the shift stage): the same
 # terms up to the dpow dx, dpow dy sums (29) and 2 reduction adds = 31 flop.
 FLOP_BWD_MEAN_ADD = 31
-# DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture scaled to 20
-# cameras, profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
+# DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture of the
+# current kernel, 264.3 MB for 8.47M pairs, scaled by pairs to the 28.34M pairs of 20 cameras,
+# profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
 RENDER_BWD_TRAFFIC = 8.80e8
 
 
