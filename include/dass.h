@@ -297,13 +297,15 @@ int dass_field_bwd(const dass_field* field, int64_t n_rows, const int32_t* rows,
 /* Identity-feature rendering (Sec. 3.3: Gaussian Grouping object features, rendered like colour
  * to query object IDs in any view): the lists, alpha, skip and stop rules of dass_render_fwd
  * (no background) compositing per-Gaussian feature vectors features[g][n_features], g = record
- * % rec_stride. n_features in {4, 8, 16, 32}. out: pixel-major [pixels_total][n_features]. */
+ * % rec_stride (< 2^31). n_features in {4, 8, 16, 32}; features 16-byte aligned (its rows are read
+ * as float4). out: pixel-major [pixels_total][n_features]. */
 int dass_render_features(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                          const dass_camera* cams /* host */, int n_cams, int tile, const float* features,
                          int n_features, int64_t rec_stride, float* out, void* stream);
 
 /* Object IDs of feature rows (the linear classifier of Gaussian Grouping):
- * ids[i] = argmax_k (W x_i + b)_k over n_classes (ties to the lower k), W [n_classes][n_features]. */
+ * ids[i] = argmax_k (W x_i + b)_k over n_classes (ties to the lower k), W [n_classes][n_features].
+ * x and W must be 16-byte aligned (DASS_ERR_INVALID_ARG otherwise); n_features in {4, 8, 16, 32}. */
 int dass_object_ids(const float* x, int64_t n, int n_features, const float* W, const float* b, int n_classes,
                     int32_t* ids, void* stream);
 
@@ -314,7 +316,7 @@ int dass_dynamic_objects(const int32_t* ids, const uint8_t* dyn_area, int64_t n,
                          uint32_t min_pixels, uint8_t* obj_mask, uint32_t* hist, void* stream);
 
 /* Per-Gaussian dynamics mask (Sec. 3.3): dyn_mask[g] = obj_mask[argmax_k (W f_g + b)_k] for the
- * Gaussians' own identity features f_g. */
+ * Gaussians' own identity features f_g (features and W 16-byte aligned, as in dass_object_ids). */
 int dass_dynamic_gaussians(const float* features, int64_t n, int n_features, const float* W, const float* b,
                            int n_classes, const uint8_t* obj_mask, uint8_t* dyn_mask, void* stream);
 

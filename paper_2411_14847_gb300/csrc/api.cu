@@ -420,6 +420,7 @@ DASS_API int dass_render_features(const dass_splat* splats, const uint32_t* pair
                                   const dass_camera* cams, int n_cams, int tile, const float* features,
                                   int n_features, int64_t rec_stride, float* out, void* stream) {
     if (rec_stride <= 0 || !features || !out || !pair_rec || !tile_ranges || !splats) return DASS_ERR_INVALID_ARG;
+    if (rec_stride >= (1ll << 31) || reinterpret_cast<uintptr_t>(features) % 16) return DASS_ERR_INVALID_ARG;
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
     return render_features_launch(splats, pair_rec, tile_ranges, ct, features, n_features, rec_stride, out,
@@ -429,6 +430,7 @@ DASS_API int dass_render_features(const dass_splat* splats, const uint32_t* pair
 DASS_API int dass_object_ids(const float* x, int64_t n, int n_features, const float* W, const float* b,
                              int n_classes, int32_t* ids, void* stream) {
     if (n < 0 || n_classes < 1 || (n > 0 && (!x || !W || !b || !ids))) return DASS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(W)) % 16) return DASS_ERR_INVALID_ARG;  // float4 rows
     return object_ids_launch(x, n, n_features, W, b, n_classes, ids, as_stream(stream));
 }
 
@@ -443,6 +445,8 @@ DASS_API int dass_dynamic_gaussians(const float* features, int64_t n, int n_feat
                                     void* stream) {
     if (n < 0 || n_classes < 1 || (n > 0 && (!features || !W || !b || !obj_mask || !dyn_mask)))
         return DASS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(features) | reinterpret_cast<uintptr_t>(W)) % 16)
+        return DASS_ERR_INVALID_ARG;   // rows are read as float4
     return dynamic_gaussians_launch(features, n, n_features, W, b, n_classes, obj_mask, dyn_mask, as_stream(stream));
 }
 

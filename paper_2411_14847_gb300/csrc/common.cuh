@@ -125,6 +125,32 @@ __device__ __forceinline__ float2 splat_gauss2(float2 cp, float2 dy, float2 A, f
     return make_float2(ex2_approx(q.x), ex2_approx(q.y));
 }
 
+// Does the footprint F = (a, b, c, k2) of a splat centred at (u, v) = -(nu, nv) reach the
+// rectangle of pixel centres [bx, bx + wm1] x [by, by + hm1]? Ellipse-rectangle test: the quadratic
+// form is evaluated at a point of each edge facing the centre (the clamped 1-D minimiser, computed
+// with a fast division); any point of the rectangle gives an upper bound of its minimum, so a
+// splat is culled only if every pixel of the rectangle is outside its footprint (up to k2's
+// slack). Used to cull staged splats per warp block in the compositing kernels.
+__device__ __forceinline__ bool footprint_reaches_rect(float nu, float nv, const float4 F, float bx, float by,
+                                                       float wm1, float hm1) {
+    if (F.w < 0.f) return false;
+    const float x0 = bx + nu, x1 = (bx + wm1) + nu, y0 = by + nv, y1 = (by + hm1) + nv;
+    const bool in_x = x0 <= 0.f && x1 >= 0.f, in_y = y0 <= 0.f && y1 >= 0.f;
+    if (in_x && in_y) return true;
+    float qmin = 3.4e38f;
+    if (!in_x) {
+        const float X = x0 > 0.f ? x0 : x1;
+        const float dy = fminf(fmaxf(__fdividef(-F.y * X, F.z), y0), y1);
+        qmin = fminf(qmin, F.x * X * X + 2.f * F.y * X * dy + F.z * dy * dy);
+    }
+    if (!in_y) {
+        const float Y = y0 > 0.f ? y0 : y1;
+        const float dx = fminf(fmaxf(__fdividef(-F.y * Y, F.x), x0), x1);
+        qmin = fminf(qmin, F.x * dx * dx + 2.f * F.y * dx * Y + F.z * Y * Y);
+    }
+    return qmin <= F.w;
+}
+
 // ----------------------------------------------------------------- real SH (degree <= 3)
 
 // Real spherical harmonics without the Condon-Shortley phase, k = l*l + l + m. Constants are

@@ -58,31 +58,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Does the footprint F of a staged entry centred at (u, v) = -(nu, nv) reach the warp's 8 x BH
-// block whose first pixel centre is (bx, by)? Ellipse-rectangle test: the quadratic form is
-// evaluated at a point of each edge facing the centre (the clamped 1-D minimiser, computed with
-// a fast division); any point of the rectangle gives an upper bound of its minimum, so a
-// Gaussian is culled only if every pixel of the block is outside its footprint (up to k2's slack).
-template <int BH>
-__device__ __forceinline__ bool reaches_block(float nu, float nv, const float4 F, float bx, float by) {
-    if (F.w < 0.f) return false;
-    const float x0 = bx + nu, x1 = (bx + 7.f) + nu, y0 = by + nv, y1 = (by + (float)(BH - 1)) + nv;
-    const bool in_x = x0 <= 0.f && x1 >= 0.f, in_y = y0 <= 0.f && y1 >= 0.f;
-    if (in_x && in_y) return true;
-    float qmin = 3.4e38f;
-    if (!in_x) {
-        const float X = x0 > 0.f ? x0 : x1;
-        const float dy = fminf(fmaxf(__fdividef(-F.y * X, F.z), y0), y1);
-        qmin = fminf(qmin, F.x * X * X + 2.f * F.y * X * dy + F.z * dy * dy);
-    }
-    if (!in_y) {
-        const float Y = y0 > 0.f ? y0 : y1;
-        const float dx = fminf(fmaxf(__fdividef(-F.y * Y, F.x), x0), x1);
-        qmin = fminf(qmin, F.x * dx * dx + 2.f * F.y * dx * Y + F.z * Y * Y);
-    }
-    return qmin <= F.w;
-}
-
 // Compact the indices [0, cnt) of the staged batch whose footprint reaches this warp's 8 x BH
 // block into list[] (ascending), only indices <= jmax. Returns the count (warp-uniform).
 template <int BH, int BATCH>
@@ -95,7 +70,7 @@ __device__ __forceinline__ int warp_compact(const float4* __restrict__ sP0, cons
         bool hit = false;
         if (j < lim) {
             const float4 c = sP0[j];
-            hit = reaches_block<BH>(c.x, c.z, sF[j], bx, by);
+            hit = footprint_reaches_rect(c.x, c.z, sF[j], bx, by, 7.f, (float)(BH - 1));
         }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[n + __popc(m & lanemask_lt())] = (unsigned short)j;
