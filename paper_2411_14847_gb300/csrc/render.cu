@@ -273,6 +273,20 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum four values across the warp with a transposed butterfly (2+1+1+1+1 shuffles). Lane l with
+// (l & 7) == 0 ends with the full sum of value index ((l >> 4) & 1) * 2 + ((l >> 3) & 1).
+__device__ __forceinline__ float warp_reduce4(float v0, float v1, float v2, float v3, int lane) {
+    const bool h4 = lane & 16;
+    const float a = (h4 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, h4 ? v0 : v2, 16);
+    const float b = (h4 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, h4 ? v1 : v3, 16);
+    const bool h3 = lane & 8;
+    float r = (h3 ? b : a) + __shfl_xor_sync(0xffffffffu, h3 ? a : b, 8);
+    r += __shfl_xor_sync(0xffffffffu, r, 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
 // Sum two values across the warp: lane 0 ends with the sum of a, lane 16 with the sum of b.
 __device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
     const bool h = lane & 16;
@@ -466,16 +480,31 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
         __syncthreads();
         const int jmax = (int)((long long)wlast - lo);   // entries beyond every lane's last are skipped
         const int nl = jmax >= 0 ? warp_compact<BH, BATCH>(sP[0], sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
-        for (int t = nl - 1; t >= 0; --t) {
-            const int j = sList[warp][t];
+        // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm); returns whether a
+        // pixel of this lane took part
+        auto mean_steps = [&](int j, float2* vm) {
             const int pos = (int)(lo + j);
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             float2 A, B;
             splat_column2(lo2(P1), hi2(P1), dx, A, B);
+            bool c = false;
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                c |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4, vm,
+                                              nullptr);
+            return c;
+        };
+        for (int t = nl - 1; t >= 0; --t) {
+            const int j = sList[warp][t];
             bool contrib = false;
             float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (sFull[j]) {          // warp-uniform: the same Gaussian for every lane
+                const int pos = (int)(lo + j);
+                const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
+                const float2 dx = __fadd2_rn(fx2, lo2(P0));
+                float2 A, B;
+                splat_column2(lo2(P1), hi2(P1), dx, A, B);
                 float2 vf[7];
 #pragma unroll
                 for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
@@ -493,14 +522,27 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                     if (lane == 1) atomicAdd(&sG[j][8], e);
                 }
             } else {
-#pragma unroll
-                for (int k = 0; k < NP; ++k)
-                    contrib |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
-                                                        vm, nullptr);
+                // mean-only entries are taken two at a time when the next one is mean-only too
+                // (warp-uniform), so that one 4-value reduction serves both
+                const int j2 = t >= 1 ? sList[warp][t - 1] : 0;
+                const bool two = t >= 1 && !sFull[j2];
+                contrib = mean_steps(j, vm);
+                float2 vm2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                if (two) {
+                    contrib |= mean_steps(j2, vm2);
+                    --t;
+                }
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                    // lane 0 holds X, lane 16 holds Y (the conic is applied at the flush)
-                    if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
+                    if (two) {
+                        const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
+                                                     vm2[1].x + vm2[1].y, lane);
+                        // lanes 0, 8 hold X, Y of j; lanes 16, 24 those of j2 (conic at the flush)
+                        if ((lane & 7) == 0) atomicAdd(&sG[(lane & 16) ? j2 : j][(lane >> 3) & 1], r);
+                    } else {
+                        const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
+                        // lane 0 holds X, lane 16 holds Y (the conic is applied at the flush)
+                        if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
+                    }
                 }
             }
         }
