@@ -344,10 +344,11 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 // Reverse step of staged entry P0..P4 (list position pos) for both pixels of the pair; adds the
 // entry's gradient contributions: vm[0..1] (packed, both pixels) the sums of dx and dy times
 // dL/d(power) -- dL/d(u, v) = (a X + b Y, b X + c Y) of those sums X, Y, applied once per
-// staged Gaussian when the CTA's block sums are flushed, since the conic is the Gaussian's; if
-// FULL also vf[0..2]
-// the sums of dx^2, dx dy, dy^2 times dL/d(power) (dL/d(a, b, c) after scaling by -1/2, -1, -1/2),
-// vf[3] dL/do and vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
+// staged Gaussian when the CTA's block sums are flushed, since the conic is the Gaussian's. If
+// FULL, the lane's shared dx is factored out: vm[0] holds sum dL/d(power) (X = dx vm[0], and the
+// dx^2 moment dx X), vm[1] the dy moment Y (the dx dy moment is dx Y), vf[2] the dy^2 moment --
+// the three second moments give dL/d(a, b, c) after scaling by -1/2, -1, -1/2 -- and vf[3]
+// dL/do, vf[4..6] dL/d(r, g, blue). A pixel whose list ends before pos, or where alpha <
 // 1/255, takes alpha = 0, which leaves its T and R exactly unchanged and adds nothing. The step is
 // branch-free (no early exit when neither pixel takes part: under SIMT the warp runs the body
 // whenever any lane needs it, and the divergent exits cost more than the masked work; measured
@@ -377,17 +378,21 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     // the clamp alpha = 0.99 has zero derivative
     const bool cm0 = val0 && oG.x < kAlphaMax, cm1 = val1 && oG.y < kAlphaMax;
     const float2 dpow = __fmul2_rn(dLda, make_float2(cm0 ? alpha.x : 0.f, cm1 ? alpha.y : 0.f));
-    vm[0] = __ffma2_rn(dpow, dx, vm[0]);
-    vm[1] = __ffma2_rn(dpow, dy, vm[1]);
     if (FULL) {
-        vf[0] = __ffma2_rn(__fmul2_rn(dx, dx), dpow, vf[0]);
-        vf[1] = __ffma2_rn(__fmul2_rn(dx, dy), dpow, vf[1]);
-        vf[2] = __ffma2_rn(__fmul2_rn(dy, dy), dpow, vf[2]);
+        // a lane's pixels share dx: vm[0] collects sum dpow (times dx, and dx^2, once per entry)
+        // and vm[1], vf[2] the sums of dpow dy and dpow dy^2; sum dpow dx dy = dx sum dpow dy
+        vm[0] = __fadd2_rn(vm[0], dpow);
+        const float2 t = __fmul2_rn(dpow, dy);
+        vm[1] = __fadd2_rn(vm[1], t);
+        vf[2] = __ffma2_rn(t, dy, vf[2]);
         vf[3] = __ffma2_rn(dLda, make_float2(cm0 ? G.x : 0.f, cm1 ? G.y : 0.f), vf[3]);
         const float2 w = __fmul2_rn(am, Tj);
         vf[4] = __ffma2_rn(w, g0, vf[4]);
         vf[5] = __ffma2_rn(w, g1, vf[5]);
         vf[6] = __ffma2_rn(w, g2, vf[6]);
+    } else {
+        vm[0] = __ffma2_rn(dpow, dx, vm[0]);
+        vm[1] = __ffma2_rn(dpow, dy, vm[1]);
     }
     return val0 || val1;
 }
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                 const float2 dx = __fadd2_rn(fx2, lo2(P0));
                 float2 A, B;
                 splat_column2(lo2(P1), hi2(P1), dx, A, B);
-                float2 vf[7];
+                float2 vf[7];      // vf[0], vf[1] unused: formed from vm below
 #pragma unroll
                 for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -513,8 +518,9 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                     contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
                                                        vm, vf);
                 if (__ballot_sync(0xffffffffu, contrib)) {
-                    float r[8] = {vm[0].x + vm[0].y, vm[1].x + vm[1].y, vf[0].x + vf[0].y, vf[1].x + vf[1].y,
-                                  vf[2].x + vf[2].y, vf[3].x + vf[3].y, vf[4].x + vf[4].y, vf[5].x + vf[5].y};
+                    const float X = dx.x * (vm[0].x + vm[0].y), Y = vm[1].x + vm[1].y;
+                    float r[8] = {X, Y, dx.x * X, dx.x * Y, vf[2].x + vf[2].y, vf[3].x + vf[3].y,
+                                  vf[4].x + vf[4].y, vf[5].x + vf[5].y};
                     float s = warp_reduce8(r, lane);
                     const float e = warp_sum(vf[6].x + vf[6].y);
                     // lanes 0 and 4 hold the moments X and Y (the conic is applied at the flush)
