@@ -241,15 +241,18 @@ __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, 
 
 // ----------------------------------------------------------------- tile rectangle (FP32)
 
+// 1 / tile for the bin sizes 8, 16, 32 (the tables accept no others): a power of two, so x * (1 /
+// tile) is the same correctly rounded number as x / tile, without a division.
+__device__ __forceinline__ float inv_tile(int tile) { return tile == 8 ? 0.125f : tile == 16 ? 0.0625f : 0.03125f; }
+
 // [x0, x1] x [y0, y1] tiles of the square [u-r, u+r] x [v-r, v+r]; empty if x0 > x1 or y0 > y1.
 __device__ __forceinline__ void tile_rect(float u, float v, int r, int tiles_x, int tiles_y, int tile,
                                           int& x0, int& x1, int& y0, int& y1) {
     float rf = (float)r;
-    float B = (float)tile;
-    x0 = max(0, (int)floorf(__fdiv_rn(__fsub_rn(u, rf), B)));
-    x1 = min(tiles_x - 1, (int)floorf(__fdiv_rn(__fadd_rn(u, rf), B)));
-    y0 = max(0, (int)floorf(__fdiv_rn(__fsub_rn(v, rf), B)));
-    y1 = min(tiles_y - 1, (int)floorf(__fdiv_rn(__fadd_rn(v, rf), B)));
+    x0 = max(0, (int)floorf(__fmul_rn(__fsub_rn(u, rf), inv_tile(tile))));
+    x1 = min(tiles_x - 1, (int)floorf(__fmul_rn(__fadd_rn(u, rf), inv_tile(tile))));
+    y0 = max(0, (int)floorf(__fmul_rn(__fsub_rn(v, rf), inv_tile(tile))));
+    y1 = min(tiles_y - 1, (int)floorf(__fmul_rn(__fadd_rn(v, rf), inv_tile(tile))));
 }
 
 __device__ __forceinline__ int tile_count(float u, float v, int r, int tiles_x, int tiles_y, int tile) {
@@ -316,11 +319,10 @@ __device__ __forceinline__ float rect_qmin(const Footprint& f, float x0, float x
 // Candidate tiles from the bounding box, clamped to the camera's tile grid.
 __device__ __forceinline__ void footprint_tiles(const Footprint& f, int tiles_x, int tiles_y, int tile, int& x0, int& x1,
                                                 int& y0, int& y1) {
-    float B = (float)tile;
-    x0 = max(0, (int)floorf(__fdiv_rn(__fsub_rn(f.u, f.ex), B)));
-    x1 = min(tiles_x - 1, (int)floorf(__fdiv_rn(__fadd_rn(f.u, f.ex), B)));
-    y0 = max(0, (int)floorf(__fdiv_rn(__fsub_rn(f.v, f.ey), B)));
-    y1 = min(tiles_y - 1, (int)floorf(__fdiv_rn(__fadd_rn(f.v, f.ey), B)));
+    x0 = max(0, (int)floorf(__fmul_rn(__fsub_rn(f.u, f.ex), inv_tile(tile))));
+    x1 = min(tiles_x - 1, (int)floorf(__fmul_rn(__fadd_rn(f.u, f.ex), inv_tile(tile))));
+    y0 = max(0, (int)floorf(__fmul_rn(__fsub_rn(f.v, f.ey), inv_tile(tile))));
+    y1 = min(tiles_y - 1, (int)floorf(__fmul_rn(__fadd_rn(f.v, f.ey), inv_tile(tile))));
 }
 
 // Does the footprint ellipse reach a pixel centre of tile (tx, ty)? (pixel centres of the tile
@@ -362,8 +364,8 @@ __device__ __forceinline__ bool footprint_row(const Footprint& f, int ty, int ti
         if (disc < 0.f) return false;
         L = __fdiv_rn(__fsub_rn(-__fmul_rn(f.b, yy), __fsqrt_rn(disc)), f.a);
     }
-    tx0 = max(0, (int)ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(f.u, L), B - 1.f), B)));
-    tx1 = min(tiles_x - 1, (int)floorf(__fdiv_rn(__fadd_rn(f.u, R), B)));
+    tx0 = max(0, (int)ceilf(__fmul_rn(__fsub_rn(__fadd_rn(f.u, L), B - 1.f), inv_tile(tile))));
+    tx1 = min(tiles_x - 1, (int)floorf(__fmul_rn(__fadd_rn(f.u, R), inv_tile(tile))));
     return tx0 <= tx1;
 }
 
