@@ -72,3 +72,21 @@ def test_host_side_argument_checks(lib):
     # empty inputs are no-ops that succeed without launching
     assert lib.dass_shift(0, None, None, None, None, None, None, None) == 0
     assert lib.dass_preprocess(0, 0, None, None, None, None, None, None, cams, 2, 16, None, None) == 0
+
+
+def test_host_side_layout_checks(lib):
+    """Cameras whose planes would overflow 32-bit pixel offsets, and feature rows that are not
+    16-byte aligned (they are read as float4), are rejected before any launch."""
+    from paper_2411_14847_gb300 import dass, synth
+    t, p = C.c_int32(), C.c_int64()
+    big = synth.arc_cameras(1, 4.0, 50000, 50000)
+    assert lib.dass_tile_layout(dass.cameras(big), 1, 16, C.byref(t), C.byref(p)) == -1
+    ok = synth.arc_cameras(1, 4.0, 40000, 40000)
+    assert lib.dass_tile_layout(dass.cameras(ok), 1, 16, C.byref(t), C.byref(p)) == 0
+    aligned, misaligned = C.c_void_p(256), C.c_void_p(260)
+    assert lib.dass_object_ids(misaligned, 10, 16, aligned, aligned, 4, aligned, None) == -1
+    assert lib.dass_object_ids(aligned, 10, 16, misaligned, aligned, 4, aligned, None) == -1
+    assert lib.dass_dynamic_gaussians(misaligned, 10, 16, aligned, aligned, 4, aligned, aligned, None) == -1
+    cams = dass.cameras(synth.arc_cameras(2, 4.0, 100, 50))
+    assert lib.dass_render_features(aligned, aligned, aligned, cams, 2, 16, misaligned, 16, 10, aligned, None) == -1
+    assert lib.dass_render_features(aligned, aligned, aligned, cams, 2, 16, aligned, 16, 1 << 31, aligned, None) == -1
