@@ -569,6 +569,8 @@ def main():
     # ---------------- end to end through the public API with host buffers
     host_tgt = targets.cpu().pin_memory()
     dev_tgt = torch.empty_like(targets)
+    # G_t comes back into pinned host buffers sized for the scene's capacity (rows [0, n) per step)
+    host_g = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ts.bufs[ts.cur].items()}
     one_timestep(t, targets)
     t += 1
     torch.cuda.synchronize()
@@ -580,10 +582,12 @@ def main():
         r = ts.run(t, dev_tgt, dyn_t, off_t.clone(), z=z)
         t += 1
         gv = ts.view()
-        host = {k: v.to("cpu") for k, v in gv.items()}
+        for k, v in gv.items():
+            host_g[k][:v.shape[0]].copy_(v, non_blocking=True)
+        torch.cuda.current_stream().synchronize()      # the step's result is on the host
         loss_h = r["loss"]
         h2d = host_tgt.numel() * 4
-        d2h = sum(v.numel() * 4 for v in host.values()) + 8
+        d2h = sum(v.numel() * 4 for v in gv.values()) + 8
     b.record()
     torch.cuda.synchronize()
     e2e_s = a.elapsed_time(b) / 1e3 / args.e2e_steps
