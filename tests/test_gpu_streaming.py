@@ -68,3 +68,48 @@ def test_streaming_timesteps(dass):
     # move the dynamic Gaussians towards their new positions
     assert all(h["err_after"] < h["err_before"] for h in history[:3]), history[:3]
     assert sum(h["spawned"] for h in history) > 0
+
+
+def test_streaming_full_schedule(dass):
+    """The paper's whole per-timestep schedule (inheritance stage, shift stage, error-guided
+    densification, densification stage with pruning) over a few timesteps of a moving scene:
+    every stage runs, the shift stage fits its timestep, base rows persist and the var rows only
+    change by the rules (inherited by the learned mask, spawned, pruned)."""
+    from paper_2411_14847_gb300 import dass as D, raster
+    from paper_2411_14847_gb300.timestep import Timestep
+    ms = synth.moving_scene(2500, 300, 200, 1, 43, log_scale_mean=-3.2)
+    cams = synth.arc_cameras(3, 4.0, 80, 60)
+    g0 = ms.initial()
+    n_base = g0.n
+    k_max = 120
+    ts = Timestep(cams, n_base + 8 * k_max, 1, tile=16, batch=128, lambda_dssim=0.2, n_shift=8, k_max=k_max,
+                  tau_pos=2e-4, tau_err=1e-4, n_inherit=5, n_densify=6)
+    ts.load(g0.arrays())
+    dyn = torch.as_tensor(ms.dyn_idx, dtype=torch.int32, device="cuda")
+    z = torch.as_tensor(synth.standard_normal((n_base + 8 * k_max, 3), 11), device="cuda")
+    off = torch.zeros((len(ms.dyn_idx), 7), device="cuda")
+    off[:, 3] = 1.0
+    lws = torch.empty(D.dass_loss_workspace(cams), dtype=torch.uint8, device="cuda")
+    spawned_total = 0
+    for t in range(1, 6):
+        gt_scene = ms.at(t)
+        fr = raster.Frame(cams, gt_scene.n)
+        fr.render(raster.to_device(gt_scene.arrays()))
+        gt = fr.image.clone()
+        fr0 = raster.Frame(cams, ts.n)
+        fr0.render(ts.view())
+        dimg = torch.empty_like(fr0.image)
+        l0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        D.dass_loss(fr0.image, gt, cams, 0.2, dimg, l0, lws)
+        n_prev = ts.n
+        n_var_prev = int(ts.is_var[ts.cur][:n_prev].sum())
+        res = ts.run(t, gt, dyn, off.clone(), z=z)
+        assert res["loss"] < float(l0), (t, res["loss"], float(l0))
+        n_var = int(ts.is_var[ts.cur][:ts.n].sum())
+        assert ts.n - n_var == n_base                              # base rows persist
+        assert 0 <= res["spawned"] <= k_max
+        assert n_var <= n_var_prev + res["spawned"]                # var rows: inherited subset + spawned - pruned
+        base_means = ts.view()["means"][:n_base]
+        assert torch.isfinite(base_means).all()
+        spawned_total += res["spawned"]
+    assert spawned_total > 0
