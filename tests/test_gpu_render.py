@@ -174,6 +174,23 @@ def test_forward_parity_multicam_sh3(dass, tile, batch):
         assert bad == 0, (bad, resolved, maxerr)
 
 
+def test_forward_parity_max_cameras(dass):
+    """The largest camera table one call accepts (64 views, packed into the kernel parameters):
+    every view against the oracle, and a 65th view is refused on the host."""
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene, cams = _small_multicam(seed=13, n=400, deg=1, n_cams=64, w=24, h=18)
+    g = raster.to_device(scene.arrays())
+    fr = _frame(dass, cams, scene.n, tile=16, batch=64)
+    imgs = fr.render(g)
+    torch.cuda.synchronize()
+    projs = og.project_all(scene.arrays(), cams, 1)
+    for img, p, cam in zip(imgs, projs, cams):
+        bad, resolved, _, maxerr = _check_image(img, p, cam)
+        assert bad == 0, (bad, resolved, maxerr)
+    with pytest.raises(D.DassError):
+        D.tile_layout(list(cams) + [cams[0]], 16)
+
+
 def test_images_bit_identical_across_tiles_and_batches(dass):
     scene, cams = _small_multicam(seed=11)
     from paper_2411_14847_gb300 import raster
