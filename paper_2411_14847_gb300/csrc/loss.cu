@@ -29,7 +29,7 @@ struct LossArgs {
     const float* x;       // image
     const float* y;       // target
     float* dx;            // dL/dimage
-    float* g;             // 3 maps, each 3 * pixels_total
+    float* g;             // gradient maps: (g1, g2) pairs [3 * pixels_total][2], then g3 [3 * pixels_total]
     double* loss;
     const float* ystats;  // optional cached target statistics (2 maps, ystride apart)
     float lambda;
@@ -174,8 +174,9 @@ __device__ __forceinline__ void vpass2(const Hor& h, const Window2& win, int col
     }
 }
 
-// Stage the 42 x 42 window of the pair (p0, p1) and the scalar plane ps (if any) of the plane at
-// element offset off, with zeros outside the image. Each thread issues all of its global loads
+// Stage the 42 x 42 window of the pair (p0, p1) -- for TileB the pair is stored interleaved at p0
+// (p1 unused) -- and the scalar plane ps (TileB) of the plane at element offset off, with zeros
+// outside the image. Each thread issues all of its global loads
 // before its first shared store, so the block waits for one memory latency, not one per element.
 // A thread's elements are threadIdx.x + 256 e; their (row, column) advance by (6, 4) per step
 // (256 = 6 * 42 + 4), and the plane offsets are 32-bit (a plane has fewer than 2^31 pixels).
@@ -183,10 +184,11 @@ template <class Tile>
 __device__ __forceinline__ void stage2(Tile& dst, const float* p0, const float* p1, const float* ps, long long off,
                                        int W, int H, int ox, int oy) {
     constexpr int kPer = (kI * kI + 255) / 256;
-    constexpr bool kScalar = std::is_same_v<Tile, TileB>;
+    constexpr bool kScalar = std::is_same_v<Tile, TileB>;   // backward: p0 holds interleaved pairs
     static_assert(256 / kI == 6 && 256 % kI == 4, "element stepping assumes a 42-wide window");
-    const float* __restrict__ b0 = p0 + off;
-    const float* __restrict__ b1 = p1 + off;
+    const float* __restrict__ b0 = kScalar ? nullptr : p0 + off;
+    const float* __restrict__ b1 = kScalar ? nullptr : p1 + off;
+    const float2* __restrict__ b01 = kScalar ? reinterpret_cast<const float2*>(p0) + off : nullptr;
     const float* __restrict__ bs = kScalar ? ps + off : nullptr;
     float2 v[kPer];
     float sv[kPer];
@@ -197,7 +199,10 @@ __device__ __forceinline__ void stage2(Tile& dst, const float* p0, const float* 
         const int gx = ox + c - kR, gy = oy + r - kR;
         const bool in = r < kI && (unsigned)gx < (unsigned)W && (unsigned)gy < (unsigned)H;
         const int q = gy * W + gx;
-        v[e] = in ? make_float2(__ldg(b0 + q), __ldg(b1 + q)) : make_float2(0.f, 0.f);
+        if constexpr (kScalar)
+            v[e] = in ? __ldg(b01 + q) : make_float2(0.f, 0.f);
+        else
+            v[e] = in ? make_float2(__ldg(b0 + q), __ldg(b1 + q)) : make_float2(0.f, 0.f);
         if constexpr (kScalar) sv[e] = in ? __ldg(bs + q) : 0.f;
         so[e] = r < kI ? r * kIP + c : -1;
         c += 4;
@@ -264,8 +269,7 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
         vpass2<true>(sh, win, col, r0, m, e, exy);
     }
     const float inv_n = a.inv_cams / (3.f * (float)W * (float)H);
-    float* __restrict__ g1 = a.g + off;
-    float* __restrict__ g2 = a.g + a.map_stride + off;
+    float2* __restrict__ g12 = reinterpret_cast<float2*>(a.g) + off;
     float* __restrict__ g3 = a.g + 2 * a.map_stride + off;
     float contrib = 0.f;
 #pragma unroll
@@ -282,8 +286,7 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
         const float dvx = -S * B1 * inv;
         const float dcxy = 2.f * A1 * inv;
         const int q = gy * W + gx;
-        g1[q] = dmu - 2.f * mx * dvx - my * dcxy;
-        g2[q] = dvx;
+        g12[q] = make_float2(dmu - 2.f * mx * dvx - my * dcxy, dvx);
         g3[q] = dcxy;
         const float2 c = sin.p[r0 + o + kR][col + kR];
         contrib += inv_n * ((1.f - a.lambda) * fabsf(c.x - c.y) - a.lambda * S);
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
         xv[o] = in ? __ldg(xb + q) : 0.f;
         yv[o] = in ? __ldg(yb + q) : 0.f;
     }
-    stage2(sin, a.g, a.g + a.map_stride, a.g + 2 * a.map_stride, off, W, H, ox, oy);
+    stage2(sin, a.g, nullptr, a.g + 2 * a.map_stride, off, W, H, ox, oy);
     __syncthreads();
     hpass2<kPairScalar>(sin, sh, win);
     __syncthreads();
