@@ -375,7 +375,8 @@ int dass_adam(int64_t n_rows, int row_width, const int32_t* rows, int64_t n_sel,
               const float* lr /* host, row_width */, float beta1, float beta2, float eps,
               int increment_step, void* stream);
 
-/* Bytes of scratch for dass_loss over a camera set (3 SSIM partial maps per pixel/channel). */
+/* Bytes of scratch for dass_loss over a camera set (3 SSIM partial maps per pixel/channel); the
+ * workspace must be 8-byte aligned. */
 int dass_loss_workspace(const dass_camera* cams, int n_cams, size_t* bytes);
 
 /* Fidelity loss of Eq. 3: L = mean_c[(1-lambda) L1_c + lambda (1 - SSIM_c)], SSIM with an
@@ -387,9 +388,10 @@ int dass_loss(const float* image, const float* target, const dass_camera* cams /
               size_t workspace_bytes, void* stream);
 
 /* Window statistics of a target for the SSIM term of Eq. 3, computed once per fixed target set:
- * stats[0 .. 3P) = w * y (the window mean) and stats[3P .. 6P) = w * y^2 (its second moment),
- * P = sum of W*H over cams, planar like the image, w the 11x11 window of dass_loss with zero
- * padding. stats: device, 6P floats, caller-owned. */
+ * for every pixel-channel i (planar like the image, P = sum of W*H over cams, 3P of them)
+ * stats[2i] = (w * y)_i (the window mean) and stats[2i + 1] = (w * y^2)_i (its second moment),
+ * w the 11x11 window of dass_loss with zero padding. stats: device, 6P floats, 8-byte aligned,
+ * caller-owned. */
 int dass_loss_target_stats(const float* target, const dass_camera* cams /* host */, int n_cams,
                            float* stats, void* stream);
 

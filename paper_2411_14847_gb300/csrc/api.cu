@@ -39,8 +39,7 @@ int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
 size_t loss_workspace_bytes(const CamTable& ct);
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
-                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr,
-                long long stats_stride = 0);
+                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr);
 int target_stats_launch(const float* target, const CamTable& ct, float* stats, cudaStream_t st);
 int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats, float* om,
                  float* oq, cudaStream_t st);
@@ -386,13 +385,14 @@ DASS_API int dass_loss(const float* image, const float* target, const dass_camer
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
     if (lambda > 0.f && workspace_bytes < loss_workspace_bytes(ct)) return DASS_ERR_OOM;
+    if (lambda > 0.f && reinterpret_cast<uintptr_t>(workspace) % 8) return DASS_ERR_INVALID_ARG;   // float2 maps
     return loss_launch(image, target, ct, lambda, 1.f / (float)n_cams, dL_dimage, loss, workspace, workspace_bytes,
                        as_stream(stream));
 }
 
 DASS_API int dass_loss_target_stats(const float* target, const dass_camera* cams, int n_cams, float* stats,
                                    void* stream) {
-    if (!target || !stats) return DASS_ERR_INVALID_ARG;
+    if (!target || !stats || reinterpret_cast<uintptr_t>(stats) % 8) return DASS_ERR_INVALID_ARG;   // float2 pairs
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
     return target_stats_launch(target, ct, stats, as_stream(stream));
@@ -403,11 +403,13 @@ DASS_API int dass_loss_cached(const float* image, const float* target, const flo
                               void* workspace, size_t workspace_bytes, void* stream) {
     if (!image || !target || !target_stats || !dL_dimage || !loss || !(lambda >= 0.f && lambda <= 1.f))
         return DASS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(target_stats) % 8) return DASS_ERR_INVALID_ARG;   // float2 pairs
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, 16, 0, &ct)) return DASS_ERR_INVALID_ARG;
     if (lambda > 0.f && workspace_bytes < loss_workspace_bytes(ct)) return DASS_ERR_OOM;
+    if (lambda > 0.f && reinterpret_cast<uintptr_t>(workspace) % 8) return DASS_ERR_INVALID_ARG;   // float2 maps
     return loss_launch(image, target, ct, lambda, 1.f / (float)n_cams, dL_dimage, loss, workspace, workspace_bytes,
-                       as_stream(stream), target_stats, 3 * ct.pixels_total);
+                       as_stream(stream), target_stats);
 }
 
 DASS_API int dass_inherit_workspace(int64_t n, size_t* bytes) {
@@ -594,8 +596,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
     char* ws = reinterpret_cast<char*>(d->workspace);
     void* bin_ws = ws;
     void* loss_ws = ws + align256(p.bin_ws);
-    const float* ystats = target_stats_ptr(d, p);
-    const long long ystride = 3 * p.all.pixels_total;
+    const float* ystats = target_stats_ptr(d, p);     // (w * y, w * y^2) pairs per pixel-channel
     const float3 bg = make_float3(0.f, 0.f, 0.f);
     int rc = shift_launch(d->n_dyn, d->dyn_idx, d->offsets, d->means, d->quats, d->render_means, d->render_quats, st);
     if (rc) return rc;
@@ -615,7 +616,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
                                d->n_last, st);
         if (rc) return rc;
         rc = loss_launch(d->image, d->targets, ct, d->lambda_dssim, inv_cams, d->dL_dimage, d->loss, loss_ws,
-                         p.loss_ws, st, ystats, ystride);
+                         p.loss_ws, st, ystats);
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemsetAsync(d->splat_grads, 0, sizeof(dass_splat_grad) * n_rec, st));
         rc = render_bwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final, d->n_last,
@@ -648,8 +649,8 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
                                    d->T_final + pb, d->n_last + pb, st);
             if (rc) return rc;
             rc = loss_launch(d->image + 3 * pb, d->targets + 3 * pb, ct, d->lambda_dssim, inv_cams,
-                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st, ystats ? ystats + 3 * pb : nullptr,
-                             ystride);
+                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st,
+                             ystats ? ystats + 2 * 3 * pb : nullptr);
             if (rc) return rc;
             DASS_CHECK_CUDA(cudaMemsetAsync(gs, 0, sizeof(dass_splat_grad) * d->n, st));
             rc = render_bwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final + pb, d->n_last + pb,

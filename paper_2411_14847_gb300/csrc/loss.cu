@@ -31,11 +31,10 @@ struct LossArgs {
     float* dx;            // dL/dimage
     float* g;             // gradient maps: (g1, g2) pairs [3 * pixels_total][2], then g3 [3 * pixels_total]
     double* loss;
-    const float* ystats;  // optional cached target statistics (2 maps, ystride apart)
+    const float2* ystats; // optional cached target statistics, (w * y, w * y^2) per pixel-channel
     float lambda;
     float inv_cams;
     long long map_stride;  // 3 * pixels_total
-    long long ystride;
 };
 
 __device__ __forceinline__ void plane_of(const CamTable& ct, int z, const CamInfo*& cam, long long& off) {
@@ -238,15 +237,15 @@ __global__ void __launch_bounds__(256, 5) ssim_fwd_kernel(CamTable ct, Window2 w
     const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
     float ym[4], y2[4];
     if constexpr (CACHED) {      // requested before the stencil work
-        const float* __restrict__ m1 = a.ystats + off;
-        const float* __restrict__ m2 = a.ystats + a.ystride + off;
+        const float2* __restrict__ ms = a.ystats + off;
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int gx = ox + col, gy = oy + r0 + o;
             const bool in = gx < W && gy < H;
             const int q = gy * W + gx;
-            ym[o] = in ? __ldg(m1 + q) : 0.f;
-            y2[o] = in ? __ldg(m2 + q) : 0.f;
+            const float2 v = in ? __ldg(ms + q) : make_float2(0.f, 0.f);
+            ym[o] = v.x;
+            y2[o] = v.y;
         }
     }
     stage2(sin, a.x, a.y, nullptr, off, W, H, ox, oy);
@@ -339,10 +338,10 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(CamTable ct, Window2 w
     }
 }
 
-// Window statistics of the target (cached across the iterations of a stage): ystats[0] = w * y,
-// ystats[1] = w * y^2, per plane, planar like the image.
+// Window statistics of the target (cached across the iterations of a stage): ystats[i] =
+// (w * y, w * y^2) at pixel-channel i, planar like the image.
 __global__ void __launch_bounds__(256, 4) ssim_target_stats_kernel(CamTable ct, Window2 win, const float* y,
-                                                                   float* ystats, long long map_stride) {
+                                                                   float2* ystats) {
     const CamInfo* cam;
     long long off;
     plane_of(ct, blockIdx.z, cam, off);
@@ -359,15 +358,13 @@ __global__ void __launch_bounds__(256, 4) ssim_target_stats_kernel(CamTable ct, 
     float2 m[4], unused[4];
     float c[4];
     vpass2<false>(sh, win, col, r0, m, unused, c);
-    float* __restrict__ s1 = ystats + off;
-    float* __restrict__ s2 = ystats + map_stride + off;
+    float2* __restrict__ so = ystats + off;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const int gx = ox + col, gy = oy + r0 + o;
         if (gx >= W || gy >= H) continue;
         const int q = gy * W + gx;
-        s1[q] = m[o].x;
-        s2[q] = m[o].y;
+        so[q] = m[o];
     }
 }
 
@@ -405,11 +402,9 @@ Window make_window() {
 size_t loss_workspace_bytes(const CamTable& ct) { return sizeof(float) * 9 * (size_t)ct.pixels_total; }
 
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
-                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats,
-                long long stats_stride) {
+                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats) {
     LossArgs a;
-    a.ystats = target_stats;
-    a.ystride = stats_stride;
+    a.ystats = reinterpret_cast<const float2*>(target_stats);
     a.x = image;
     a.y = target;
     a.dx = dL;
@@ -457,7 +452,7 @@ int target_stats_launch(const float* target, const CamTable& ct, float* stats, c
     Window2 w2;
     for (int t = 0; t < 11; ++t) w2.w[t] = make_float2(w.w[t], w.w[t]);
     dim3 grid(div_up(maxW, kO), div_up(maxH, kO), 3 * ct.n);
-    ssim_target_stats_kernel<<<grid, 256, 0, st>>>(ct, w2, target, stats, 3 * ct.pixels_total);
+    ssim_target_stats_kernel<<<grid, 256, 0, st>>>(ct, w2, target, reinterpret_cast<float2*>(stats));
     count_launch();
     return check_launch("ssim_target_stats_kernel");
 }
