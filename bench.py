@@ -231,13 +231,14 @@ def streaming_schedule(cams, tile, batch, timesteps, seed=1004):
     with low-opacity pruning. Device time per timestep by CUDA events around Timestep.run."""
     import torch
     from paper_2411_14847_gb300 import raster, synth
-    from paper_2411_14847_gb300.timestep import Timestep
+    from paper_2411_14847_gb300.timestep import PAPER_SCHEDULE, Timestep
     dev = "cuda"
     ms = synth.moving_scene(250_000, 30_000, 2_000, 3, seed)
     g0 = ms.initial()
     k_max = 5000
-    ts = Timestep(cams, g0.n + k_max * (timesteps + 2), 3, tile=tile, batch=batch, lambda_dssim=0.2, n_shift=100,
-                  k_max=k_max, n_inherit=20, n_densify=60)
+    s1, s2, s3 = PAPER_SCHEDULE
+    ts = Timestep(cams, g0.n + k_max * (timesteps + 2), 3, tile=tile, batch=batch, lambda_dssim=0.2, n_shift=s2,
+                  k_max=k_max, n_inherit=s1, n_densify=s3)
     ts.load(g0.arrays())
     dyn = torch.as_tensor(ms.dyn_idx, dtype=torch.int32, device=dev)
     z = torch.as_tensor(synth.standard_normal((g0.n + k_max * (timesteps + 2), 3), seed + 3), device=dev)
@@ -259,7 +260,7 @@ def streaming_schedule(cams, tile, batch, timesteps, seed=1004):
         rows.append({"t": t, "s": round(a.elapsed_time(b) / 1e3, 4), "loss": round(r["loss"], 6), "n": r["n"],
                      "spawned": r["spawned"]})
     steady = [x["s"] for x in rows[1:]] or [rows[0]["s"]]
-    return {"workload": "moving scene 250k static + 30k dynamic SH3, 20 cams 1352x1014", "s1_s2_s3": [20, 100, 60],
+    return {"workload": "moving scene 250k static + 30k dynamic SH3, 20 cams 1352x1014", "s1_s2_s3": [s1, s2, s3],
             "s_per_timestep": round(sum(steady) / len(steady), 4), "timesteps": rows,
             "note": "mean over timesteps 2.. (timestep 1 has no var rows to inherit)"}
 
@@ -337,7 +338,7 @@ def main():
     import torch.distributed as dist
     from paper_2411_14847_gb300 import build, dass as D, raster, replicas, synth
     from paper_2411_14847_gb300.autotune import autotune
-    from paper_2411_14847_gb300.timestep import ShiftStage, Timestep
+    from paper_2411_14847_gb300.timestep import PAPER_SCHEDULE, ShiftStage, Timestep
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -584,9 +585,10 @@ def main():
     if inh is not None and den is not None:
         # the paper's schedule per timestep: s1 = 20 inheritance, s2 = 100 shift, s3 = 60 densification
         # iterations (Sec. 4.1), from the per-iteration costs measured above
-        stages = {"s1_s2_s3": [20, 100, 60],
-                  "estimated_s_per_timestep": round((20 * inh["ms_per_iter"] + 100 * batched_ms
-                                                     + 60 * den["ms_per_iter"]) / 1e3, 4)}
+        s1, s2, s3 = PAPER_SCHEDULE
+        stages = {"s1_s2_s3": [s1, s2, s3],
+                  "estimated_s_per_timestep": round((s1 * inh["ms_per_iter"] + s2 * batched_ms
+                                                     + s3 * den["ms_per_iter"]) / 1e3, 4)}
 
     # ---------------- the paper's full schedule, measured: streaming over a moving scene
     streaming = None

@@ -169,6 +169,10 @@ def _ptr(t, dtype=None, name="tensor"):
     return C.c_void_p(t.data_ptr())
 
 
+# Feature widths dass_render_features, dass_object_ids and dass_dynamic_gaussians accept.
+FEATURE_WIDTHS = (4, 8, 16, 32)
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)

@@ -22,6 +22,10 @@ from . import dass as D
 from .raster import PARAM_NAMES, Frame
 
 
+# Optimisation steps per timestep of the inheritance, shift and densification stages (Sec. 4.1).
+PAPER_SCHEDULE = (20, 100, 60)
+
+
 def _vp(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
