@@ -63,6 +63,10 @@ FLOP_BWD_MEAN_ADD = 31
 # current kernel, 264.3 MB for 8.47M pairs, scaled by pairs to the 28.34M pairs of 20 cameras,
 # profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
 RENDER_BWD_TRAFFIC = 8.80e8
+# Issue utilisation of the same render_bwd capture (smsp__issue_active, fraction of cycles a warp
+# scheduler issued): the kernel is bound by instruction issue, not by FP32 throughput, so its
+# fraction of the FP32 peak is read next to this figure. None once the kernel changes.
+RENDER_BWD_ISSUE_ACTIVE = 0.726
 
 
 def measured_hbm_gbs():
@@ -467,6 +471,7 @@ def main():
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
                 "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                 "traffic": RENDER_BWD_TRAFFIC if (dom == "render_bwd" and tile == 32) else None,
+                "issue_active": RENDER_BWD_ISSUE_ACTIVE if (dom == "render_bwd" and tile == 32) else None,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)",
                 "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
