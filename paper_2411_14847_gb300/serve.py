@@ -174,7 +174,7 @@ class RenderServer:
 
     def _launch(self, slot, reqs, scenes, est, cap, bid=None):
         stream = self._streams[slot]
-        cams = [r.cam for r in reqs]
+        cams = D.cameras([r.cam for r in reqs])     # marshalled once for every call below
         rec_stride = max(s["means"].shape[0] for s in scenes)
         tiles_total, pixels = D.tile_layout(cams, self.tile)
         n_rec = len(reqs) * rec_stride
@@ -184,7 +184,7 @@ class RenderServer:
                 splats=torch.empty((max(1, n_rec), D.SPLAT_FLOATS), dtype=torch.float32, device=self.device),
                 pair_rec=torch.empty(max(1, cap), dtype=torch.int32, device=self.device),
                 ranges=torch.empty((max(1, tiles_total), 2), dtype=torch.int32, device=self.device),
-                counters=torch.zeros(4, dtype=torch.int64, device=self.device),
+                counters=torch.empty(4, dtype=torch.int64, device=self.device),   # written by the sort
                 image=torch.empty(3 * pixels, dtype=torch.float32, device=self.device),
                 T=torch.empty(pixels, dtype=torch.float32, device=self.device),
                 last=torch.empty(pixels, dtype=torch.int32, device=self.device),
