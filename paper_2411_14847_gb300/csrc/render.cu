@@ -20,7 +20,7 @@ namespace {
 // of the per-pixel math is stored twice, so one shared load yields the operand pair of the
 // packed arithmetic without register moves:
 //   P0 = (-u, -u, -v, -v)     P1 = (a', a', b2', b2')     P2 = (c', c', o, o)
-//   P3 = (r, r, g, g)         P4 = (blue, blue, a, a)
+//   P3 = (r, r, g, g)         P4 = (blue, blue, 0, 0)
 // with a' = a kNegHalfLog2e, b2' = 2 b kNegHalfLog2e, c' = c kNegHalfLog2e (see splat_gauss);
 // F = (a, b, c, k2) is the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
 // NEG (forward only): o, r, g and blue are staged negated, so that the forward works with -alpha
@@ -39,7 +39,7 @@ __device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splat
     sP[1][i] = make_float4(ap, ap, b2p, b2p);
     sP[2][i] = make_float4(cp, cp, sg * s1.y, sg * s1.y);
     sP[3][i] = make_float4(sg * s1.z, sg * s1.z, sg * s1.w, sg * s1.w);
-    sP[4][i] = make_float4(sg * bl, sg * bl, s0.z, s0.z);
+    sP[4][i] = make_float4(sg * bl, sg * bl, 0.f, 0.f);
     sF[i] = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
 }
 
