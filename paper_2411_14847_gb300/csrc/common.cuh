@@ -291,31 +291,6 @@ __device__ __forceinline__ bool footprint_of(float u, float v, float a, float b,
     return true;
 }
 
-// Minimum over the rectangle [x0,x1] x [y0,y1] (offsets from the centre) of the quadratic form
-// q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2. The form is positive definite with its minimum 0 at
-// the origin; if the origin is outside the rectangle the minimum lies on an edge facing it.
-__device__ __forceinline__ float rect_qmin(const Footprint& f, float x0, float x1, float y0, float y1) {
-    bool in_x = x0 <= 0.f && x1 >= 0.f;
-    bool in_y = y0 <= 0.f && y1 >= 0.f;
-    if (in_x && in_y) return 0.f;
-    float qmin = 3.4e38f;
-    if (!in_x) {
-        float X = x0 > 0.f ? x0 : x1;
-        float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(f.b, X), f.c), y0), y1);
-        float q = __fadd_rn(__fadd_rn(__fmul_rn(f.a, __fmul_rn(X, X)), __fmul_rn(2.f, __fmul_rn(f.b, __fmul_rn(X, dy)))),
-                            __fmul_rn(f.c, __fmul_rn(dy, dy)));
-        qmin = fminf(qmin, q);
-    }
-    if (!in_y) {
-        float Y = y0 > 0.f ? y0 : y1;
-        float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(f.b, Y), f.a), x0), x1);
-        float q = __fadd_rn(__fadd_rn(__fmul_rn(f.a, __fmul_rn(dx, dx)), __fmul_rn(2.f, __fmul_rn(f.b, __fmul_rn(dx, Y)))),
-                            __fmul_rn(f.c, __fmul_rn(Y, Y)));
-        qmin = fminf(qmin, q);
-    }
-    return qmin;
-}
-
 // Candidate tiles from the bounding box, clamped to the camera's tile grid.
 __device__ __forceinline__ void footprint_tiles(const Footprint& f, int tiles_x, int tiles_y, int tile, int& x0, int& x1,
                                                 int& y0, int& y1) {
@@ -323,14 +298,6 @@ __device__ __forceinline__ void footprint_tiles(const Footprint& f, int tiles_x,
     x1 = min(tiles_x - 1, (int)floorf(__fmul_rn(__fadd_rn(f.u, f.ex), inv_tile(tile))));
     y0 = max(0, (int)floorf(__fmul_rn(__fsub_rn(f.v, f.ey), inv_tile(tile))));
     y1 = min(tiles_y - 1, (int)floorf(__fmul_rn(__fadd_rn(f.v, f.ey), inv_tile(tile))));
-}
-
-// Does the footprint ellipse reach a pixel centre of tile (tx, ty)? (pixel centres of the tile
-// span [tx*B, tx*B + B - 1]; pixels beyond the image edge are included, which is conservative)
-__device__ __forceinline__ bool footprint_hits_tile(const Footprint& f, int tx, int ty, int tile) {
-    float px0 = (float)(tx * tile), py0 = (float)(ty * tile);
-    float px1 = (float)(tx * tile + tile - 1), py1 = (float)(ty * tile + tile - 1);
-    return rect_qmin(f, __fsub_rn(px0, f.u), __fsub_rn(px1, f.u), __fsub_rn(py0, f.v), __fsub_rn(py1, f.v)) <= f.k2;
 }
 
 // Tiles of row ty that the footprint reaches. The slice of the ellipse over the band of pixel
