@@ -216,10 +216,6 @@ def config_c(seed=1003, n=300_000, n_cams=20, width=1352, height=1014):
     return scene, cams, dyn_idx, offsets
 
 
-def cameras_array(cams) -> np.ndarray:
-    return np.stack([c.as_record() for c in cams])
-
-
 # ----------------------------------------------------------------- streaming scene
 
 @dataclass

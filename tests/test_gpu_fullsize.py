@@ -1,4 +1,5 @@
-"""Parity at the full benchmark size: 300k Gaussians, SH degree 3, 20 cameras of 1352x1014.
+"""Parity at the full benchmark size: 300k Gaussians, SH degree 3, 20 cameras of 1352x1014 (and
+the 100k-Gaussian, 4-camera 960x540 ring workload).
 
 The oracle cannot render 27M pixels against 300k Gaussians in FP64, so it computes sampled
 outputs one by one: colours and transmittance of seeded pixel samples, and the parameter
@@ -18,7 +19,8 @@ from paper_2411_14847_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SAMPLE_CAMS = (0, 9, 19)
+# sampled cameras of each workload: the ends and the middle of the arc; three of the ring's four
+SAMPLE = {"arc_300k_20x1352x1014": (0, 9, 19), "ring_100k_4x960x540": (0, 1, 3)}
 PIX_PER_CAM = 48
 
 
@@ -28,13 +30,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.fixture(scope="module")
-def workload():
-    scene, cams, dyn_idx, offsets = synth.config_c()
-    projs = og.project_all(scene.arrays(), [cams[c] for c in SAMPLE_CAMS], 3)
+@pytest.fixture(scope="module", params=sorted(SAMPLE))
+def workload(request):
+    if request.param.startswith("arc"):
+        scene, cams, dyn_idx, offsets = synth.config_c()
+    else:
+        scene, cams, dyn_idx, offsets = synth.config_b()
+    sample_cams = SAMPLE[request.param]
+    projs = og.project_all(scene.arrays(), [cams[c] for c in sample_cams], 3)
     rng = np.random.default_rng(77)
     samples = []
-    for c, proj in zip(SAMPLE_CAMS, projs):
+    for c, proj in zip(sample_cams, projs):
         cam = cams[c]
         # half of the samples at projected centres of visible Gaussians (covered pixels), half uniform
         vis = np.nonzero(proj["valid"].numpy())[0]
@@ -46,19 +52,19 @@ def workload():
         ys = np.concatenate([ys, rng.integers(0, cam.height, PIX_PER_CAM // 2)]).astype(np.float64)
         keep = np.unique(ys * cam.width + xs, return_index=True)[1]
         samples.append((xs[keep], ys[keep]))
-    return scene, cams, dyn_idx, offsets, projs, samples
+    return scene, cams, dyn_idx, offsets, projs, samples, sample_cams
 
 
 @pytest.mark.parametrize("tile,batch", [(32, 256), (16, 256)])
 def test_fullsize_sampled_forward(dass, workload, tile, batch):
     from paper_2411_14847_gb300 import raster
-    scene, cams, _, _, projs, samples = workload
+    scene, cams, _, _, projs, samples, sample_cams = workload
     fr = raster.Frame(cams, scene.n, tile=tile, batch=batch)
     imgs = fr.render(raster.to_device(scene.arrays()))
     tfs = fr.pixel_views(fr.T_final)
     torch.cuda.synchronize()
     n_flag = 0
-    for c, proj, (xs, ys) in zip(SAMPLE_CAMS, projs, samples):
+    for c, proj, (xs, ys) in zip(sample_cams, projs, samples):
         order = comp.depth_order(proj)
         ref = comp.composite_pixels(proj, torch.tensor(xs), torch.tensor(ys), order=order, want_flags=True)
         gi = imgs[c].cpu().double()
@@ -82,14 +88,14 @@ def test_fullsize_sampled_forward(dass, workload, tile, batch):
 
 def test_fullsize_sampled_gradients(dass, workload):
     from paper_2411_14847_gb300 import dass as D, raster
-    scene, cams, _, _, projs, samples = workload
+    scene, cams, _, _, projs, samples, sample_cams = workload
     fr = raster.Frame(cams, scene.n, tile=32, batch=256)
     g = raster.to_device(scene.arrays())
     fr.render(g)
     rng = np.random.default_rng(5)
     bases = np.cumsum([0] + [3 * cam.width * cam.height for cam in cams])
     idx, vals, pixel_grads = [], [], []
-    for c, (xs, ys) in zip(SAMPLE_CAMS, samples):
+    for c, (xs, ys) in zip(sample_cams, samples):
         cam = cams[c]
         gvals = rng.normal(size=(len(xs), 3))
         for ch in range(3):
@@ -105,7 +111,7 @@ def test_fullsize_sampled_gradients(dass, workload):
            "d_sh": torch.empty_like(g["sh"])}
     D.dass_preprocess_bwd(g, cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL)
     torch.cuda.synchronize()
-    ref = og.image_vjp(scene.arrays(), [cams[c] for c in SAMPLE_CAMS], 3, pixel_grads)
+    ref = og.image_vjp(scene.arrays(), [cams[c] for c in sample_cams], 3, pixel_grads)
     for k in og.PARAMS:
         got = out["d_" + k].cpu().numpy()
         want = ref[k].numpy()
@@ -118,7 +124,7 @@ def test_fullsize_graph_step_equals_composed_calls(dass, workload):
     of the individual entry points (loss and dynamic-offset gradients)."""
     from paper_2411_14847_gb300 import dass as D, raster
     from paper_2411_14847_gb300.timestep import ShiftStage
-    scene, cams, dyn_idx, offsets, _, _ = workload
+    scene, cams, dyn_idx, offsets, _, _, _ = workload
     g = raster.to_device(scene.arrays())
     tfr = raster.Frame(cams, scene.n, tile=32, batch=256)
     tfr.render(raster.to_device(synth.perturbed(scene, 2003).arrays()))
