@@ -13,11 +13,12 @@
  *    the host before anything is launched; DASS_ERR_CUDA reports a failed launch or CUDA
  *    call (see dass_last_error()).
  *  - Memory: every array argument is a DEVICE pointer owned by the caller, except where a
- *    parameter says "host". The library never allocates device memory. Scratch memory is
- *    a caller-provided `workspace` whose size the matching *_workspace() query returns.
+ *    parameter says "host". The library never allocates device memory (dass_bin_sort_static
+ *    uses one file-scope device array instead). Scratch memory is a caller-provided
+ *    `workspace` whose size the matching *_workspace() query returns.
  *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls only
- *    enqueue work; none synchronises the host except dass_step and dass_timestep where
- *    documented. Results are valid once the stream reaches them.
+ *    enqueue work; none synchronises the host except dass_step, as documented there.
+ *    Results are valid once the stream reaches them.
  *  - Layout: float32, structure of arrays, N-major, contiguous. Gaussians:
  *      means[N][3], log_scales[N][3], quats[N][4] (w,x,y,z; need not be unit),
  *      opacity_logit[N], sh[N][K][3] with K = (sh_degree+1)^2 real-SH coefficients
