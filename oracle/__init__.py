@@ -22,7 +22,10 @@ Modules:
   stages     -- selective inheritance (Eq. 1), dynamics-aware shift (Sec. 3.3),
                 masked Adam, error map + Alg. 1 projection + Eq. 4 selection + spawn (Sec. 3.4)
   binning    -- brute-force (tile, depth, index) ordering in FP32 for the tile-list check
-  grad       -- end-to-end loss gradients by autograd through all of the above
+  grad       -- end-to-end loss gradients by autograd through all of the above, the learned
+                inheritance mask's straight-through gradient (Eq. 1-2)
+  field      -- hash-encoding deformation fields H_dyn / H_st (Sec. 3.3, App. B.2)
+  dynamics   -- identity-feature rendering and the per-Gaussian dynamics query (Sec. 3.3, App. A.2)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, library routines, brute force, invariants or finite differences,
