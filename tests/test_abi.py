@@ -90,3 +90,35 @@ def test_host_side_layout_checks(lib):
     cams = dass.cameras(synth.arc_cameras(2, 4.0, 100, 50))
     assert lib.dass_render_features(aligned, aligned, aligned, cams, 2, 16, misaligned, 16, 10, aligned, None) == -1
     assert lib.dass_render_features(aligned, aligned, aligned, cams, 2, 16, aligned, 16, 1 << 31, aligned, None) == -1
+
+
+def test_host_side_field_and_loss_checks(lib):
+    """Deformation-field descriptors and the cached-loss statistics are validated on the host:
+    a malformed field is refused, an empty row set succeeds without a launch, a (levels,
+    features) shape without a compiled kernel reports DASS_ERR_UNSUPPORTED before launching,
+    and misaligned statistics pairs are refused."""
+    from paper_2411_14847_gb300 import dass, synth
+    f = dass.dass_field()
+    f.levels, f.features, f.log2_table, f.hidden = 16, 2, 14, 64
+    for i in range(16):
+        f.res[i] = 16 + i
+    for d in range(3):
+        f.bbox_min[d], f.bbox_max[d] = -1.0, 1.0
+    for k in ("table", "w1", "b1", "w2", "b2"):
+        setattr(f, k, 256)
+    ok = C.c_void_p(256)
+    assert lib.dass_field_fwd(C.byref(f), 0, None, ok, ok, None) == 0          # empty: no launch
+    assert lib.dass_field_fwd(C.byref(f), -1, None, ok, ok, None) == -1
+    bad = dass.dass_field.from_buffer_copy(f)
+    bad.features = 3
+    assert lib.dass_field_fwd(C.byref(bad), 5, None, ok, ok, None) == -1      # features not in {2, 4}
+    bad = dass.dass_field.from_buffer_copy(f)
+    bad.hidden = 32
+    assert lib.dass_field_fwd(C.byref(bad), 5, None, ok, ok, None) == -1      # hidden width fixed at 64
+    odd = dass.dass_field.from_buffer_copy(f)
+    odd.levels = 12
+    assert lib.dass_field_fwd(C.byref(odd), 5, None, ok, ok, None) == -6      # no kernel for 12 levels
+    cams = dass.cameras(synth.arc_cameras(2, 4.0, 100, 50))
+    assert lib.dass_loss_target_stats(ok, cams, 2, C.c_void_p(260), None) == -1
+    assert lib.dass_loss_cached(ok, ok, C.c_void_p(260), cams, 2, C.c_float(0.2), ok, ok, ok, 1 << 30, None) == -1
+    assert lib.dass_loss_cached(ok, ok, ok, cams, 2, C.c_float(1.5), ok, ok, ok, 1 << 30, None) == -1   # lambda
