@@ -218,7 +218,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "iters_per_timestep": args.iters, "extrapolated": True},
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "cams": args.cams,
+                       "resolution": f"{args.width}x{args.height}", "iters_per_timestep": args.iters,
+                       "extrapolated": True},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
