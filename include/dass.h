@@ -143,8 +143,20 @@ typedef struct dass_scene {
 int dass_preprocess_scenes(const dass_scene* scenes /* host */, const dass_camera* cams /* host */,
                            int n_cams, int tile, int64_t rec_stride, dass_splat* splats, void* stream);
 
+/* Packed serving form (same render, no padding): camera c's records are the segment
+ * splats[rec_offsets[c] + g], g < scenes[c].n, with rec_offsets (host, n_cams + 1 values)
+ * rec_offsets[0] = 0 and rec_offsets[c + 1] = rec_offsets[c] + scenes[c].n, total < 2^32.
+ * A batch of requests of small and large scenes then projects and sorts sum_c n_c records instead
+ * of n_cams * max_c n_c. Pair with dass_bin_sort_packed (same offsets) and dass_render_fwd.
+ * DASS_ERR_INVALID_ARG if the offsets do not match the scene sizes. */
+int dass_preprocess_scenes_packed(const dass_scene* scenes /* host */, const dass_camera* cams /* host */,
+                                  int n_cams, int tile, const int64_t* rec_offsets /* host */,
+                                  dass_splat* splats, void* stream);
+
 /* Bytes of scratch that dass_bin_sort needs for n_records = n_cams * rec_stride records,
- * `pair_capacity` (tile, Gaussian) pairs and `tiles_total` tiles. */
+ * `pair_capacity` (tile, Gaussian) pairs and `tiles_total` tiles. n_records < 2^32 and
+ * pair_capacity < 2^31 (sorted-pair positions are 32-bit signed in the compositing kernels),
+ * else DASS_ERR_INVALID_ARG. */
 int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total,
                             size_t* bytes);
 
@@ -157,12 +169,24 @@ int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t ti
  * passes run on the pairs. Outputs: pair_rec[M] (record id per sorted pair),
  * tile_ranges[2*tiles_total] ([start, end) per tile, 0,0 when empty) and
  * counters[0] = M, counters[1] = 1 if M > pair_capacity (pairs beyond the capacity are
- * dropped: the render is then incomplete and the caller must grow and rerun).
- * Returns DASS_ERR_OOM if workspace_bytes < dass_bin_sort_workspace(). */
+ * dropped: the render is then incomplete and the caller must grow and rerun; a pair count of
+ * 2^31 or more cannot be stored by any capacity the call accepts).
+ * Returns DASS_ERR_INVALID_ARG if pair_capacity >= 2^31 and DASS_ERR_OOM if workspace_bytes <
+ * dass_bin_sort_workspace(). */
 int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camera* cams /* host */,
                   int n_cams, int tile, uint32_t* pair_rec, int64_t pair_capacity,
                   uint32_t* tile_ranges, int64_t* counters, void* workspace,
                   size_t workspace_bytes, void* stream);
+
+/* dass_bin_sort over packed per-camera record segments (camera c owns records
+ * [rec_offsets[c], rec_offsets[c + 1]), rec_offsets a host array of n_cams + 1 non-decreasing values
+ * with rec_offsets[0] = 0 and total < 2^32), e.g. the output of dass_preprocess_scenes_packed. Same
+ * outputs, order and errors as dass_bin_sort; the workspace is dass_bin_sort_workspace(
+ * rec_offsets[n_cams], pair_capacity, tiles_total). */
+int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_offsets /* host */,
+                         const dass_camera* cams /* host */, int n_cams, int tile, uint32_t* pair_rec,
+                         int64_t pair_capacity, uint32_t* tile_ranges, int64_t* counters, void* workspace,
+                         size_t workspace_bytes, void* stream);
 
 /* Size of the static device scratch array used by dass_bin_sort_static (64 MiB). */
 #define DASS_BIN_SORT_STATIC_BYTES (64ull << 20)
@@ -179,7 +203,9 @@ int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camer
  *    DASS_BIN_SORT_STATIC_BYTES (e.g. 500k records with 4M pairs fit); larger requests return
  *    DASS_ERR_OOM with an explanation in dass_last_error() and launch nothing.
  *  - Set-up: the first call on a device looks up the device address of the array (once per
- *    device, with that device current); make that first call before any stream capture.
+ *    device, with that device current); make that first call before any stream capture. The
+ *    address is kept for the life of the process: do not use this entry point across a
+ *    cudaDeviceReset or another teardown of the device's primary context.
  *  - Sharing: every call uses the same array, which keeps the previous call's contents; the
  *    sort writes every scratch word before reading it, so nothing needs clearing. Calls whose
  *    work overlaps on the GPU (other streams, other threads) race on the array: serialise them. */

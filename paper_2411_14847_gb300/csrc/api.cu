@@ -18,7 +18,7 @@ int preprocess_launch(long long n, int deg, const float* means, const float* log
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                       dass_splat* splats, cudaStream_t st);
 int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
-                             cudaStream_t st);
+                             cudaStream_t st, long long n_max = 0);
 int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                           const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                           const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
@@ -118,13 +118,20 @@ int check_launch(const char* what) {
     return DASS_OK;
 }
 
-bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec_stride, CamTable* out) {
+bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec_stride, CamTable* out,
+                    const int64_t* rec_offsets) {
     if (!cams || n_cams < 1 || n_cams > DASS_MAX_CAMERAS) return false;
     if (tile != 8 && tile != 16 && tile != 32) return false;
+    if (rec_offsets) {
+        if (rec_offsets[0] != 0) return false;
+        for (int i = 0; i < n_cams; ++i)
+            if (rec_offsets[i + 1] < rec_offsets[i]) return false;
+        if (rec_offsets[n_cams] >= (1ll << 32)) return false;
+    }
     std::memset(out, 0, sizeof(CamTable));
     out->n = n_cams;
     out->tile = tile;
-    out->rec_stride = rec_stride;
+    out->rec_stride = rec_offsets ? 0 : rec_stride;
     long long tiles = 0, pix = 0;
     for (int i = 0; i < n_cams; ++i) {
         const dass_camera& c = cams[i];
@@ -156,7 +163,7 @@ bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec
         ci.tiles_y = (c.height + tile - 1) / tile;
         ci.tile_base = (int)tiles;
         ci.pix_base = pix;
-        ci.rec_base = (long long)i * rec_stride;
+        ci.rec_base = rec_offsets ? (long long)rec_offsets[i] : (long long)i * rec_stride;
         tiles += (long long)ci.tiles_x * ci.tiles_y;
         pix += (long long)c.width * c.height;
     }
@@ -230,9 +237,28 @@ DASS_API int dass_preprocess_scenes(const dass_scene* scenes, const dass_camera*
     return preprocess_scenes_launch(scenes, deg, ct, splats, as_stream(stream));
 }
 
+DASS_API int dass_preprocess_scenes_packed(const dass_scene* scenes, const dass_camera* cams, int n_cams, int tile,
+                                          const int64_t* rec_offsets, dass_splat* splats, void* stream) {
+    if (!scenes || !rec_offsets || n_cams < 1 || n_cams > DASS_MAX_CAMERAS) return DASS_ERR_INVALID_ARG;
+    int deg = scenes[0].sh_degree;
+    if (deg < 0 || deg > 3) return DASS_ERR_INVALID_ARG;
+    long long n_max = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const dass_scene& sc = scenes[c];
+        if (sc.sh_degree != deg || sc.n < 0 || rec_offsets[c + 1] - rec_offsets[c] != sc.n) return DASS_ERR_INVALID_ARG;
+        if (sc.n > 0 && (!sc.means || !sc.log_scales || !sc.quats || !sc.opacity_logit || !sc.sh))
+            return DASS_ERR_INVALID_ARG;
+        n_max = sc.n > n_max ? sc.n : n_max;
+    }
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct, rec_offsets)) return DASS_ERR_INVALID_ARG;
+    if (rec_offsets[n_cams] > 0 && !splats) return DASS_ERR_INVALID_ARG;
+    return preprocess_scenes_launch(scenes, deg, ct, splats, as_stream(stream), n_max);
+}
+
 DASS_API int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total, size_t* bytes) {
     if (n_records < 0 || pair_capacity < 0 || tiles_total < 0 || !bytes) return DASS_ERR_INVALID_ARG;
-    if (n_records >= (1ll << 32) || pair_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (n_records >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     *bytes = bin_sort_workspace_bytes(n_records, pair_capacity);
     return DASS_OK;
 }
@@ -244,7 +270,23 @@ DASS_API int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const d
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
     long long n_rec = (long long)n_cams * rec_stride;
-    if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    // sorted-pair positions are held as int32 by the compositing kernels: capacity < 2^31
+    if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
+    if (n_rec > 0 && (!splats || !pair_rec || !workspace)) return DASS_ERR_INVALID_ARG;
+    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity)) return DASS_ERR_OOM;
+    return bin_sort_launch(splats, n_rec, ct, pair_rec, pair_capacity, tile_ranges, (long long*)counters, workspace,
+                           workspace_bytes, as_stream(stream));
+}
+
+DASS_API int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_offsets, const dass_camera* cams,
+                                 int n_cams, int tile, uint32_t* pair_rec, int64_t pair_capacity,
+                                 uint32_t* tile_ranges, int64_t* counters, void* workspace, size_t workspace_bytes,
+                                 void* stream) {
+    if (!rec_offsets || pair_capacity < 0 || !tile_ranges || !counters) return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, 0, &ct, rec_offsets)) return DASS_ERR_INVALID_ARG;
+    long long n_rec = rec_offsets[n_cams];
+    if (pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     if (n_rec > 0 && (!splats || !pair_rec || !workspace)) return DASS_ERR_INVALID_ARG;
     if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity)) return DASS_ERR_OOM;
     return bin_sort_launch(splats, n_rec, ct, pair_rec, pair_capacity, tile_ranges, (long long*)counters, workspace,
@@ -678,6 +720,7 @@ int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStr
 bool desc_ok(const dass_step_desc* d) {
     if (!d || d->n < 0 || d->n_dyn < 0 || d->sh_degree < 0 || d->sh_degree > 3) return false;
     if (d->n >= (1ll << 31) || (long long)d->n_cams * d->n >= (1ll << 32)) return false;
+    if (d->pair_capacity < 0 || d->pair_capacity >= (1ll << 31)) return false;
     if (!batch_ok(d->batch)) return false;
     if (!d->means || !d->log_scales || !d->quats || !d->opacity_logit || !d->sh || !d->targets) return false;
     if (d->n_dyn > 0 && (!d->dyn_idx || !d->offsets || !d->offset_grad || !d->adam_m || !d->adam_v)) return false;

@@ -66,18 +66,33 @@ struct CamTable {
     int tiles_total;
     int pad;
     long long pixels_total;
-    long long rec_stride;
+    long long rec_stride;   // records per camera; 0 = packed segments (camera c owns [rec_base_c, rec_base_c+1))
     CamInfo c[DASS_MAX_CAMERAS];
 };
 
-// Fill a CamTable on the host. Returns false on bad arguments.
-bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec_stride, CamTable* out);
+// Fill a CamTable on the host. Returns false on bad arguments. With rec_offsets (host, n_cams + 1
+// non-decreasing values starting at 0) camera c's records are [rec_offsets[c], rec_offsets[c + 1])
+// and rec_stride is stored as 0 (packed segments); otherwise camera c's records start at c * rec_stride.
+bool make_cam_table(const dass_camera* cams, int n_cams, int tile, long long rec_stride, CamTable* out,
+                    const int64_t* rec_offsets = nullptr);
 
 __device__ __forceinline__ int cam_of_tile(const CamTable& ct, int tile_id) {
     int lo = 0, hi = ct.n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (ct.c[mid].tile_base <= tile_id) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Camera of a record: a division for a uniform record stride, else the last camera whose segment
+// starts at or before the record (empty segments share their start with the next camera's).
+__device__ __forceinline__ int cam_of_record(const CamTable& ct, long long rec) {
+    if (ct.rec_stride > 0) return (int)(rec / ct.rec_stride);
+    int lo = 0, hi = ct.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ct.c[mid].rec_base <= rec) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

@@ -30,6 +30,9 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_sort_scratch on the current device, looked up once per device. In host
 // code the symbol names a host-side stand-in, so only this address may be given to kernels.
+// The cached address belongs to the device's context at lookup time: a cudaDeviceReset (or any
+// teardown of the primary context) reloads the module at another address, so this entry point
+// must not be used across such a reset.
 int scratch_for_current_device(void** out) {
     int dev = -1;
     DASS_CHECK_CUDA(cudaGetDevice(&dev));
@@ -57,7 +60,7 @@ DASS_API int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, 
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, rec_stride, &ct)) return DASS_ERR_INVALID_ARG;
     long long n_rec = (long long)n_cams * rec_stride;
-    if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     if (n_rec > 0 && (!splats || !pair_rec)) return DASS_ERR_INVALID_ARG;
     size_t need = bin_sort_workspace_bytes(n_rec, pair_capacity);
     if (need > kScratchBytes) {

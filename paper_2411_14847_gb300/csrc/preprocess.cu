@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, P
     for (int ci = 0; ci < ct.n; ++ci) write_record<K>(ct.c[ci], ct.tile, deg, p, o, Sig, coef, out + ct.c[ci].rec_base + g);
 }
 
-// Serving form: camera c shows its own scene; thread (g, c) writes record c * rec_stride + g,
-// culled (radius 0) for g beyond that scene's Gaussian count.
+// Serving form: camera c shows its own scene; thread (g, c) writes record rec_base_c + g. With a
+// uniform record stride the records g in [n_c, rec_stride) are written as culled (radius 0); with
+// packed segments (rec_stride 0) camera c has exactly n_c records.
 struct SceneTable {
     Params prm[DASS_MAX_CAMERAS];
     long long n[DASS_MAX_CAMERAS];
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(128) preprocess_scenes_kernel(int deg, SceneTa
                                                                 dass_splat* __restrict__ out) {
     const int ci = blockIdx.y;
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ct.rec_stride) return;
+    if (g >= (ct.rec_stride > 0 ? ct.rec_stride : st.n[ci])) return;
     const CamInfo& cam = ct.c[ci];
     dass_splat* rec = out + cam.rec_base + g;
     if (g >= st.n[ci]) {
@@ -469,8 +470,9 @@ int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass
 }
 
 template <int K>
-int launch_pre_scenes(int deg, const SceneTable& stb, const CamTable& ct, dass_splat* out, cudaStream_t st) {
-    dim3 grid(div_up(ct.rec_stride, 128), ct.n);
+int launch_pre_scenes(int deg, const SceneTable& stb, const CamTable& ct, long long rows, dass_splat* out,
+                      cudaStream_t st) {
+    dim3 grid(div_up(rows, 128), ct.n);
     preprocess_scenes_kernel<K><<<grid, 128, 0, st>>>(deg, stb, ct, out); count_launch();
     return check_launch("preprocess_scenes_kernel");
 }
@@ -501,19 +503,20 @@ int preprocess_launch(long long n, int deg, const float* means, const float* log
 }
 
 int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
-                             cudaStream_t st) {
+                             cudaStream_t st, long long n_max) {
     static thread_local SceneTable stb;
     for (int c = 0; c < ct.n; ++c) {
         stb.prm[c] = Params{scenes[c].means, scenes[c].log_scales, scenes[c].quats, scenes[c].opacity_logit,
                             scenes[c].sh, nullptr};
         stb.n[c] = scenes[c].n;
     }
-    if (ct.rec_stride <= 0) return DASS_OK;
+    const long long rows = ct.rec_stride > 0 ? ct.rec_stride : n_max;   // threads per camera
+    if (rows <= 0) return DASS_OK;
     switch (deg) {
-        case 0: return launch_pre_scenes<1>(deg, stb, ct, splats, st);
-        case 1: return launch_pre_scenes<4>(deg, stb, ct, splats, st);
-        case 2: return launch_pre_scenes<9>(deg, stb, ct, splats, st);
-        case 3: return launch_pre_scenes<16>(deg, stb, ct, splats, st);
+        case 0: return launch_pre_scenes<1>(deg, stb, ct, rows, splats, st);
+        case 1: return launch_pre_scenes<4>(deg, stb, ct, rows, splats, st);
+        case 2: return launch_pre_scenes<9>(deg, stb, ct, rows, splats, st);
+        case 3: return launch_pre_scenes<16>(deg, stb, ct, rows, splats, st);
     }
     return DASS_ERR_INVALID_ARG;
 }

@@ -306,8 +306,7 @@ __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long lon
                                  uint32_t* __restrict__ counts) {
     long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (rec >= n_rec) return;
-    int ci = (int)(rec / ct.rec_stride);
-    const CamInfo& cam = ct.c[ci];
+    const CamInfo& cam = ct.c[cam_of_record(ct, rec)];
     Footprint f;
     float depth;
     int cnt = 0;
@@ -390,7 +389,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     float depth;
     int ci = 0, y0 = 0, y1 = -1;
     if (active && record_footprint(splats, rec, f, depth)) {
-        ci = (int)(rec / ct.rec_stride);
+        ci = cam_of_record(ct, rec);
         const CamInfo& cam = ct.c[ci];
         int x0, x1;
         footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);

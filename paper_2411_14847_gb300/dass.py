@@ -81,7 +81,9 @@ _SIGS = {
     "dass_render_work": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P]),
     "dass_preprocess": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P]),
     "dass_preprocess_scenes": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _P, _P]),
+    "dass_preprocess_scenes_packed": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P]),
     "dass_bin_sort_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
+    "dass_bin_sort_packed": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort_static": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]),
     "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
@@ -217,15 +219,38 @@ def dass_preprocess(g, cams, tile, splats, keep=None, stream=None):
 
 def dass_preprocess_scenes(scenes, cams, tile, rec_stride, splats, stream=None):
     """scenes: one dict of Gaussian tensors per camera (same SH degree)."""
-    arr = (dass_scene * len(cams))()
+    _call("dass_preprocess_scenes", _scene_array(scenes), cameras(cams), len(cams), tile, rec_stride,
+          _ptr(splats, F32), _stream(stream))
+
+
+def _scene_array(scenes):
+    arr = (dass_scene * len(scenes))()
     for i, g in enumerate(scenes):
-        n = g["means"].shape[0]
-        arr[i].n = n
+        arr[i].n = g["means"].shape[0]
         arr[i].sh_degree = int(round(math.sqrt(g["sh"].shape[1]))) - 1
         for name in ("means", "log_scales", "quats", "opacity_logit", "sh"):
             setattr(arr[i], name, _ptr(g[name], F32).value)
-    _call("dass_preprocess_scenes", arr, cameras(cams), len(cams), tile, rec_stride, _ptr(splats, F32),
-          _stream(stream))
+    return arr
+
+
+def record_offsets(scenes):
+    """Host int64 array [len(scenes) + 1] of packed record segments: 0, n_0, n_0 + n_1, ..."""
+    off = (C.c_int64 * (len(scenes) + 1))()
+    for i, g in enumerate(scenes):
+        off[i + 1] = off[i] + int(g["means"].shape[0])
+    return off
+
+
+def dass_preprocess_scenes_packed(scenes, cams, tile, rec_offsets, splats, stream=None):
+    """scenes: one dict of Gaussian tensors per camera; rec_offsets from record_offsets(scenes)."""
+    _call("dass_preprocess_scenes_packed", _scene_array(scenes), cameras(cams), len(cams), tile, rec_offsets,
+          _ptr(splats, F32), _stream(stream))
+
+
+def dass_bin_sort_packed(splats, rec_offsets, cams, tile, pair_rec, tile_ranges, counters, workspace, stream=None):
+    _call("dass_bin_sort_packed", _ptr(splats, F32), rec_offsets, cameras(cams), len(cams), tile,
+          _ptr(pair_rec, I32), pair_rec.numel(), _ptr(tile_ranges, I32), _ptr(counters, I64), _ptr(workspace, U8),
+          workspace.numel(), _stream(stream))
 
 
 def dass_bin_sort_workspace(n_records, pair_capacity, tiles_total):

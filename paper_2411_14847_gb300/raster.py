@@ -41,6 +41,9 @@ class Frame:
         self._alloc_pairs(cap)
 
     def _alloc_pairs(self, cap):
+        if cap >= 1 << 31:
+            raise D.DassError(f"pair buffer of {cap} pairs (sorted-pair positions are 32-bit: at most 2^31 - 1)",
+                              D.ERR_INVALID_ARG)
         self.pair_capacity = int(cap)
         self.pair_rec = torch.empty(max(1, self.pair_capacity), dtype=torch.int32, device=self.device)
         ws = D.dass_bin_sort_workspace(self.n_rec, self.pair_capacity, self.tiles_total)

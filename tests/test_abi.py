@@ -66,9 +66,14 @@ def test_host_side_argument_checks(lib):
     assert lib.dass_densify_select(10, None, None, None, None, 1e-4, -1.0, 10, None, None, None, 0, None) == -1
     b = C.c_size_t()
     assert lib.dass_bin_sort_workspace(1000, 5000, 10, C.byref(b)) == 0 and b.value > 0
+    # pair positions are int32 in the compositing kernels: capacities of 2^31 or more are refused
+    assert lib.dass_bin_sort_workspace(1000, (1 << 31) - 1, 10, C.byref(b)) == 0
+    assert lib.dass_bin_sort_workspace(1000, 1 << 31, 10, C.byref(b)) == -1
     # a workspace smaller than the query is reported as DASS_ERR_OOM
     fake = C.c_void_p(16)
     assert lib.dass_bin_sort(fake, 10, cams, 2, 16, fake, 100, fake, fake, fake, 8, None) == -3
+    assert lib.dass_bin_sort(fake, 10, cams, 2, 16, fake, 1 << 31, fake, fake, fake, 1 << 40, None) == -1
+    assert lib.dass_bin_sort_static(fake, 10, cams, 2, 16, fake, 1 << 31, fake, fake, None) == -1
     # empty inputs are no-ops that succeed without launching
     assert lib.dass_shift(0, None, None, None, None, None, None, None) == 0
     assert lib.dass_preprocess(0, 0, None, None, None, None, None, None, cams, 2, 16, None, None) == 0

@@ -479,3 +479,91 @@ def test_prune_low_opacity_closed_form():
     assert out["opacity_logit"].tolist() == [-9.0, -4.0, 2.0, 0.0]
     assert out["means"][:, 0].tolist() == [0.0, 9.0, 3.0, 12.0]
     assert new_var.tolist() == [False, False, True, True]
+
+
+# ------------------------------------------------------------- densification-statistics visibility
+
+def _stats_proj(u, v, sigma, opacity, valid=True):
+    """Projection dict of isotropic splats: cov2d = sigma^2 I, so lambda_max = sigma^2 exactly."""
+    n = len(u)
+    s2 = np.asarray(sigma, dtype=np.float64) ** 2
+    return dict(mean2d=torch.tensor(np.stack([u, v], 1), dtype=DT),
+                cov2d=torch.tensor(np.stack([s2, np.zeros(n), s2], 1), dtype=DT),
+                opacity=torch.tensor(opacity, dtype=DT),
+                valid=torch.tensor(np.broadcast_to(valid, (n,)).copy(), dtype=torch.bool))
+
+
+def test_stats_visible_edges_near_plane_and_opacity():
+    """Visibility rule of the positional-gradient statistics (Sec. 3.4, reading: radius > 0 and
+    the square of half-side r around mean2D overlapping the pixel-centre box [0, W-1] x [0, H-1]).
+    sigma = 2 px and opacity 1 give r = ceil(2 sqrt(2 ln 255 + 0.01)) = ceil(6.664) = 7, so a
+    splat is visible exactly while its centre lies within 7 px outside an edge: each edge is
+    probed at r (visible) and r + 1 (not), plus half-pixel offsets."""
+    cam = _cam(32, 24)
+    W, H = 32, 24
+    r = 7
+    assert math.ceil(2.0 * math.sqrt(2.0 * math.log(255.0) + 0.01)) == r
+    cx, cy = 15.0, 11.0
+    cases = [  # (u, v, visible)
+        (-r, cy, True), (-r - 1, cy, False), (-r + 0.5, cy, True), (-r - 0.5, cy, False),
+        (W - 1 + r, cy, True), (W - 1 + r + 1, cy, False), (W - 1 + r - 0.5, cy, True), (W - 1 + r + 0.5, cy, False),
+        (cx, -r, True), (cx, -r - 1, False), (cx, -r - 0.5, False),
+        (cx, H - 1 + r, True), (cx, H - 1 + r + 1, False), (cx, H - 1 + r + 0.5, False),
+        (-r, -r, True), (W - 1 + r, H - 1 + r, True), (-r - 1, H - 1 + r, False),   # corners
+    ]
+    u = np.array([c[0] for c in cases], dtype=np.float64)
+    v = np.array([c[1] for c in cases], dtype=np.float64)
+    vis = og.stats_visible(_stats_proj(u, v, np.full(len(cases), 2.0), np.ones(len(cases))), cam)
+    assert vis.tolist() == [c[2] for c in cases]
+    # behind the near plane (valid = False): never visible, even at the image centre
+    assert og.stats_visible(_stats_proj([cx], [cy], [2.0], [1.0], valid=False), cam).tolist() == [False]
+    # 255 o <= 1 has no footprint (r = 0); just above 1/255 the radius is 1 and a centred splat counts
+    o = np.array([1.0 / 255.0, 0.0039, 0.004])
+    vis = og.stats_visible(_stats_proj(np.full(3, cx), np.full(3, cy), np.full(3, 2.0), o), cam)
+    assert vis.tolist() == [False, False, True]
+    # the radius, not the centre, decides: a centre 1 px outside with r = 1 is visible, 2 px is not
+    r1 = _stats_proj(np.array([-1.0, -2.0]), np.full(2, cy), np.full(2, 2.0), np.full(2, 0.004))
+    assert G.footprint_radius(r1["cov2d"], r1["opacity"]).tolist() == [1.0, 1.0]
+    assert og.stats_visible(r1, cam).tolist() == [True, False]
+
+
+# ------------------------------------------------------------- near-threshold alternatives
+
+def test_alternatives_single_result_away_from_thresholds():
+    """Three splats at the pixel with alphas far from 1/255 and T(1 - alpha) far from 1e-4:
+    exactly one alternative, equal to the hand-composited colour."""
+    proj = _manual_proj([[0.0, 0.0]] * 3, [[1, 0, 1]] * 3, [0.5, 0.3, 0.2],
+                        [[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]], [1.0, 2.0, 3.0])
+    alts = comp.pixel_alternatives(proj, 0.0, 0.0)
+    assert len(alts) == 1
+    col, T = alts[0]
+    expect = [0.5, 0.3 * 0.5, 0.2 * 0.5 * 0.7]
+    np.testing.assert_allclose(col, expect, atol=1e-15)
+    assert T == pytest.approx(0.5 * 0.7 * 0.8, abs=1e-15)
+
+
+def test_alternatives_exactly_two_at_an_alpha_tie():
+    """A splat whose alpha is exactly 1/255 at the pixel may be skipped or blended: exactly two
+    alternatives, with and without its contribution; 1% above the threshold there is one."""
+    a_tie = 1.0 / 255.0
+    proj = _manual_proj([[0.0, 0.0]] * 2, [[1, 0, 1]] * 2, [0.5, a_tie], [[1.0, 0, 0], [0, 1.0, 0]], [1.0, 2.0])
+    alts = comp.pixel_alternatives(proj, 0.0, 0.0)
+    assert len(alts) == 2
+    cols = sorted(tuple(a[0]) for a in alts)
+    np.testing.assert_allclose(cols[0], [0.5, 0.0, 0.0], atol=1e-15)             # skipped
+    np.testing.assert_allclose(cols[1], [0.5, a_tie * 0.5, 0.0], atol=1e-15)      # blended
+    assert sorted(a[1] for a in alts) == pytest.approx([0.5 * (1 - a_tie), 0.5])
+    proj["opacity"] = torch.tensor([0.5, 1.01 * a_tie], dtype=DT)
+    assert len(comp.pixel_alternatives(proj, 0.0, 0.0)) == 1
+
+
+def test_alternatives_exactly_two_at_a_stop_tie():
+    """T (1 - alpha) within 0.1% of 1e-4 may stop or blend: exactly two alternatives."""
+    # alpha 0.99 then alpha 0.99 * (1 - 1e-6): T before the second is 0.01, T(1 - alpha) ~ 1e-4
+    a2 = 0.99 * (1.0 - 1e-6)
+    proj = _manual_proj([[0.0, 0.0]] * 2, [[1, 0, 1]] * 2, [1.0, a2], [[1.0, 0, 0], [0, 1.0, 0]], [1.0, 2.0])
+    alts = comp.pixel_alternatives(proj, 0.0, 0.0)
+    assert len(alts) == 2
+    cols = sorted(tuple(a[0]) for a in alts)
+    np.testing.assert_allclose(cols[0], [0.99, 0.0, 0.0], atol=1e-15)              # stopped
+    np.testing.assert_allclose(cols[1], [0.99, a2 * 0.01, 0.0], atol=1e-12)        # blended
