@@ -59,14 +59,57 @@ FLOP_BWD_ADD = 56
 # Backward of a pair whose Gaussian only needs dL/dmean2D (static in the shift stage): the same
 # terms up to the dpow dx, dpow dy sums (29) and 2 reduction adds = 31 flop.
 FLOP_BWD_MEAN_ADD = 31
-# DRAM bytes (read + write) of one full-size render_bwd launch from ncu (6-camera capture of the
-# current kernel, 264.3 MB for 8.47M pairs, scaled by pairs to the 28.34M pairs of 20 cameras,
-# profiles/render_bwd_config_c_6cams.txt); None once the kernel changes after that capture.
-RENDER_BWD_TRAFFIC = 8.80e8
-# Issue utilisation of the same render_bwd capture (smsp__issue_active, fraction of cycles a warp
-# scheduler issued): the kernel is bound by instruction issue, not by FP32 throughput, so its
-# fraction of the FP32 peak is read next to this figure. None once the kernel changes.
-RENDER_BWD_ISSUE_ACTIVE = 0.726
+# Algorithmic bytes of the per-Gaussian stage kernels. shift: read index 4 + mean 12 + quaternion 16
+# + offsets 28, write mean 12 + quaternion 16 = 88 B per dynamic Gaussian; shift backward: read index
+# 4 + offsets 28 + quaternion 16 + mean and quaternion gradients 28, write offset gradient 28 = 104 B;
+# masked Adam: read parameter, gradient, m, v and write parameter, m, v = 28 B per parameter, 7 per
+# dynamic Gaussian; inheritance copy: the surviving row read and written (2 x the row bytes) plus the
+# flag and logit read (5 B) per input row; error pass: image and target read (24 B), error written and
+# read back (8 B) and 4 radix-select passes over it (16 B) per pixel, plus the mean read and the
+# selection flag written (13 B) per Gaussian.
+SHIFT_DYN_BYTES = 88
+SHIFT_BWD_DYN_BYTES = 104
+ADAM_PARAM_BYTES = 28
+INHERIT_ROW_FLAG_BYTES = 5
+ERROR_PIX_BYTES = 48
+ERROR_GAUSS_BYTES = 13
+
+
+def profile_figures(kernel_file):
+    """DRAM traffic and issue utilisation of the dominant kernel from its committed ncu summary
+    (profiles/<name>.txt: lines `source_sha16: ...`, `traffic_per_launch: ...`, `issue_active: ...`),
+    valid only while the kernel source still has the hash the capture was taken from."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    src = os.path.join(ROOT, "paper_2411_14847_gb300", "csrc", "render.cu")
+    try:
+        fields = dict(l.split(":", 1) for l in open(path) if ":" in l)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if fields.get("source_sha16", "").strip() != sha:
+        return None
+    return {"traffic": float(fields["traffic_per_launch"]), "issue_active": float(fields["issue_active"]),
+            "source": "profiles/" + kernel_file}
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def measured_hbm_gbs():
@@ -221,7 +264,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "gaussians": args.n, "cams": args.cams,
                        "resolution": f"{args.width}x{args.height}", "iters_per_timestep": args.iters,
                        "extrapolated": True},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
+                             "sample": sample, "spread": [round(min(vals), 1), round(max(vals), 1)]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -383,22 +427,24 @@ def main():
         (tile, batch), table = autotune(g0, cams, targets, dyn_t, off_t, iters=3)
 
     k_max = 5000
-    n_max = args.n + k_max * (args.warmup + args.steps + args.e2e_steps + 3)
+    n_max = args.n + k_max * (args.warmup + args.steps + 3)
     ts = Timestep(cams, n_max, 3, tile=tile, batch=batch, lambda_dssim=0.2, n_shift=args.iters, k_max=k_max)
     ts.load(scene.arrays())
 
-    def one_timestep(t, tgt):
-        return ts.run(t, tgt, dyn_t, off_t.clone(), z=z)
+    def one_timestep(t, tgt, **kw):
+        return ts.run(t, tgt, dyn_t, off_t.clone(), z=z, **kw)
 
     t = 1
     for _ in range(args.warmup):
         one_timestep(t, targets)
         t += 1
     torch.cuda.synchronize()
+    # the scene the timed steps start from (the end-to-end steps below restart from it)
+    start_state = ({k: v.clone() for k, v in ts.bufs.items()}, ts.is_var.clone(), ts.n, t)
     if world > 1:
         dist.barrier()
 
-    # ---------------- timed region: K whole timesteps, device time by CUDA events
+    # ---------------- timed region: K whole timesteps (dass_timestep), device time by CUDA events
     clocks = ClockSampler(local)
     clocks.start()
     l0 = D.dass_kernel_launches()
@@ -406,12 +452,12 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0.record()
+    e0.record(ts.stream)
     results = []
     for _ in range(args.steps):
         results.append(one_timestep(t, targets))
         t += 1
-    e1.record()
+    e1.record(ts.stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -421,8 +467,10 @@ def main():
     ms_max = replicas.max_over_ranks(ms, dist if world > 1 else None, device=dev)
     value = replicas.seconds_per_timestep(ms_max, args.steps, world)
 
-    # ---------------- dominant kernels, timed standalone on the last iteration's buffers
-    stage = results[-1]["stage"]
+    # ---------------- dominant kernels, timed standalone on one shift-stage iteration's buffers of G_t
+    stage = ShiftStage(ts.view(), cams, targets, dyn_t, off_t.clone(), tile=tile, batch=batch, lambda_dssim=0.2)
+    stage.run(1, D.STEP_BATCHED)
+    torch.cuda.synchronize()
     sfr = stage.frame
     work = torch.zeros(5, dtype=torch.int64, device=dev)
     D.dass_render_work(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch, sfr.image, sfr.T_final,
@@ -467,6 +515,33 @@ def main():
                                                   D.GRAD_MEANS | D.GRAD_QUATS, rows=stage.dyn_idx), reps=5)
     stats_ms = timed(lambda: D.dass_densify_stats(sfr.n, sfr.splats, sfr.splat_grads, cams, stage.stat_accum,
                                                   stage.stat_count), reps=5)
+    # per-Gaussian stage kernels (Sec. 3.2-3.4): shift and its backward, masked Adam, inheritance copy,
+    # error pass
+    n_dyn = int(stage.n_dyn)
+    sh_out_m, sh_out_q = stage.render_means.clone(), stage.render_quats.clone()
+    shift_ms = timed(lambda: D.dass_shift(stage.dyn_idx, stage.offsets, stage.g["means"], stage.g["quats"], sh_out_m,
+                                          sh_out_q), reps=20)
+    shift_bwd_ms = timed(lambda: D.dass_shift_bwd(stage.dyn_idx, stage.offsets, stage.g["quats"], stage.d_means_dyn,
+                                                  stage.d_quats_dyn, stage.offset_grad), reps=20)
+    a_p, a_m, a_v = stage.offsets.clone(), torch.zeros_like(stage.offsets), torch.zeros_like(stage.offsets)
+    a_step = torch.zeros(1, dtype=torch.int32, device=dev)
+    adam_ms = timed(lambda: D.dass_adam(a_p, stage.offset_grad, a_m, a_v, a_step, [1e-3] * 7, 0.9, 0.999, 1e-15,
+                                        increment_step=False), reps=20)
+    gv = ts.view()
+    n_g = ts.n
+    inh_out = {k: torch.empty_like(v) for k, v in gv.items()}
+    inh_var = torch.empty(n_g, dtype=torch.uint8, device=dev)
+    inh_remap = torch.empty(n_g, dtype=torch.int32, device=dev)
+    inh_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    inh_ws = torch.empty(max(1, D.dass_inherit_workspace(n_g)), dtype=torch.uint8, device=dev)
+    inh_m = torch.ones(n_g, device=dev)
+    inherit_ms = timed(lambda: D.dass_inherit(gv, ts.is_var[:n_g], inh_m, False, inh_out, inh_var, inh_remap, inh_n,
+                                              inh_ws), reps=5)
+    n_kept = int(inh_n.item())
+    err_ws = torch.empty(D.dass_error_pass_workspace(cams), dtype=torch.uint8, device=dev)
+    s_err = torch.zeros(n_g, dtype=torch.uint8, device=dev)
+    err_ms = timed(lambda: D.dass_error_pass(sfr.image, stage.targets, cams, 0.95, gv["means"], ts.is_var[:n_g], s_err,
+                                             err_ws), reps=5)
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     mhz = clk["sm_mhz"] or 2070.0
@@ -477,10 +552,12 @@ def main():
     fwd_tf = fwd_flop / (fwd_ms * 1e-3) / 1e12
     dom = "render_bwd" if bwd_ms >= fwd_ms else "render_fwd"
     ach = bwd_tf if dom == "render_bwd" else fwd_tf
+    prof = profile_figures(f"{dom}_config_c.txt") if tile == 32 else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 3),
                 "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-                "traffic": RENDER_BWD_TRAFFIC if (dom == "render_bwd" and tile == 32) else None,
-                "issue_active": RENDER_BWD_ISSUE_ACTIVE if (dom == "render_bwd" and tile == 32) else None,
+                "traffic": prof["traffic"] if prof else None,
+                "issue_active": prof["issue_active"] if prof else None,
+                "ncu_source": prof["source"] if prof else None,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)",
                 "flop_per_launch": bwd_flop if dom == "render_bwd" else fwd_flop,
                 "kernel_ms": round(bwd_ms if dom == "render_bwd" else fwd_ms, 3)}
@@ -492,9 +569,14 @@ def main():
     hbm = {}
     for name, nbytes, ms_ in (("bin_sort", SORT_REC_BYTES * n_rec + SORT_PAIR_BYTES * n_pairs, sort_ms),
                               ("loss", LOSS_PIX_BYTES * 3 * n_px, loss_ms),
-                              ("preprocess", deg_bytes * sfr.n + 48 * n_rec, pre_ms)):
+                              ("preprocess", deg_bytes * sfr.n + 48 * n_rec, pre_ms),
+                              ("shift", SHIFT_DYN_BYTES * n_dyn, shift_ms),
+                              ("shift_bwd", SHIFT_BWD_DYN_BYTES * n_dyn, shift_bwd_ms),
+                              ("adam", ADAM_PARAM_BYTES * 7 * n_dyn, adam_ms),
+                              ("inherit", 2 * deg_bytes * n_kept + INHERIT_ROW_FLAG_BYTES * n_g, inherit_ms),
+                              ("error_pass", ERROR_PIX_BYTES * n_px + ERROR_GAUSS_BYTES * n_g, err_ms)):
         gbs = nbytes / (ms_ * 1e-3) / 1e9
-        hbm[name] = {"bytes": int(nbytes), "ms": round(ms_, 3), "achieved_gbs": round(gbs, 1),
+        hbm[name] = {"bytes": int(nbytes), "ms": round(ms_, 4), "achieved_gbs": round(gbs, 1),
                      "frac": round(gbs / hbm_peak, 4) if hbm_peak else None}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
                "preprocess_ms": round(pre_ms, 3), "loss_ms": round(loss_ms, 3),
@@ -504,6 +586,7 @@ def main():
                "list_prefix_bwd": n_bwd,
                "bin_sort_bytes_per_pair": round(hbm["bin_sort"]["bytes"] / max(1, n_pairs), 1),
                "hbm": hbm, "hbm_peak_gbs": hbm_peak}
+    del inh_out, err_ws
 
     # ---------------- plain form (one launch per camera, no graph) vs batched, per iteration
     plain_st = ShiftStage(ts.view(), cams, targets, dyn_t, off_t.clone(), tile=tile, batch=batch, lambda_dssim=0.2)
@@ -527,7 +610,7 @@ def main():
     # var rows the timesteps above spawned, on the final G_t against the last targets (graph-replayed)
     from paper_2411_14847_gb300.timestep import InheritStage
     inh = None
-    isv = ts.is_var[ts.cur][:ts.n]
+    isv = ts.is_var[:ts.n]
     if int(isv.sum()) > 0:
         ist = InheritStage(ts.view(), isv, cams, targets, tile=tile, batch=batch, lambda_dssim=0.2)
         ist.run(2)                                 # eager iteration + capture
@@ -631,29 +714,32 @@ def main():
     # ---------------- serving under mixed load (continuous batching)
     serve = serve_load([int(r) for r in args.serve_rates.split(",") if r], args.serve_seconds) if rank == 0 else None
 
-    # ---------------- end to end through the public API with host buffers
+    # ---------------- end to end through the C ABI with host buffers: each dass_timestep call uploads
+    # its images from pinned host memory and writes G_t back into pinned host buffers; the steps restart
+    # from the scene the timed steps started from, with the same timestep indices
+    bufs0, isv0, n0, t0 = start_state
+    for k, v in bufs0.items():
+        ts.bufs[k].copy_(v)
+    ts.is_var.copy_(isv0)
+    ts.n = n0
     host_tgt = targets.cpu().pin_memory()
     dev_tgt = torch.empty_like(targets)
-    # G_t comes back into pinned host buffers sized for the scene's capacity (rows [0, n) per step)
-    host_g = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ts.bufs[ts.cur].items()}
-    one_timestep(t, targets)
-    t += 1
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ts.bufs.items()}
+    host_out["is_var"] = torch.empty(ts.is_var.shape, dtype=torch.uint8).pin_memory()
+    del start_state, bufs0
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h2d = d2h = 0
-    a.record()
+    e2e_n = []
+    a.record(ts.stream)
+    te = t0
     for _ in range(args.e2e_steps):
-        dev_tgt.copy_(host_tgt, non_blocking=True)
-        r = ts.run(t, dev_tgt, dyn_t, off_t.clone(), z=z)
-        t += 1
-        gv = ts.view()
-        for k, v in gv.items():
-            host_g[k][:v.shape[0]].copy_(v, non_blocking=True)
-        torch.cuda.current_stream().synchronize()      # the step's result is on the host
-        loss_h = r["loss"]
+        r = one_timestep(te, dev_tgt, targets_host=host_tgt, host_out=host_out)   # returns once G_t is on the host
+        te += 1
         h2d = host_tgt.numel() * 4
-        d2h = sum(v.numel() * 4 for v in gv.values()) + 8
-    b.record()
+        d2h = r["n"] * (4 * (3 + 3 + 4 + 1 + 3 * 16) + 1)
+        e2e_n.append(r["n"])
+    b.record(ts.stream)
     torch.cuda.synchronize()
     e2e_s = a.elapsed_time(b) / 1e3 / args.e2e_steps
 
@@ -661,7 +747,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_iter, secs, threads, det = oracle_sample(scene, cams, args.cpu_pixels)
-        cpu = {"value": per_iter * args.iters, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": per_iter * args.iters, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(),
+               "kind": "oracle",
                "sample": (f"camera 0 projection of {args.n} Gaussians + fwd/bwd of {args.cpu_pixels // 2} and "
                           f"{2 * (args.cpu_pixels // 2)} sampled "
                           f"pixels ({secs:.1f} s), extrapolated to {args.cams} cams x {args.width}x{args.height} "
@@ -676,13 +763,17 @@ def main():
                            "tile": tile, "batch": batch, "autotune_ms_per_iter": table,
                            "l2": "not flushed: per-iteration working set ~1.5 GB >> 129 MB L2",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "gaussians_end": ts.n, "loss_last": results[-1]["loss"]},
+                           "gaussians_start": n0, "gaussians_end": results[-1]["n"],
+                           "loss_last": results[-1]["loss"]},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "kernels": kernels,
                 "plain": plain, "inherit_stage": inh, "densify_stage": den, "field_shift_stage": field_shift,
                 "dynamics_query_ms": round(dyn_query_ms, 3),
                 "paper_schedule": stages, "streaming_schedule": streaming,
                 "render_latency": {"single_view": render, "under_load": serve},
-                "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "path": "dass_timestep with host targets and host G_t buffers (pinned)",
+                        "start_state": "the timed steps' starting scene and timestep indices",
+                        "gaussians": e2e_n},
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:

@@ -17,7 +17,8 @@
  *    uses one file-scope device array instead). Scratch memory is a caller-provided
  *    `workspace` whose size the matching *_workspace() query returns.
  *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls only
- *    enqueue work; none synchronises the host except dass_step, as documented there.
+ *    enqueue work; none synchronises the host except the stage drivers (dass_step,
+ *    dass_inherit_step, dass_densify_step) and dass_timestep, as documented there.
  *    Results are valid once the stream reaches them.
  *  - Layout: float32, structure of arrays, N-major, contiguous. Gaussians:
  *      means[N][3], log_scales[N][3], quats[N][4] (w,x,y,z; need not be unit),
@@ -550,6 +551,191 @@ int dass_step_workspace(const dass_step_desc* d, size_t* bytes);
  * synchronisation and a read of the pair-overflow flag: it returns DASS_ERR_CAPACITY if any
  * iteration overflowed pair_capacity (results of the stage are then unreliable). */
 int dass_step(const dass_step_desc* d, int n_iters, int mode, void* stream);
+
+/* All buffers of one selective-inheritance stage (Sec. 3.2, Eq. 1-2, App. B.2): learns one logit m
+ * per var Gaussian of G_{t-1} against the views of timestep t, every other parameter fixed. One
+ * iteration: keep = Quant(sigmoid(m)) on var rows (1 on base rows) -> projection with opacity and
+ * scale multiplied by keep (Eq. 1) -> bin/sort -> forward -> fidelity loss of Eq. 3 -> backward
+ * (full splat gradients for var rows only) -> dL/dkeep -> straight-through gradient of the loss of
+ * Eq. 2 (fidelity + lambda_inher sum sigmoid(m) over var rows) -> Adam on m (var rows).
+ * Device pointers owned by the caller unless noted. */
+typedef struct dass_inherit_step_desc {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t n_cams;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logit;
+    const float* sh;
+    const uint8_t* is_var;            /* [n] 1 on var rows */
+    const dass_camera* cams;          /* host [n_cams] */
+    const float* targets;             /* images of timestep t, planar like image */
+    int64_t n_var;
+    const int32_t* var_rows;          /* [n_var] the var rows, ascending */
+    float* m;                         /* [n] logits, updated in place on the var rows */
+    uint8_t* keep;                    /* [n] scratch (the rendering mask) */
+    float* m_grad;                    /* [n] scratch */
+    float* adam_m;                    /* [n] */
+    float* adam_v;                    /* [n] */
+    int32_t* adam_step;               /* device int, incremented once per iteration */
+    float* d_keep;                    /* [n_var] dL/dkeep of the last iteration */
+    float lr, beta1, beta2, eps, lambda_dssim, lambda_inher;
+    int32_t tile, batch;
+    dass_splat* splats;               /* [n_cams * n] */
+    dass_splat_grad* splat_grads;     /* [n_cams * n] */
+    uint32_t* pair_rec;               /* [pair_capacity] */
+    int64_t pair_capacity;            /* < 2^31 */
+    uint32_t* tile_ranges;            /* [2 * tiles_total] */
+    int64_t* counters;                /* [4] */
+    float* image;                     /* [pixels * 3] */
+    float* T_final;                   /* [pixels] */
+    int32_t* n_last;                  /* [pixels] */
+    float* dL_dimage;                 /* [pixels * 3] */
+    double* loss;                     /* [1] loss of Eq. 2 at the last iteration */
+    void* workspace;                  /* >= dass_inherit_step_workspace() bytes */
+    size_t workspace_bytes;
+} dass_inherit_step_desc;
+
+int dass_inherit_step_workspace(const dass_inherit_step_desc* d, size_t* bytes);
+
+/* Runs n_iters iterations of the selective-inheritance stage, one iteration captured as a CUDA graph
+ * on `stream` (not the legacy default stream) and replayed; the targets' SSIM window statistics are
+ * computed once into the workspace first. Ends with one stream synchronisation; returns
+ * DASS_ERR_CAPACITY if any iteration overflowed pair_capacity (the learned m is then unreliable;
+ * counters[0] holds the last iteration's pair count). n_var == 0 renders and leaves m unchanged. */
+int dass_inherit_step(const dass_inherit_step_desc* d, int n_iters, void* stream);
+
+/* All buffers of the densification-stage training (Sec. 3.4: the new and inherited var Gaussians
+ * are optimised with the fidelity loss of Eq. 3, base Gaussians fixed). The var rows must be the
+ * contiguous tail [n_base, n) of the arrays (the layout dass_inherit and dass_spawn produce). One
+ * iteration: projection -> bin/sort -> forward -> loss -> backward (full splat gradients for var rows
+ * only) -> parameter gradients of the var rows -> Adam on each parameter slice of the tail with the
+ * learning rates below (the SH degree-0 band and the higher bands separately). */
+typedef struct dass_densify_step_desc {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t n_cams;
+    float* means;                     /* rows [n_base, n) of every parameter are updated in place */
+    float* log_scales;
+    float* quats;
+    float* opacity_logit;
+    float* sh;
+    int64_t n_base;
+    const uint8_t* is_var;            /* [n] 1 exactly on [n_base, n) */
+    const dass_camera* cams;          /* host [n_cams] */
+    const float* targets;
+    /* gradients and Adam moments of the var rows, each (11 + 3K)(n - n_base) floats, parameter-major:
+     * means [n_var][3], log_scales [n_var][3], quats [n_var][4], opacity_logit [n_var], sh [n_var][K][3] */
+    float* grad;
+    float* adam_m;
+    float* adam_v;
+    int32_t* adam_step;
+    float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps, lambda_dssim;
+    int32_t tile, batch;
+    dass_splat* splats;
+    dass_splat_grad* splat_grads;
+    uint32_t* pair_rec;
+    int64_t pair_capacity;
+    uint32_t* tile_ranges;
+    int64_t* counters;
+    float* image;
+    float* T_final;
+    int32_t* n_last;
+    float* dL_dimage;
+    double* loss;                     /* [1] loss of the last iteration */
+    void* workspace;                  /* >= dass_densify_step_workspace() bytes */
+    size_t workspace_bytes;
+} dass_densify_step_desc;
+
+int dass_densify_step_workspace(const dass_densify_step_desc* d, size_t* bytes);
+
+/* Runs n_iters densification-stage iterations (graph capture and replay, one synchronisation at the
+ * end, DASS_ERR_CAPACITY on a pair overflow, as dass_inherit_step). */
+int dass_densify_step(const dass_densify_step_desc* d, int n_iters, void* stream);
+
+/* One whole timestep of the streaming reconstruction (Sec. 3.1: from G_{t-1} and the C views of
+ * timestep t derive G_t):
+ *   1. selective inheritance (Sec. 3.2): unless t is a multiple of erase_every (every var row is then
+ *      erased, App. B.2) or n_inherit == 0 or G_{t-1} has no var rows, n_inherit iterations of the
+ *      inheritance stage learn m (initialised to inherit_m0); the copy keeps every base row and the
+ *      var rows with m > 0 (all var rows when the stage did not run);
+ *   2. dynamics-aware shift (Sec. 3.3): n_shift iterations of the shift stage of dass_step (offsets
+ *      of the dynamic rows dyn_idx start at offsets_init), then the learned offsets are applied to the
+ *      dynamic rows;
+ *   3. error-guided densification (Sec. 3.4, Eq. 4, Alg. 1): error pass on the last shift render
+ *      (quantile), Eq. 4 selection (tau_pos, tau_err, at most k_max) and spawn (z);
+ *   4. densification stage (Sec. 3.4): if n_densify > 0 and var rows exist, n_densify iterations over
+ *      the var rows, then var rows of opacity <= prune_opacity are pruned.
+ * Every stage captures one iteration as a CUDA graph and replays it. G_{t-1} is read from the scene
+ * arrays and G_t written back into them (rows [0, *n)); base rows come first and keep their
+ * indices, so dyn_idx indexes base rows. */
+typedef struct dass_timestep_desc {
+    /* scene arrays: G_{t-1} on entry, G_t on return; room for n_max rows (>= *n + k_max) */
+    int64_t n_max;
+    int32_t sh_degree;
+    int32_t n_cams;
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logit;
+    float* sh;
+    uint8_t* is_var;                  /* [n_max] */
+    int64_t* n;                       /* HOST: rows of G_{t-1} on entry, of G_t on return */
+    const dass_camera* cams;          /* host [n_cams] */
+    float* targets;                   /* device images of timestep t, planar like the render */
+    const float* targets_host;        /* optional host images: copied into targets at the start */
+    int32_t t;                        /* timestep index */
+    int32_t erase_every;              /* 20 in the paper; 0 = never erase */
+    int64_t n_dyn;
+    const int32_t* dyn_idx;           /* [n_dyn] dynamic base rows */
+    const float* offsets_init;        /* [n_dyn][7] initial (dmu, sigma) */
+    float* offsets;                   /* [n_dyn][7] the learned offsets on return */
+    const float* z;                   /* [n_max][3] N(0,1) draws of the spawn, indexed by source row */
+    int32_t n_inherit, n_shift, n_densify, k_max;    /* s1, s2, s3 and the spawn limit */
+    int32_t tile, batch;
+    float lambda_dssim, lambda_inher, inherit_m0, quantile, tau_pos, tau_err, prune_opacity;
+    float lr_inherit, lr_mu, lr_sigma;
+    float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps;
+    int64_t pair_capacity;            /* pair buffer of every stage's render, < 2^31 */
+    void* workspace;                  /* >= dass_timestep_workspace() bytes */
+    size_t workspace_bytes;
+    /* optional HOST copies of G_t (rows [0, *n), capacity n_max) written before the call returns */
+    float* host_means;
+    float* host_log_scales;
+    float* host_quats;
+    float* host_opacity_logit;
+    float* host_sh;
+    uint8_t* host_is_var;
+} dass_timestep_desc;
+
+/* What one timestep did (host struct filled by dass_timestep). */
+typedef struct dass_timestep_stats {
+    int64_t n_in;                     /* rows of G_{t-1} */
+    int64_t n_var_in;                 /* its var rows */
+    int64_t n_inherited;              /* rows after the inheritance copy */
+    int64_t n_spawned;                /* rows added by the spawn */
+    int64_t n_var_trained;            /* var rows of the densification stage */
+    int64_t n_out;                    /* rows of G_t */
+    int64_t pairs_max;                /* largest pair count of any iteration (size pair_capacity from it) */
+    int32_t erased;                   /* 1 if this timestep erased every var row */
+    int32_t inherit_ran;              /* 1 if the inheritance stage ran */
+    double loss_inherit;              /* last iteration of each stage (0 if it did not run) */
+    double loss_shift;
+    double loss_densify;
+} dass_timestep_stats;
+
+int dass_timestep_workspace(const dass_timestep_desc* d, size_t* bytes);
+
+/* Runs the timestep on `stream` (not the legacy default stream). Host synchronisations: after the
+ * inheritance stage, the copy, the shift stage, the spawn and the densification stage (row counts
+ * and overflow flags are read back). The scene arrays and *n are written only at the end: on any
+ * error, including DASS_ERR_CAPACITY (a pair overflow in some stage; stats->pairs_max says how many
+ * pairs were needed), G_{t-1} is left as it was and the call can be repeated with a larger
+ * pair_capacity and workspace. DASS_ERR_INVALID_ARG if *n + k_max > n_max. */
+int dass_timestep(const dass_timestep_desc* d, dass_timestep_stats* stats /* host */, void* stream);
 
 #ifdef __cplusplus
 }

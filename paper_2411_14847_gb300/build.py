@@ -18,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdass.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "render.cu", "loss.cu", "stages.cu", "field.cu", "features.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "render.cu", "loss.cu", "stages.cu", "field.cu", "features.cu", "noalloc.cu",
+           "timestep.cu"]
 
 
 def nvcc() -> str:

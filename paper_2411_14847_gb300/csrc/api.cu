@@ -1,5 +1,5 @@
-// extern "C" entry points of libdass: argument checks, camera tables, dispatch to the kernel
-// launchers, and the per-stage driver dass_step (CUDA-graph replay of one iteration).
+// extern "C" entry points of libdass: argument checks, camera tables and dispatch to the kernel
+// launchers. The stage drivers and the whole-timestep driver are in timestep.cu.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,78 +10,9 @@
 #include <utility>
 
 #include "common.cuh"
+#include "launch.cuh"
 
 namespace dass {
-
-// launchers defined in the other translation units
-int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
-                      const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
-                      dass_splat* splats, cudaStream_t st);
-int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
-                             cudaStream_t st, long long n_max = 0);
-int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
-                          const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
-                          const dass_splat* splats, const dass_splat_grad* gsp, const int* rows, long long n_rows,
-                          unsigned flags, int accumulate, float* d_means, float* d_log_scales, float* d_quats,
-                          float* d_opacity_logit, float* d_sh, float* d_keep, cudaStream_t st);
-int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
-                         float* accum, int* count, cudaStream_t st);
-size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
-int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
-                    uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
-int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
-                      int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
-                      unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,
-                      long long rec_stride = 1);
-int render_prepare(int tile, int batch);
-int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
-                      int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
-                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
-size_t loss_workspace_bytes(const CamTable& ct);
-int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
-                double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr);
-int target_stats_launch(const float* target, const CamTable& ct, float* stats, cudaStream_t st);
-int shift_launch(long long n_dyn, const int* idx, const float* off, const float* means, const float* quats, float* om,
-                 float* oq, cudaStream_t st);
-int shift_bwd_launch(long long n_dyn, const int* idx, const float* off, const float* quats, const float* dm,
-                     const float* dq, float* doff, float* dqin, cudaStream_t st);
-int adam_launch(long long n_sel, int width, const int* rows, float* p, const float* g, float* m, float* v,
-                int* step_dev, const float* lr, float b1, float b2, float eps, int inc, cudaStream_t st);
-size_t inherit_workspace_bytes(long long n);
-int inherit_launch(long long n, int deg, const float* means, const float* ls, const float* quats, const float* logit,
-                   const float* sh, const uint8_t* is_var, const float* m, int erase, float* om, float* ols, float* oq,
-                   float* ologit, float* osh, uint8_t* ovar, int* remap, long long* n_out, void* ws, size_t ws_bytes,
-                   cudaStream_t st);
-int inherit_keep_launch(long long n, const uint8_t* is_var, const float* m, uint8_t* keep, cudaStream_t st);
-int render_features_launch(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct,
-                           const float* feats, int F, long long stride, float* out, cudaStream_t st);
-int object_ids_launch(const float* x, long long n, int F, const float* W, const float* b, int K, int* ids,
-                      cudaStream_t st);
-int dynamic_objects_launch(const int* ids, const uint8_t* dyn_area, long long n, int K, unsigned int min_pixels,
-                           uint8_t* obj_mask, unsigned int* hist, cudaStream_t st);
-int dynamic_gaussians_launch(const float* feats, long long n, int F, const float* W, const float* b, int K,
-                             const uint8_t* obj_mask, uint8_t* dyn_mask, cudaStream_t st);
-size_t mask_rows_workspace_bytes(long long n);
-int mask_rows_launch(const uint8_t* mask, long long n, int* rows, long long* count, void* ws, size_t ws_bytes,
-                     cudaStream_t st);
-int field_fwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, float* out,
-                     cudaStream_t st);
-int field_bwd_launch(const dass_field* f, long long n_rows, const int* rows, const float* means, const float* dof,
-                     float* dt, float* dw1, float* db1, float* dw2, float* db2, cudaStream_t st);
-int prune_logits_launch(long long n, const float* logit, float min_opacity, float* m, cudaStream_t st);
-int inherit_mask_grad_launch(long long n_rows, const int* rows, const float* m, const float* d_keep, float lambda,
-                             float* grad, double* loss, cudaStream_t st);
-size_t error_pass_workspace_bytes(const CamTable& ct);
-int error_pass_launch(const float* img, const float* tgt, const CamTable& ct, double quantile, long long n,
-                      const float* means, const uint8_t* is_var, float* error_map, float* gamma, uint8_t* s_err,
-                      void* ws, size_t ws_bytes, cudaStream_t st);
-size_t select_workspace_bytes(long long n);
-int select_launch(long long n, const float* accum, const int* count, const uint8_t* s_err, const uint8_t* is_var,
-                  float tau_pos, float tau_err, int k_max, int* selected, int* n_selected, void* ws, size_t ws_bytes,
-                  cudaStream_t st);
-int spawn_launch(long long n, int deg, float* means, float* ls, float* quats, float* logit, float* sh, uint8_t* is_var,
-                 const int* selected, const int* n_sel, int k_max, const float* z, long long* n_total,
-                 cudaStream_t st);
 
 static thread_local char g_err[512] = {0};
 static thread_local long long g_launches = 0;
@@ -293,7 +224,7 @@ DASS_API int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_o
                            workspace_bytes, as_stream(stream));
 }
 
-static bool batch_ok(int b) { return b == 64 || b == 128 || b == 256; }
+bool dass::batch_ok(int b) { return b == 64 || b == 128 || b == 256; }
 
 DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                              const dass_camera* cams, int n_cams, int tile, int batch, const float* bg, float* image,
@@ -597,192 +528,3 @@ DASS_API int dass_spawn(int64_t n, int sh_degree, float* means, float* log_scale
                         z, (long long*)n_total, as_stream(stream));
 }
 
-// ----------------------------------------------------------------- dass_step
-
-namespace {
-
-struct StepPlan {
-    CamTable all;
-    std::vector<CamTable> per;   // one-camera tables (plain mode)
-    size_t bin_ws = 0, loss_ws = 0;
-    size_t stats_bytes = 0;      // cached target statistics of the SSIM term (2 maps)
-    size_t total() const;
-};
-
-bool plan_step(const dass_step_desc* d, StepPlan& p, int mode) {
-    if (!make_cam_table(d->cams, d->n_cams, d->tile, d->n, &p.all)) return false;
-    long long n_rec = (long long)d->n_cams * d->n;
-    p.bin_ws = bin_sort_workspace_bytes(mode == DASS_STEP_PLAIN ? d->n : n_rec, d->pair_capacity);
-    p.loss_ws = loss_workspace_bytes(p.all);
-    p.stats_bytes = d->lambda_dssim > 0.f ? sizeof(float) * 6 * (size_t)p.all.pixels_total : 0;
-    if (mode == DASS_STEP_PLAIN) {
-        p.per.resize(d->n_cams);
-        for (int c = 0; c < d->n_cams; ++c)
-            if (!make_cam_table(d->cams + c, 1, d->tile, d->n, &p.per[c])) return false;
-    }
-    return true;
-}
-
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-size_t StepPlan::total() const { return align256(bin_ws) + align256(loss_ws) + align256(stats_bytes); }
-
-float* target_stats_ptr(const dass_step_desc* d, const StepPlan& p) {
-    if (!p.stats_bytes) return nullptr;
-    return reinterpret_cast<float*>(reinterpret_cast<char*>(d->workspace) + align256(p.bin_ws) + align256(p.loss_ws));
-}
-
-__global__ void or_flag_kernel(long long* counters) { counters[3] |= counters[1]; }
-
-int step_iteration(const dass_step_desc* d, const StepPlan& p, int mode, cudaStream_t st) {
-    char* ws = reinterpret_cast<char*>(d->workspace);
-    void* bin_ws = ws;
-    void* loss_ws = ws + align256(p.bin_ws);
-    const float* ystats = target_stats_ptr(d, p);     // (w * y, w * y^2) pairs per pixel-channel
-    const float3 bg = make_float3(0.f, 0.f, 0.f);
-    int rc = shift_launch(d->n_dyn, d->dyn_idx, d->offsets, d->means, d->quats, d->render_means, d->render_quats, st);
-    if (rc) return rc;
-    DASS_CHECK_CUDA(cudaMemsetAsync(d->loss, 0, sizeof(double), st));
-    const float inv_cams = 1.f / (float)d->n_cams;
-    if (mode == DASS_STEP_BATCHED) {
-        const CamTable& ct = p.all;
-        long long n_rec = (long long)d->n_cams * d->n;
-        rc = preprocess_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats, d->opacity_logit,
-                               d->sh, nullptr, ct, d->splats, st);
-        if (rc) return rc;
-        rc = bin_sort_launch(d->splats, n_rec, ct, d->pair_rec, d->pair_capacity, d->tile_ranges,
-                             (long long*)d->counters, bin_ws, p.bin_ws, st);
-        if (rc) return rc;
-        or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters); count_launch();
-        rc = render_fwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image, d->T_final,
-                               d->n_last, st);
-        if (rc) return rc;
-        rc = loss_launch(d->image, d->targets, ct, d->lambda_dssim, inv_cams, d->dL_dimage, d->loss, loss_ws,
-                         p.loss_ws, st, ystats);
-        if (rc) return rc;
-        DASS_CHECK_CUDA(cudaMemsetAsync(d->splat_grads, 0, sizeof(dass_splat_grad) * n_rec, st));
-        rc = render_bwd_launch(d->splats, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final, d->n_last,
-                               d->dL_dimage, d->dyn_mask, d->n, d->splat_grads, st);
-        if (rc) return rc;
-        rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
-                                   d->opacity_logit, d->sh, nullptr, ct, d->splats, d->splat_grads, d->dyn_idx,
-                                   d->n_dyn, DASS_GRAD_MEANS | DASS_GRAD_QUATS, 0, d->d_means_dyn, nullptr,
-                                   d->d_quats_dyn, nullptr, nullptr, nullptr, st);
-        if (rc) return rc;
-        if (d->stat_accum && d->stat_count) {
-            rc = densify_stats_launch(d->n, ct, d->splats, d->splat_grads, d->stat_accum, d->stat_count, st);
-            if (rc) return rc;
-        }
-    } else {
-        for (int c = 0; c < d->n_cams; ++c) {
-            const CamTable& ct = p.per[c];
-            const CamInfo& full = p.all.c[c];
-            dass_splat* sp = d->splats + (long long)c * d->n;
-            dass_splat_grad* gs = d->splat_grads + (long long)c * d->n;
-            long long pb = full.pix_base;
-            rc = preprocess_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
-                                   d->opacity_logit, d->sh, nullptr, ct, sp, st);
-            if (rc) return rc;
-            rc = bin_sort_launch(sp, d->n, ct, d->pair_rec, d->pair_capacity, d->tile_ranges, (long long*)d->counters,
-                                 bin_ws, p.bin_ws, st);
-            if (rc) return rc;
-            or_flag_kernel<<<1, 1, 0, st>>>((long long*)d->counters); count_launch();
-            rc = render_fwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->image + 3 * pb,
-                                   d->T_final + pb, d->n_last + pb, st);
-            if (rc) return rc;
-            rc = loss_launch(d->image + 3 * pb, d->targets + 3 * pb, ct, d->lambda_dssim, inv_cams,
-                             d->dL_dimage + 3 * pb, d->loss, loss_ws, p.loss_ws, st,
-                             ystats ? ystats + 2 * 3 * pb : nullptr);
-            if (rc) return rc;
-            DASS_CHECK_CUDA(cudaMemsetAsync(gs, 0, sizeof(dass_splat_grad) * d->n, st));
-            rc = render_bwd_launch(sp, d->pair_rec, d->tile_ranges, ct, d->batch, bg, d->T_final + pb, d->n_last + pb,
-                                   d->dL_dimage + 3 * pb, d->dyn_mask, d->n, gs, st);
-            if (rc) return rc;
-            rc = preprocess_bwd_launch(d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats,
-                                       d->opacity_logit, d->sh, nullptr, ct, sp, gs, d->dyn_idx, d->n_dyn,
-                                       DASS_GRAD_MEANS | DASS_GRAD_QUATS, c > 0, d->d_means_dyn, nullptr,
-                                       d->d_quats_dyn, nullptr, nullptr, nullptr, st);
-            if (rc) return rc;
-            if (d->stat_accum && d->stat_count) {
-                rc = densify_stats_launch(d->n, ct, sp, gs, d->stat_accum, d->stat_count, st);
-                if (rc) return rc;
-            }
-        }
-    }
-    rc = shift_bwd_launch(d->n_dyn, d->dyn_idx, d->offsets, d->quats, d->d_means_dyn, d->d_quats_dyn, d->offset_grad,
-                          nullptr, st);
-    if (rc) return rc;
-    float lr[7] = {d->lr_mu, d->lr_mu, d->lr_mu, d->lr_sigma, d->lr_sigma, d->lr_sigma, d->lr_sigma};
-    return adam_launch(d->n_dyn, 7, nullptr, d->offsets, d->offset_grad, d->adam_m, d->adam_v, d->adam_step, lr,
-                       d->beta1, d->beta2, d->eps, 1, st);
-}
-
-bool desc_ok(const dass_step_desc* d) {
-    if (!d || d->n < 0 || d->n_dyn < 0 || d->sh_degree < 0 || d->sh_degree > 3) return false;
-    if (d->n >= (1ll << 31) || (long long)d->n_cams * d->n >= (1ll << 32)) return false;
-    if (d->pair_capacity < 0 || d->pair_capacity >= (1ll << 31)) return false;
-    if (!batch_ok(d->batch)) return false;
-    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logit || !d->sh || !d->targets) return false;
-    if (d->n_dyn > 0 && (!d->dyn_idx || !d->offsets || !d->offset_grad || !d->adam_m || !d->adam_v)) return false;
-    if (!d->adam_step || !d->render_means || !d->render_quats || !d->splats || !d->splat_grads) return false;
-    if (!d->pair_rec || !d->tile_ranges || !d->counters || !d->image || !d->T_final || !d->n_last) return false;
-    if (!d->dL_dimage || !d->loss || !d->workspace) return false;
-    if (d->n_dyn > 0 && (!d->d_means_dyn || !d->d_quats_dyn)) return false;
-    return true;
-}
-
-}  // namespace
-
-DASS_API int dass_step_workspace(const dass_step_desc* d, size_t* bytes) {
-    if (!d || !bytes) return DASS_ERR_INVALID_ARG;
-    StepPlan p;
-    if (!plan_step(d, p, DASS_STEP_BATCHED)) return DASS_ERR_INVALID_ARG;
-    *bytes = p.total();
-    return DASS_OK;
-}
-
-DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* stream) {
-    if (!desc_ok(d) || n_iters < 0 || (mode != DASS_STEP_BATCHED && mode != DASS_STEP_PLAIN))
-        return DASS_ERR_INVALID_ARG;
-    StepPlan p;
-    if (!plan_step(d, p, mode)) return DASS_ERR_INVALID_ARG;
-    if (d->workspace_bytes < p.total()) return DASS_ERR_OOM;
-    cudaStream_t st = as_stream(stream);
-    DASS_CHECK_CUDA(cudaMemsetAsync(d->counters, 0, sizeof(int64_t) * 4, st));
-    if (n_iters == 0) return DASS_OK;
-    if (float* ys = target_stats_ptr(d, p))   // the targets are fixed for the whole call
-        if (int rc = target_stats_launch(d->targets, p.all, ys, st)) return rc;
-    if (mode == DASS_STEP_BATCHED) {
-        if (st == nullptr) return DASS_ERR_INVALID_ARG;   // the legacy stream cannot be captured
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        if (int rc = render_prepare(d->tile, d->batch)) return rc;   // attributes are not set under capture
-        DASS_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        long long l0 = launches_so_far();
-        int rc = step_iteration(d, p, mode, st);
-        long long per_iter = launches_so_far() - l0;
-        set_launches(l0 + per_iter * (long long)n_iters);   // every replay runs the captured kernels
-        cudaError_t ec = cudaStreamEndCapture(st, &graph);
-        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
-        if (ec != cudaSuccess) { set_last_error("cudaStreamEndCapture", ec); return DASS_ERR_CUDA; }
-        ec = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ec != cudaSuccess) { set_last_error("cudaGraphInstantiate", ec); return DASS_ERR_CUDA; }
-        for (int i = 0; i < n_iters; ++i) {
-            ec = cudaGraphLaunch(exec, st);
-            if (ec != cudaSuccess) { cudaGraphExecDestroy(exec); set_last_error("cudaGraphLaunch", ec); return DASS_ERR_CUDA; }
-        }
-        ec = cudaStreamSynchronize(st);
-        cudaGraphExecDestroy(exec);
-        if (ec != cudaSuccess) { set_last_error("cudaStreamSynchronize", ec); return DASS_ERR_CUDA; }
-    } else {
-        for (int i = 0; i < n_iters; ++i) {
-            int rc = step_iteration(d, p, mode, st);
-            if (rc) return rc;
-        }
-        DASS_CHECK_CUDA(cudaStreamSynchronize(st));
-    }
-    int64_t flags[4];
-    DASS_CHECK_CUDA(cudaMemcpy(flags, d->counters, sizeof(flags), cudaMemcpyDeviceToHost));
-    return flags[3] ? DASS_ERR_CAPACITY : DASS_OK;
-}

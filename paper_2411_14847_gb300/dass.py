@@ -65,6 +65,58 @@ class dass_step_desc(C.Structure):
     ]
 
 
+_V, _F, _I32, _I64 = C.c_void_p, C.c_float, C.c_int32, C.c_int64
+_RENDER_FIELDS = [("tile", _I32), ("batch", _I32), ("splats", _V), ("splat_grads", _V), ("pair_rec", _V),
+                  ("pair_capacity", _I64), ("tile_ranges", _V), ("counters", _V), ("image", _V), ("T_final", _V),
+                  ("n_last", _V), ("dL_dimage", _V), ("loss", _V), ("workspace", _V), ("workspace_bytes", C.c_size_t)]
+_SCENE_FIELDS = [("n", _I64), ("sh_degree", _I32), ("n_cams", _I32), ("means", _V), ("log_scales", _V),
+                 ("quats", _V), ("opacity_logit", _V), ("sh", _V)]
+
+
+class dass_inherit_step_desc(C.Structure):
+    _fields_ = _SCENE_FIELDS + [
+        ("is_var", _V), ("cams", _V), ("targets", _V), ("n_var", _I64), ("var_rows", _V), ("m", _V), ("keep", _V),
+        ("m_grad", _V), ("adam_m", _V), ("adam_v", _V), ("adam_step", _V), ("d_keep", _V),
+        ("lr", _F), ("beta1", _F), ("beta2", _F), ("eps", _F), ("lambda_dssim", _F), ("lambda_inher", _F),
+    ] + _RENDER_FIELDS
+
+
+class dass_densify_step_desc(C.Structure):
+    _fields_ = _SCENE_FIELDS + [
+        ("n_base", _I64), ("is_var", _V), ("cams", _V), ("targets", _V), ("grad", _V), ("adam_m", _V),
+        ("adam_v", _V), ("adam_step", _V),
+        ("lr_means", _F), ("lr_log_scales", _F), ("lr_quats", _F), ("lr_opacity", _F), ("lr_sh_dc", _F),
+        ("lr_sh_rest", _F), ("beta1", _F), ("beta2", _F), ("eps", _F), ("lambda_dssim", _F),
+    ] + _RENDER_FIELDS
+
+
+class dass_timestep_desc(C.Structure):
+    _fields_ = [
+        ("n_max", _I64), ("sh_degree", _I32), ("n_cams", _I32), ("means", _V), ("log_scales", _V), ("quats", _V),
+        ("opacity_logit", _V), ("sh", _V), ("is_var", _V), ("n", _V), ("cams", _V), ("targets", _V),
+        ("targets_host", _V), ("t", _I32), ("erase_every", _I32), ("n_dyn", _I64), ("dyn_idx", _V),
+        ("offsets_init", _V), ("offsets", _V), ("z", _V),
+        ("n_inherit", _I32), ("n_shift", _I32), ("n_densify", _I32), ("k_max", _I32), ("tile", _I32), ("batch", _I32),
+        ("lambda_dssim", _F), ("lambda_inher", _F), ("inherit_m0", _F), ("quantile", _F), ("tau_pos", _F),
+        ("tau_err", _F), ("prune_opacity", _F), ("lr_inherit", _F), ("lr_mu", _F), ("lr_sigma", _F),
+        ("lr_means", _F), ("lr_log_scales", _F), ("lr_quats", _F), ("lr_opacity", _F), ("lr_sh_dc", _F),
+        ("lr_sh_rest", _F), ("beta1", _F), ("beta2", _F), ("eps", _F),
+        ("pair_capacity", _I64), ("workspace", _V), ("workspace_bytes", C.c_size_t),
+        ("host_means", _V), ("host_log_scales", _V), ("host_quats", _V), ("host_opacity_logit", _V),
+        ("host_sh", _V), ("host_is_var", _V),
+    ]
+
+
+class dass_timestep_stats(C.Structure):
+    _fields_ = [("n_in", _I64), ("n_var_in", _I64), ("n_inherited", _I64), ("n_spawned", _I64),
+                ("n_var_trained", _I64), ("n_out", _I64), ("pairs_max", _I64), ("erased", _I32),
+                ("inherit_ran", _I32), ("loss_inherit", C.c_double), ("loss_shift", C.c_double),
+                ("loss_densify", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class dass_scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad", C.c_int32), ("means", C.c_void_p),
                 ("log_scales", C.c_void_p), ("quats", C.c_void_p), ("opacity_logit", C.c_void_p),
@@ -125,6 +177,12 @@ _SIGS = {
     "dass_spawn": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
     "dass_step_workspace": (C.c_int, [_P, _P]),
     "dass_step": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "dass_inherit_step_workspace": (C.c_int, [_P, _P]),
+    "dass_inherit_step": (C.c_int, [_P, C.c_int, _P]),
+    "dass_densify_step_workspace": (C.c_int, [_P, _P]),
+    "dass_densify_step": (C.c_int, [_P, C.c_int, _P]),
+    "dass_timestep_workspace": (C.c_int, [_P, _P]),
+    "dass_timestep": (C.c_int, [_P, _P, _P]),
 }
 
 
@@ -526,3 +584,47 @@ def dass_step(desc, n_iters, mode=STEP_BATCHED, stream=None):
     if st not in (OK, ERR_CAPACITY):
         raise DassError("dass_step", st)
     return st
+
+
+def dass_inherit_step_workspace(desc):
+    b = C.c_size_t()
+    _call("dass_inherit_step_workspace", C.byref(desc), C.byref(b))
+    return b.value
+
+
+def dass_inherit_step(desc, n_iters, stream=None):
+    """Returns OK or ERR_CAPACITY (pair overflow in some iteration); raises on other errors."""
+    st = load().dass_inherit_step(C.byref(desc), n_iters, _stream(stream))
+    if st not in (OK, ERR_CAPACITY):
+        raise DassError("dass_inherit_step", st)
+    return st
+
+
+def dass_densify_step_workspace(desc):
+    b = C.c_size_t()
+    _call("dass_densify_step_workspace", C.byref(desc), C.byref(b))
+    return b.value
+
+
+def dass_densify_step(desc, n_iters, stream=None):
+    """Returns OK or ERR_CAPACITY (pair overflow in some iteration); raises on other errors."""
+    st = load().dass_densify_step(C.byref(desc), n_iters, _stream(stream))
+    if st not in (OK, ERR_CAPACITY):
+        raise DassError("dass_densify_step", st)
+    return st
+
+
+def dass_timestep_workspace(desc):
+    b = C.c_size_t()
+    _call("dass_timestep_workspace", C.byref(desc), C.byref(b))
+    return b.value
+
+
+def dass_timestep(desc, stream=None):
+    """Returns (status, stats): status OK or ERR_CAPACITY (G_{t-1} left unchanged); raises on other
+    errors."""
+    stats = dass_timestep_stats()
+    st = load().dass_timestep(C.byref(desc), C.byref(stats), _stream(stream))
+    if st not in (OK, ERR_CAPACITY):
+        raise DassError("dass_timestep", st)
+    return st, stats

@@ -1,15 +1,16 @@
 """Per-timestep driver of the streaming reconstruction on top of libdass.
 
-A timestep (Sec. 3.1) turns G_{t-1} into G_t with the multi-view images of timestep t:
-  1. selective inheritance (Sec. 3.2): s1 iterations learning the var-row mask (InheritStage:
-     dass_inherit_keep, dass_keep_grad, dass_inherit_mask_grad, dass_adam), then the copy
-                                                           -> dass_inherit
-  2. dynamics-aware shift stage, n_shift iterations (Sec. 3.3) -> dass_step (graph replay)
-  3. error pass on the last shift render, Eq. 4 selection and spawn (Sec. 3.4)
-                                                           -> dass_error_pass, dass_densify_select, dass_spawn
-  4. densification-stage training of the var rows, s3 iterations (DensifyStage: dass_preprocess_bwd
-     over the var tail, dass_adam), then low-opacity pruning -> dass_prune_logits, dass_inherit
-This module only allocates buffers (PyTorch) and sequences the calls.
+A timestep (Sec. 3.1) turns G_{t-1} into G_t with the multi-view images of timestep t; the whole
+sequence runs inside one C call, dass_timestep (Timestep below):
+  1. selective inheritance (Sec. 3.2): s1 iterations learning the var-row mask, then the copy;
+  2. dynamics-aware shift stage, s2 iterations (Sec. 3.3);
+  3. error pass on the last shift render, Eq. 4 selection and spawn (Sec. 3.4);
+  4. densification-stage training of the var rows, s3 iterations, then low-opacity pruning.
+The stage classes run one stage through its C stage driver (ShiftStage -> dass_step, InheritStage
+-> dass_inherit_step, DensifyStage -> dass_densify_step) over buffers allocated here, so each stage
+can be run, timed and checked against the oracle on its own; FieldShiftStage composes the shift
+stage with the hash-encoding deformation fields from individual entry points. This module only
+allocates buffers (PyTorch) and marshals descriptors.
 """
 from __future__ import annotations
 
@@ -152,24 +153,40 @@ class ShiftStage:
         raise D.DassError("dass_step", D.ERR_CAPACITY)
 
 
-class InheritStage:
-    """Selective-inheritance stage (Sec. 3.2, App. B.2): learns one logit m per var Gaussian of
-    G_{t-1} against the images of timestep t, every other parameter fixed.
+def _render_fields(d, fr, dL_dimage, loss_buf):
+    d.tile, d.batch = fr.tile, fr.batch
+    d.splats, d.splat_grads = _vp(fr.splats), _vp(fr.splat_grads)
+    d.pair_rec, d.pair_capacity = _vp(fr.pair_rec), fr.pair_capacity
+    d.tile_ranges, d.counters = _vp(fr.tile_ranges), _vp(fr.counters)
+    d.image, d.T_final, d.n_last = _vp(fr.image), _vp(fr.T_final), _vp(fr.n_last)
+    d.dL_dimage, d.loss = _vp(dL_dimage), _vp(loss_buf)
 
-    One iteration: keep = Quant(sigmoid(m)) on var rows (dass_inherit_keep) -> projection with
-    opacity and scale multiplied by keep (Eq. 1) -> bin/sort -> forward -> loss of Eq. 3 ->
-    backward (full splat gradients for var rows only) -> dL/dkeep (dass_keep_grad) -> the
-    straight-through gradient with the mask loss of Eq. 2 (dass_inherit_mask_grad) -> Adam on m.
-    The first iteration runs eagerly (it sizes the pair buffer with every var row rendered, the
-    most the stage can render since a masked row only receives the mask loss); the others replay
-    it as one captured CUDA graph.
+
+def _scene_fields(d, g, n, cams_arr, n_cams):
+    d.n, d.n_cams = n, n_cams
+    d.sh_degree = int(round(math.sqrt(g["sh"].shape[1]))) - 1
+    d.means, d.log_scales, d.quats = _vp(g["means"]), _vp(g["log_scales"]), _vp(g["quats"])
+    d.opacity_logit, d.sh = _vp(g["opacity_logit"]), _vp(g["sh"])
+    d.cams = C.cast(cams_arr, C.c_void_p)
+
+
+class InheritStage:
+    """Selective-inheritance stage (Sec. 3.2, App. B.2) through dass_inherit_step: learns one logit m
+    per var Gaussian of G_{t-1} against the images of timestep t, every other parameter fixed.
+
+    One iteration (captured once as a CUDA graph and replayed): keep = Quant(sigmoid(m)) on var rows ->
+    projection with opacity and scale multiplied by keep (Eq. 1) -> bin/sort -> forward -> loss of
+    Eq. 3 -> backward (full splat gradients for var rows only) -> dL/dkeep -> the straight-through
+    gradient with the mask loss of Eq. 2 -> Adam on m. The pair buffer is sized by one binning with
+    every var row rendered (the most the stage can render, since a masked row only receives the mask
+    loss); an overflow restores m and its Adam state and reruns with a larger buffer.
 
     The paper fixes neither lambda_inher, the initial logit nor the optimiser of m: m starts at
     m0 > 0 (every var row inherited unless the stage learns otherwise) and takes Adam steps.
     """
 
     def __init__(self, g, is_var, cams, targets, tile=16, batch=128, lambda_dssim=0.2, lambda_inher=1e-6, m0=0.5,
-                 lr=0.05, beta1=0.9, beta2=0.999, eps=1e-15):
+                 lr=0.05, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
         self.g = {k: g[k].contiguous() for k in PARAM_NAMES}
         self.cams = list(cams)
         self.n = int(self.g["means"].shape[0])
@@ -178,8 +195,6 @@ class InheritStage:
         self.var_rows = torch.nonzero(self.is_var).flatten().to(torch.int32).contiguous()
         self.n_var = int(self.var_rows.numel())
         self.targets = targets.contiguous()
-        self.lam, self.lam_inher = float(lambda_dssim), float(lambda_inher)
-        self.lr, self.betas, self.eps = float(lr), (float(beta1), float(beta2)), float(eps)
         self.m = torch.full((max(1, self.n),), float(m0), device=dev)
         self.keep = torch.ones(max(1, self.n), dtype=torch.uint8, device=dev)
         self.grad = torch.zeros(max(1, self.n), device=dev)
@@ -187,78 +202,72 @@ class InheritStage:
         self.adam_v = torch.zeros(max(1, self.n), device=dev)
         self.step = torch.zeros(1, dtype=torch.int32, device=dev)
         self.d_keep = torch.zeros(max(1, self.n_var), device=dev)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.fidelity = _FidelityLoss(self.targets, self.cams, self.lam)
-        self.graph = None
+        self.hp = dict(lr=float(lr), beta1=float(beta1), beta2=float(beta2), eps=float(eps),
+                       lambda_dssim=float(lambda_dssim), lambda_inher=float(lambda_inher))
+        self._cams_arr = D.cameras(self.cams)
+        if self.n:
+            self.frame.project(self.g)             # every var row rendered: the stage's largest pair count
+            m_pairs = self.frame.bin_sort()
+            self.frame._alloc_pairs(int(m_pairs * 1.1) + 4096)
+        self._build_desc()
 
-    def _iteration(self, eager=False):
-        fr = self.frame
-        D.dass_inherit_keep(self.is_var, self.m, self.keep)
-        fr.project(self.g, keep=self.keep)
-        if eager:
-            fr.bin_sort()
-        else:
-            fr.bin_sort(grow=False)
-            torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
-        fr.render_fwd()
-        self.loss_buf.zero_()
-        self.fidelity(fr.image, self.dL_dimage, self.loss_buf)
-        D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
-                          fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.is_var, rec_stride=self.n)
-        if self.n_var:
-            D.dass_keep_grad(self.g, self.cams, fr.splats, fr.splat_grads, self.d_keep, keep=self.keep,
-                             rows=self.var_rows)
-            D.dass_inherit_mask_grad(self.var_rows, self.m, self.d_keep, self.lam_inher, self.grad, self.loss_buf)
-            D.dass_adam(self.m.view(-1, 1), self.grad.view(-1, 1), self.adam_m.view(-1, 1), self.adam_v.view(-1, 1),
-                        self.step, [self.lr], self.betas[0], self.betas[1], self.eps, rows=self.var_rows)
+    def _build_desc(self):
+        d = D.dass_inherit_step_desc()
+        _scene_fields(d, self.g, self.n, self._cams_arr, len(self.cams))
+        d.is_var, d.targets = _vp(self.is_var), _vp(self.targets)
+        d.n_var, d.var_rows = self.n_var, _vp(self.var_rows)
+        d.m, d.keep, d.m_grad = _vp(self.m), _vp(self.keep), _vp(self.grad)
+        d.adam_m, d.adam_v, d.adam_step, d.d_keep = _vp(self.adam_m), _vp(self.adam_v), _vp(self.step), _vp(self.d_keep)
+        for k, v in self.hp.items():
+            setattr(d, k, v)
+        _render_fields(d, self.frame, self.dL_dimage, self.loss_buf)
+        d.workspace, d.workspace_bytes = None, 0
+        ws = D.dass_inherit_step_workspace(d)
+        self.workspace = torch.empty(max(1, ws), dtype=torch.uint8, device=self.g["means"].device)
+        d.workspace, d.workspace_bytes = _vp(self.workspace), ws
+        self.desc = d
 
     @property
     def loss(self):
         return float(self.loss_buf.item())
 
-    def run(self, n_iters):
+    def run(self, n_iters, max_regrow=3):
         """n_iters iterations; returns the learned logits m (var rows meaningful)."""
         if n_iters <= 0 or self.n == 0:
             return self.m
-        replays = n_iters
-        if self.graph is None:
-            self._iteration(eager=True)
-            replays -= 1
-            if replays > 0:
-                # the pair buffer now holds the exact count with every var row rendered (+ margin)
-                m_pairs = int(self.frame.counters[0].item())
-                if self.frame.pair_capacity < m_pairs * 1.05 + 1024:
-                    self.frame._alloc_pairs(int(m_pairs * 1.1) + 1024)
-                torch.cuda.synchronize()
-                self.graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(self.graph):
-                    self._iteration()
-        for _ in range(replays):
-            self.graph.replay()
-        if replays > 0 and int(self.overflow.item()):
-            raise D.DassError("inherit stage bin_sort", D.ERR_CAPACITY)
-        return self.m
+        torch.cuda.current_stream().synchronize()
+        for _ in range(max_regrow + 1):
+            snap = [t.clone() for t in (self.m, self.adam_m, self.adam_v, self.step)]
+            torch.cuda.synchronize()
+            if D.dass_inherit_step(self.desc, n_iters, stream=self.stream) == D.OK:
+                return self.m
+            for dst, src in zip((self.m, self.adam_m, self.adam_v, self.step), snap):
+                dst.copy_(src)
+            self.frame._alloc_pairs(int(self.frame.pair_capacity * 1.5) + 4096)
+            self._build_desc()
+        raise D.DassError("dass_inherit_step", D.ERR_CAPACITY)
 
 
 class DensifyStage:
-    """Densification-stage training (Sec. 3.4): s3 iterations of the fidelity loss (Eq. 3) over every
-    parameter of the var Gaussians (the new spawns and the inherited var rows), base rows fixed.
+    """Densification-stage training (Sec. 3.4) through dass_densify_step: s3 iterations of the fidelity
+    loss (Eq. 3) over every parameter of the var Gaussians (the new spawns and the inherited var
+    rows), base rows fixed.
 
     The var rows must be the contiguous tail [n_base, n) of the arrays (the layout dass_inherit and
-    dass_spawn produce), so each parameter's var part is a slice: the backward runs full splat
-    gradients for var rows only (dass_render_bwd full_grad), dass_preprocess_bwd with rows = the
-    tail gives compact gradients of exactly those slices, and dass_adam updates the slices. One
-    iteration runs eagerly, the rest replay it as a captured CUDA graph.
+    dass_spawn produce): the backward runs full splat gradients for var rows only, the parameter
+    gradients of the tail land in one buffer (per parameter: `grads[name]` views it) and Adam updates
+    each parameter slice of the tail. One iteration is captured as a CUDA graph and replayed.
 
     The paper trains these Gaussians as vanilla 3DGS does and states no learning rates; the 3DGS
     ones are used (positions 1.6e-4 per unit of scene extent, log-scales 5e-3, rotations 1e-3,
     opacity logits 5e-2, SH DC 2.5e-3 and higher bands 2.5e-3 / 20)."""
 
     def __init__(self, g, n_base, cams, targets, tile=16, batch=128, lambda_dssim=0.2, extent=3.0, lr=None,
-                 beta1=0.9, beta2=0.999, eps=1e-15):
+                 beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
         self.g = {k: g[k] for k in PARAM_NAMES}
         for k in PARAM_NAMES:
             assert self.g[k].is_contiguous()
@@ -269,65 +278,53 @@ class DensifyStage:
         dev = self.g["means"].device
         self.K = int(self.g["sh"].shape[1])
         self.targets = targets.contiguous()
-        self.lam = float(lambda_dssim)
         lr = dict(lr or {})
         self.lr = dict(means=lr.get("means", 1.6e-4 * extent), log_scales=lr.get("log_scales", 5e-3),
                        quats=lr.get("quats", 1e-3), opacity_logit=lr.get("opacity_logit", 5e-2),
                        sh_dc=lr.get("sh_dc", 2.5e-3), sh_rest=lr.get("sh_rest", 2.5e-3 / 20))
-        self.betas, self.eps = (float(beta1), float(beta2)), float(eps)
-        self.rows = torch.arange(self.n_base, self.n, dtype=torch.int32, device=dev)
+        self.betas, self.eps, self.lam = (float(beta1), float(beta2)), float(eps), float(lambda_dssim)
         self.full = torch.zeros(max(1, self.n), dtype=torch.uint8, device=dev)
         self.full[self.n_base:self.n] = 1
         nv = max(1, self.n_var)
         widths = dict(means=3, log_scales=3, quats=4, opacity_logit=1, sh=3 * self.K)
-        self.grads = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
-        self.adam_m = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
-        self.adam_v = {k: torch.zeros((nv, w), device=dev) for k, w in widths.items()}
+        total = sum(widths.values()) * nv
+        self.grad_buf = torch.zeros(total, device=dev)
+        self.m_buf = torch.zeros(total, device=dev)
+        self.v_buf = torch.zeros(total, device=dev)
+        self.grads, off = {}, 0
+        for k, w in widths.items():          # parameter-major views of the packed gradient buffer
+            self.grads[k] = self.grad_buf[off:off + w * nv].view(nv, w)
+            off += w * nv
         self.step = torch.zeros(1, dtype=torch.int32, device=dev)
-        band = torch.arange(max(1, self.n_var) * self.K, device=dev) % self.K
-        self.sh_dc_rows = torch.nonzero(band == 0).flatten().to(torch.int32).contiguous()
-        self.sh_rest_rows = torch.nonzero(band > 0).flatten().to(torch.int32).contiguous()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         self.frame = Frame(self.cams, self.n, tile=tile, batch=batch)
         self.dL_dimage = torch.zeros_like(self.frame.image)
         self.loss_buf = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.overflow = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.fidelity = _FidelityLoss(self.targets, self.cams, self.lam)
-        self.graph = None
+        self._cams_arr = D.cameras(self.cams)
+        if self.n:
+            self.frame.project(self.g)
+            m_pairs = self.frame.bin_sort()
+            # the var rows move and change size: 50% headroom over the pairs of the starting scene
+            self.frame._alloc_pairs(int(m_pairs * 1.5) + 4096)
+        self._build_desc()
+
+    def _build_desc(self):
+        d = D.dass_densify_step_desc()
+        _scene_fields(d, self.g, self.n, self._cams_arr, len(self.cams))
+        d.n_base, d.is_var, d.targets = self.n_base, _vp(self.full), _vp(self.targets)
+        d.grad, d.adam_m, d.adam_v, d.adam_step = _vp(self.grad_buf), _vp(self.m_buf), _vp(self.v_buf), _vp(self.step)
+        d.lr_means, d.lr_log_scales, d.lr_quats = self.lr["means"], self.lr["log_scales"], self.lr["quats"]
+        d.lr_opacity, d.lr_sh_dc, d.lr_sh_rest = self.lr["opacity_logit"], self.lr["sh_dc"], self.lr["sh_rest"]
+        d.beta1, d.beta2, d.eps, d.lambda_dssim = self.betas[0], self.betas[1], self.eps, self.lam
+        _render_fields(d, self.frame, self.dL_dimage, self.loss_buf)
+        d.workspace, d.workspace_bytes = None, 0
+        ws = D.dass_densify_step_workspace(d)
+        self.workspace = torch.empty(max(1, ws), dtype=torch.uint8, device=self.g["means"].device)
+        d.workspace, d.workspace_bytes = _vp(self.workspace), ws
+        self.desc = d
 
     def _slice(self, k):
         return self.g[k][self.n_base:self.n].reshape(self.n_var, -1)
-
-    def _iteration(self, eager=False):
-        fr = self.frame
-        fr.project(self.g)
-        if eager:
-            fr.bin_sort()
-        else:
-            fr.bin_sort(grow=False)
-            torch.maximum(self.overflow, fr.counters[1:2], out=self.overflow)
-        fr.render_fwd()
-        self.loss_buf.zero_()
-        self.fidelity(fr.image, self.dL_dimage, self.loss_buf)
-        D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, self.cams, fr.tile, fr.batch, fr.T_final,
-                          fr.n_last, self.dL_dimage, fr.splat_grads, full_grad=self.full, rec_stride=self.n)
-        if self.n_var == 0:
-            return
-        out = {"d_means": self.grads["means"], "d_log_scales": self.grads["log_scales"],
-               "d_quats": self.grads["quats"], "d_opacity_logit": self.grads["opacity_logit"],
-               "d_sh": self.grads["sh"]}
-        D.dass_preprocess_bwd(self.g, self.cams, fr.splats, fr.splat_grads, out, D.GRAD_ALL, rows=self.rows)
-        b1, b2 = self.betas
-        for k in ("means", "log_scales", "quats", "opacity_logit"):
-            D.dass_adam(self._slice(k), self.grads[k], self.adam_m[k], self.adam_v[k], self.step,
-                        [self.lr[k]] * self.grads[k].shape[1], b1, b2, self.eps, increment_step=False)
-        # SH as [rows * K, 3]: the DC band and the higher bands take their own learning rates
-        sh = self.g["sh"][self.n_base:self.n].reshape(-1, 3)
-        gs, ms, vs = (t.view(-1, 3) for t in (self.grads["sh"], self.adam_m["sh"], self.adam_v["sh"]))
-        D.dass_adam(sh, gs, ms, vs, self.step, [self.lr["sh_dc"]] * 3, b1, b2, self.eps, rows=self.sh_dc_rows,
-                    increment_step=self.K == 1)
-        if self.K > 1:
-            D.dass_adam(sh, gs, ms, vs, self.step, [self.lr["sh_rest"]] * 3, b1, b2, self.eps,
-                        rows=self.sh_rest_rows, increment_step=True)
 
     @property
     def loss(self):
@@ -335,46 +332,23 @@ class DensifyStage:
 
     def run(self, n_iters, max_regrow=2):
         """n_iters iterations; on pair-buffer overflow the var rows and optimiser state are restored
-        and the stage reruns with twice the pair capacity."""
-        snap = [self._slice(k).clone() for k in PARAM_NAMES]
-        for _ in range(max_regrow + 1):
-            try:
-                self._run(n_iters)
-                return
-            except D.DassError as e:
-                if e.status != D.ERR_CAPACITY:
-                    raise
-                for k, v in zip(PARAM_NAMES, snap):
-                    self._slice(k).copy_(v)
-                for d in (self.adam_m, self.adam_v):
-                    for t in d.values():
-                        t.zero_()
-                self.step.zero_()
-                self.overflow.zero_()
-                self.frame._alloc_pairs(2 * self.frame.pair_capacity)
-                self.graph = None
-        raise D.DassError("densify stage bin_sort", D.ERR_CAPACITY)
-
-    def _run(self, n_iters):
+        and the stage reruns with a larger pair buffer."""
         if n_iters <= 0 or self.n == 0:
             return
-        replays = n_iters
-        if self.graph is None:
-            self._iteration(eager=True)
-            replays -= 1
-            if replays > 0:
-                m_pairs = int(self.frame.counters[0].item())
-                # the var rows move and change size: keep 50% headroom over the pairs of the first render
-                if self.frame.pair_capacity < int(m_pairs * 1.5) + 4096:
-                    self.frame._alloc_pairs(int(m_pairs * 1.5) + 4096)
-                torch.cuda.synchronize()
-                self.graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(self.graph):
-                    self._iteration()
-        for _ in range(replays):
-            self.graph.replay()
-        if replays > 0 and int(self.overflow.item()):
-            raise D.DassError("densify stage bin_sort", D.ERR_CAPACITY)
+        torch.cuda.current_stream().synchronize()
+        for _ in range(max_regrow + 1):
+            snap = [self._slice(k).clone() for k in PARAM_NAMES] + [t.clone() for t in (self.m_buf, self.v_buf,
+                                                                                         self.step)]
+            torch.cuda.synchronize()
+            if D.dass_densify_step(self.desc, n_iters, stream=self.stream) == D.OK:
+                return
+            for k, v in zip(PARAM_NAMES, snap):
+                self._slice(k).copy_(v)
+            for dst, src in zip((self.m_buf, self.v_buf, self.step), snap[len(PARAM_NAMES):]):
+                dst.copy_(src)
+            self.frame._alloc_pairs(2 * self.frame.pair_capacity)
+            self._build_desc()
+        raise D.DassError("dass_densify_step", D.ERR_CAPACITY)
 
 
 def level_resolutions(levels, n_min=16, n_max=2048):
@@ -522,120 +496,123 @@ class FieldShiftStage:
 
 
 class Timestep:
-    """One full timestep t of the streaming pipeline over resident device buffers.
+    """One full timestep t of the streaming pipeline (dass_timestep) over resident device buffers.
 
-    Scene arrays are allocated with room for `n_max` rows; `n` tracks the live count."""
+    The scene arrays have room for `n_max` rows; `n` tracks the live count. Hyper-parameters (paper
+    readings where the paper states none): lambda = 0.2, inheritance logits start at 0.5 with Adam
+    lr 0.05 and lambda_inher = 1e-6, offsets Adam lr 1e-3, error quantile 0.95, tau_pos = 2e-4,
+    tau_err = 1e-4, at most 5000 spawns, erase every 20 timesteps, prune below opacity 0.005, and the
+    3DGS learning rates in the densification stage. A pair overflow in any stage leaves G_{t-1}
+    untouched; the pair buffer is then regrown from the reported count and the timestep rerun."""
 
     def __init__(self, cams, n_max, sh_degree, tile=16, batch=128, lambda_dssim=0.2, n_shift=100,
                  quantile=0.95, tau_pos=2e-4, tau_err=1e-4, k_max=5000, erase_every=20, n_inherit=0,
-                 lambda_inher=1e-6, n_densify=0, prune_opacity=0.005, device="cuda"):
+                 lambda_inher=1e-6, n_densify=0, prune_opacity=0.005, extent=3.0, device="cuda", stream=None):
         self.cams = list(cams)
         self.n_max = int(n_max)
         self.deg = sh_degree
+        self.K = (sh_degree + 1) ** 2
         self.tile, self.batch = tile, batch
-        self.lambda_dssim = lambda_dssim
-        self.n_shift = n_shift
-        self.quantile, self.tau_pos, self.tau_err, self.k_max = quantile, tau_pos, tau_err, k_max
-        self.erase_every = erase_every
-        self.n_inherit, self.lambda_inher = int(n_inherit), float(lambda_inher)   # s1 of the inheritance stage
-        self.n_densify, self.prune_opacity = int(n_densify), float(prune_opacity)  # s3 of the densification stage
         self.device = device
-        K = (sh_degree + 1) ** 2
-        shapes = dict(means=(3,), log_scales=(3,), quats=(4,), opacity_logit=(), sh=(K, 3))
-        self.bufs = [{k: torch.zeros((self.n_max,) + s, device=device) for k, s in shapes.items()} for _ in range(2)]
-        self.is_var = [torch.zeros(self.n_max, dtype=torch.uint8, device=device) for _ in range(2)]
-        self.cur = 0
+        self.hp = dict(lambda_dssim=float(lambda_dssim), lambda_inher=float(lambda_inher), inherit_m0=0.5,
+                       quantile=float(quantile), tau_pos=float(tau_pos), tau_err=float(tau_err),
+                       prune_opacity=float(prune_opacity), lr_inherit=0.05, lr_mu=1e-3, lr_sigma=1e-3,
+                       lr_means=1.6e-4 * extent, lr_log_scales=5e-3, lr_quats=1e-3, lr_opacity=5e-2,
+                       lr_sh_dc=2.5e-3, lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15)
+        self.sched = dict(n_inherit=int(n_inherit), n_shift=int(n_shift), n_densify=int(n_densify),
+                          k_max=int(k_max), erase_every=int(erase_every))
+        self.k_max = int(k_max)
+        shapes = dict(means=(3,), log_scales=(3,), quats=(4,), opacity_logit=(), sh=(self.K, 3))
+        self.bufs = {k: torch.zeros((self.n_max,) + s, device=device) for k, s in shapes.items()}
+        self.is_var = torch.zeros(self.n_max, dtype=torch.uint8, device=device)
         self.n = 0
+        self._n_host = C.c_int64(0)
+        self._cams_arr = D.cameras(self.cams)
+        self.tiles_total, self.pixels = D.tile_layout(self.cams, tile)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.pair_capacity = None
+        self.workspace = None
+        self.last_stats = None
 
     def load(self, arrays: dict, is_var=None):
         n = int(arrays["means"].shape[0])
         assert n + self.k_max <= self.n_max
         for k in PARAM_NAMES:
-            self.bufs[self.cur][k][:n].copy_(torch.as_tensor(arrays[k], dtype=torch.float32))
-        self.is_var[self.cur].zero_()
+            self.bufs[k][:n].copy_(torch.as_tensor(arrays[k], dtype=torch.float32))
+        self.is_var.zero_()
         if is_var is not None:
-            self.is_var[self.cur][:n].copy_(torch.as_tensor(is_var, dtype=torch.uint8))
+            self.is_var[:n].copy_(torch.as_tensor(is_var, dtype=torch.uint8))
         self.n = n
 
-    def view(self, which=None):
-        b = self.bufs[self.cur if which is None else which]
-        return {k: v[:self.n] for k, v in b.items()}
+    def view(self):
+        return {k: v[:self.n] for k, v in self.bufs.items()}
 
-    def run(self, t, targets, dyn_idx, offsets, inherit_logits=None, z=None, mode=D.STEP_BATCHED):
-        """Reconstruct timestep t. Returns dict of per-stage results (loss, #Gaussians, #spawned)."""
-        dev = self.device
-        src, dst = self.cur, 1 - self.cur
-        n = self.n
-        # 1) selective inheritance (Sec. 3.2): learn the mask over the var rows (s1 iterations),
-        #    unless the logits are given or this timestep erases every var row (App. B.2)
-        erase = t % self.erase_every == 0
-        if inherit_logits is None and self.n_inherit > 0 and not erase and n > 0 and bool(self.is_var[src][:n].any()):
-            stage1 = InheritStage(self.view(src), self.is_var[src][:n], self.cams, targets, tile=self.tile,
-                                  batch=self.batch, lambda_dssim=self.lambda_dssim, lambda_inher=self.lambda_inher)
-            inherit_logits = stage1.run(self.n_inherit)[:n]
-        m = inherit_logits if inherit_logits is not None else torch.ones(n, device=dev)
-        ws = torch.empty(max(1, D.dass_inherit_workspace(n)), dtype=torch.uint8, device=dev)
-        remap = torch.empty(max(1, n), dtype=torch.int32, device=dev)
-        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
-        out = {k: v for k, v in self.bufs[dst].items()}
-        D.dass_inherit(self.view(src), self.is_var[src][:n], m[:n].contiguous(), erase, out,
-                       self.is_var[dst], remap, n_out, ws)
-        self.cur = dst
-        self.n = int(n_out.item())
-        g = self.view()
-        # dynamic rows follow the inherited layout (base rows keep their indices)
-        dyn = dyn_idx
-        # 2) shift stage
-        stage = ShiftStage(g, self.cams, targets, dyn, offsets, tile=self.tile, batch=self.batch,
-                           lambda_dssim=self.lambda_dssim)
-        stage.run(self.n_shift, mode)
-        # commit the shift into the scene (the learned offsets move the dynamic rows)
-        D.dass_shift(dyn, stage.offsets, g["means"].clone(), g["quats"].clone(), g["means"], g["quats"])
-        # 3) error-guided densification statistics, selection and spawn (Sec. 3.4)
-        n = self.n
-        s_err = torch.zeros(n, dtype=torch.uint8, device=dev)
-        ews = torch.empty(D.dass_error_pass_workspace(self.cams), dtype=torch.uint8, device=dev)
-        D.dass_error_pass(stage.frame.image, targets, self.cams, self.quantile, g["means"], self.is_var[self.cur][:n],
-                          s_err, ews)
-        sel = torch.empty(max(1, self.k_max), dtype=torch.int32, device=dev)
-        nsel = torch.zeros(1, dtype=torch.int32, device=dev)
-        sws = torch.empty(D.dass_densify_select_workspace(n), dtype=torch.uint8, device=dev)
-        D.dass_densify_select(stage.stat_accum, stage.stat_count, s_err, self.is_var[self.cur][:n], self.tau_pos,
-                              self.tau_err, self.k_max, sel, nsel, sws)
+    def _size_pairs(self):
+        """Pair buffer from one binning of the current scene (all views), with headroom for the
+        spawned and moving Gaussians of the coming timesteps."""
+        fr = Frame(self.cams, self.n, tile=self.tile, batch=self.batch)
+        fr.project(self.view())
+        return int(fr.bin_sort() * 1.3) + (1 << 16)
+
+    def _alloc(self, n_dyn):
+        d = self._desc_template(n_dyn)
+        ws = D.dass_timestep_workspace(d)
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+
+    def _desc_template(self, n_dyn):
+        d = D.dass_timestep_desc()
+        d.n_max, d.sh_degree, d.n_cams = self.n_max, self.deg, len(self.cams)
+        for k in PARAM_NAMES:
+            setattr(d, k, _vp(self.bufs[k]))
+        d.is_var, d.n, d.cams = _vp(self.is_var), C.cast(C.pointer(self._n_host), C.c_void_p), \
+            C.cast(self._cams_arr, C.c_void_p)
+        d.n_dyn = n_dyn
+        d.tile, d.batch, d.pair_capacity = self.tile, self.batch, self.pair_capacity
+        for k, v in self.sched.items():
+            setattr(d, k, v)
+        for k, v in self.hp.items():
+            setattr(d, k, v)
+        return d
+
+    def run(self, t, targets, dyn_idx, offsets, z=None, targets_host=None, host_out=None, max_regrow=3):
+        """Reconstruct timestep t from the images `targets` (device; with targets_host (pinned host
+        tensor) the call first uploads it into `targets`). `offsets` ([n_dyn][7], device) gives the
+        initial offsets and receives the learned ones. host_out (optional dict of pinned host tensors
+        like `bufs` plus is_var) receives G_t. Returns a dict of what the timestep did."""
+        n_dyn = int(dyn_idx.numel())
+        dyn_idx = dyn_idx.contiguous()
+        off_init = offsets.contiguous().clone()
         if z is None:
-            z = torch.zeros((n, 3), device=dev)
-        n_total = torch.zeros(1, dtype=torch.int64, device=dev)
-        D.dass_spawn({k: v for k, v in self.bufs[self.cur].items()}, n, self.is_var[self.cur], sel, nsel,
-                     self.k_max, z[:n].contiguous(), n_total)
-        self.n = int(n_total.item())
-        spawned = int(nsel.item())
-        out = dict(loss=stage.loss, n=self.n, spawned=spawned, stage=stage)
-        # 4) densification-stage training of the var rows (Sec. 3.4, s3 iterations), then the
-        #    low-opacity pruning of the var rows
-        if self.n_densify > 0:
-            out.update(self._densify(targets))
-        return out
-
-    def _densify(self, targets):
-        n = self.n
-        isv = self.is_var[self.cur][:n]
-        n_base = int((isv == 0).sum().item())
-        if n == n_base:
-            return dict(densify_loss=None, pruned=0)
-        if bool(isv[:n_base].any()) or not bool(isv[n_base:].all()):
-            raise ValueError("densification stage needs the var rows as the contiguous tail of the arrays")
-        stage3 = DensifyStage(self.view(), n_base, self.cams, targets, tile=self.tile, batch=self.batch,
-                              lambda_dssim=self.lambda_dssim)
-        stage3.run(self.n_densify)
-        dev = self.device
-        g = self.view()
-        m = torch.empty(n, device=dev)
-        D.dass_prune_logits(g["opacity_logit"], self.prune_opacity, m)
-        src, dst = self.cur, 1 - self.cur
-        ws = torch.empty(max(1, D.dass_inherit_workspace(n)), dtype=torch.uint8, device=dev)
-        remap = torch.empty(n, dtype=torch.int32, device=dev)
-        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
-        D.dass_inherit(g, isv, m, False, {k: v for k, v in self.bufs[dst].items()}, self.is_var[dst], remap, n_out, ws)
-        self.cur = dst
-        self.n = int(n_out.item())
-        return dict(densify_loss=stage3.loss, pruned=n - self.n, n=self.n, densify_stage=stage3)
+            z = torch.zeros((self.n_max, 3), device=self.device)
+        if self.pair_capacity is None:
+            self.pair_capacity = self._size_pairs()
+            self._alloc(n_dyn)
+        torch.cuda.current_stream().synchronize()
+        for _ in range(max_regrow + 1):
+            d = self._desc_template(n_dyn)
+            self._n_host.value = self.n
+            d.targets, d.targets_host = _vp(targets), (C.c_void_p(targets_host.data_ptr())
+                                                       if targets_host is not None else None)
+            d.t = int(t)
+            d.dyn_idx, d.offsets_init, d.offsets, d.z = _vp(dyn_idx), _vp(off_init), _vp(offsets), _vp(z)
+            need = D.dass_timestep_workspace(d)
+            if self.workspace is None or self.workspace.numel() < need:
+                self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            d.workspace, d.workspace_bytes = _vp(self.workspace), self.workspace.numel()
+            if host_out is not None:
+                for k in PARAM_NAMES:
+                    setattr(d, "host_" + k, C.c_void_p(host_out[k].data_ptr()))
+                d.host_is_var = C.c_void_p(host_out["is_var"].data_ptr())
+            st, stats = D.dass_timestep(d, stream=self.stream)
+            if st == D.OK:
+                self.n = int(self._n_host.value)
+                self.last_stats = stats.as_dict()
+                s = self.last_stats
+                return dict(loss=s["loss_shift"], n=self.n, spawned=s["n_spawned"],
+                            densify_loss=s["loss_densify"] if s["n_var_trained"] else None,
+                            pruned=s["n_inherited"] + s["n_spawned"] - s["n_out"] if s["n_var_trained"] else 0,
+                            inherit_loss=s["loss_inherit"] if s["inherit_ran"] else None, stats=s)
+            # a stage overflowed the pair buffer: G_{t-1} is unchanged, regrow and rerun
+            self.pair_capacity = min((1 << 31) - 1, int(max(stats.pairs_max, self.pair_capacity) * 1.25) + 4096)
+            self.workspace = None
+        raise D.DassError("dass_timestep", D.ERR_CAPACITY)

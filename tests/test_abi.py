@@ -127,3 +127,28 @@ def test_host_side_field_and_loss_checks(lib):
     assert lib.dass_loss_target_stats(ok, cams, 2, C.c_void_p(260), None) == -1
     assert lib.dass_loss_cached(ok, ok, C.c_void_p(260), cams, 2, C.c_float(0.2), ok, ok, ok, 1 << 30, None) == -1
     assert lib.dass_loss_cached(ok, ok, ok, cams, 2, C.c_float(1.5), ok, ok, ok, 1 << 30, None) == -1   # lambda
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every descriptor the binding passes by pointer has the header's layout: a C program built
+    with the system compiler prints sizeof and each field's offsetof, compared with ctypes."""
+    import ctypes as C
+    from paper_2411_14847_gb300 import dass
+    structs = [dass.dass_camera, dass.dass_scene, dass.dass_step_desc, dass.dass_inherit_step_desc,
+               dass.dass_densify_step_desc, dass.dass_timestep_desc, dass.dass_timestep_stats, dass.dass_field]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dass.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("{s.__name__} %zu\\n", sizeof({s.__name__}));')
+        for f, _ in s._fields_:
+            lines.append(f'printf("{s.__name__}.{f} %zu\\n", offsetof({s.__name__}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for s in structs:
+        assert int(got[s.__name__]) == C.sizeof(s), s.__name__
+        for f, _ in s._fields_:
+            assert int(got[f"{s.__name__}.{f}"]) == getattr(s, f).offset, (s.__name__, f)

@@ -103,7 +103,7 @@ def test_timestep_with_densify_stage_and_pruning(dass):
     off[:, 3] = 1.0
     res = ts.run(1, tgt, dyn, off)
     assert res["densify_loss"] is not None
-    isv = ts.is_var[ts.cur][:ts.n].cpu().numpy()
+    isv = ts.is_var[:ts.n].cpu().numpy()
     nb = int((isv == 0).sum())
     assert nb == n_base
     assert np.all(isv[:nb] == 0) and np.all(isv[nb:] == 1)

@@ -102,10 +102,10 @@ def test_streaming_full_schedule(dass):
         l0 = torch.zeros(1, dtype=torch.float64, device="cuda")
         D.dass_loss(fr0.image, gt, cams, 0.2, dimg, l0, lws)
         n_prev = ts.n
-        n_var_prev = int(ts.is_var[ts.cur][:n_prev].sum())
+        n_var_prev = int(ts.is_var[:n_prev].sum())
         res = ts.run(t, gt, dyn, off.clone(), z=z)
         assert res["loss"] < float(l0), (t, res["loss"], float(l0))
-        n_var = int(ts.is_var[ts.cur][:ts.n].sum())
+        n_var = int(ts.is_var[:ts.n].sum())
         assert ts.n - n_var == n_base                              # base rows persist
         assert 0 <= res["spawned"] <= k_max
         assert n_var <= n_var_prev + res["spawned"]                # var rows: inherited subset + spawned - pruned
