@@ -161,20 +161,19 @@ int dass_preprocess_scenes_packed(const dass_scene* scenes /* host */, const das
 int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total,
                             size_t* bytes);
 
-/* Tile binning and device sort (tile-based rasterisation, Sec. 1 / Sec. 4.2).
+/* Tile binning and device radix sort (tile-based rasterisation, Sec. 1 / Sec. 4.2).
  * Each visible record (radius > 0) emits one (tile, record) pair per tile that its footprint
  * ellipse {d : d^T conic d <= 2 ln(255 o) + 0.01} reaches (at a pixel centre of the tile; every
  * pixel with alpha >= 1/255 lies inside that ellipse, so no contribution is lost); pairs are ordered by
- * the 64-bit key (global tile id << 32 | depth bits), ties in record order: pairs are bucketed by
- * tile (per-tile counters and a scan give every tile its output range) and each tile's list is then
- * sorted by (depth bits, record) in shared memory. Outputs: pair_rec[M] (record id per sorted pair),
+ * the 64-bit key (global tile id << 32 | depth bits), stable in record order: an LSD radix
+ * sort whose 32 depth-bit passes run on the records before duplication and whose tile-bit
+ * passes run on the pairs. Outputs: pair_rec[M] (record id per sorted pair),
  * tile_ranges[2*tiles_total] ([start, end) per tile, 0,0 when empty) and
  * counters[0] = M, counters[1] = 1 if M > pair_capacity (pairs beyond the capacity are
  * dropped: the render is then incomplete and the caller must grow and rerun; a pair count of
  * 2^31 or more cannot be stored by any capacity the call accepts).
  * Returns DASS_ERR_INVALID_ARG if pair_capacity >= 2^31 and DASS_ERR_OOM if workspace_bytes <
- * dass_bin_sort_workspace(). The first call on a device opts the sort's long-list kernel in to
- * 128 KB of shared memory (a host-side attribute): make it outside CUDA stream capture. */
+ * dass_bin_sort_workspace(). */
 int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const dass_camera* cams /* host */,
                   int n_cams, int tile, uint32_t* pair_rec, int64_t pair_capacity,
                   uint32_t* tile_ranges, int64_t* counters, void* workspace,
@@ -202,7 +201,7 @@ int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_offsets /*
  * DASS_BIN_SORT_STATIC_BYTES bytes that every GPU loading the library holds until the process
  * exits. The call itself allocates nothing.
  *  - Limit: dass_bin_sort_workspace(n_cams * rec_stride, pair_capacity, ...) must not exceed
- *    DASS_BIN_SORT_STATIC_BYTES (e.g. 500k records with 2.5M pairs fit); larger requests return
+ *    DASS_BIN_SORT_STATIC_BYTES (e.g. 500k records with 4M pairs fit); larger requests return
  *    DASS_ERR_OOM with an explanation in dass_last_error() and launch nothing.
  *  - Set-up: the first call on a device looks up the device address of the array (once per
  *    device, with that device current); make that first call before any stream capture. The

@@ -190,7 +190,7 @@ DASS_API int dass_preprocess_scenes_packed(const dass_scene* scenes, const dass_
 DASS_API int dass_bin_sort_workspace(int64_t n_records, int64_t pair_capacity, int32_t tiles_total, size_t* bytes) {
     if (n_records < 0 || pair_capacity < 0 || tiles_total < 0 || !bytes) return DASS_ERR_INVALID_ARG;
     if (n_records >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
-    *bytes = bin_sort_workspace_bytes(n_records, pair_capacity, tiles_total);
+    *bytes = bin_sort_workspace_bytes(n_records, pair_capacity);
     return DASS_OK;
 }
 
@@ -204,7 +204,7 @@ DASS_API int dass_bin_sort(const dass_splat* splats, int64_t rec_stride, const d
     // sorted-pair positions are held as int32 by the compositing kernels: capacity < 2^31
     if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     if (n_rec > 0 && (!splats || !pair_rec || !workspace)) return DASS_ERR_INVALID_ARG;
-    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity, ct.tiles_total)) return DASS_ERR_OOM;
+    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity)) return DASS_ERR_OOM;
     return bin_sort_launch(splats, n_rec, ct, pair_rec, pair_capacity, tile_ranges, (long long*)counters, workspace,
                            workspace_bytes, as_stream(stream));
 }
@@ -219,7 +219,7 @@ DASS_API int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_o
     long long n_rec = rec_offsets[n_cams];
     if (pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     if (n_rec > 0 && (!splats || !pair_rec || !workspace)) return DASS_ERR_INVALID_ARG;
-    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity, ct.tiles_total)) return DASS_ERR_OOM;
+    if (workspace_bytes < bin_sort_workspace_bytes(n_rec, pair_capacity)) return DASS_ERR_OOM;
     return bin_sort_launch(splats, n_rec, ct, pair_rec, pair_capacity, tile_ranges, (long long*)counters, workspace,
                            workspace_bytes, as_stream(stream));
 }

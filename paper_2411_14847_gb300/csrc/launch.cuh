@@ -19,8 +19,7 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
                           float* d_opacity_logit, float* d_sh, float* d_keep, cudaStream_t st);
 int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
                          float* accum, int* count, cudaStream_t st);
-size_t bin_sort_workspace_bytes(long long n_rec, long long cap, long long tiles);
-int sort_prepare();   // kernel attributes of the sort, set outside stream capture
+size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,

@@ -9,7 +9,7 @@
 #include "common.cuh"
 
 namespace dass {
-size_t bin_sort_workspace_bytes(long long n_rec, long long cap, long long tiles);
+size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
 void set_error_message(const char* msg);
@@ -62,7 +62,7 @@ DASS_API int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, 
     long long n_rec = (long long)n_cams * rec_stride;
     if (n_rec >= (1ll << 32) || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
     if (n_rec > 0 && (!splats || !pair_rec)) return DASS_ERR_INVALID_ARG;
-    size_t need = bin_sort_workspace_bytes(n_rec, pair_capacity, ct.tiles_total);
+    size_t need = bin_sort_workspace_bytes(n_rec, pair_capacity);
     if (need > kScratchBytes) {
         set_error_message("dass_bin_sort_static: records and pair capacity need more scratch than the "
                           "DASS_BIN_SORT_STATIC_BYTES static array; use dass_bin_sort with a workspace");

@@ -1,15 +1,7 @@
-// Tile binning and sorting for the tile-based rasteriser (no CUB). The pair order is that of the
-// 64-bit key (tile id << 32 | depth bits), ties in record order, built in three steps:
-//   1. each visible record counts the tiles its footprint ellipse reaches; a scan over records
-//      gives every record its range of pair slots;
-//   2. duplication writes each (tile, record) pair into its slot and takes the pair's rank within
-//      its tile from an atomic per-tile counter; a scan over the tile counts gives each tile its
-//      range of the output (the tile ranges) and the pairs are scattered into their tile's range
-//      as 64-bit keys (depth bits << 32 | record);
-//   3. every tile's keys are sorted in shared memory (one CTA per tile, an ascending bitonic
-//      network on the padded list; long lists go to a second kernel with a larger shared buffer, or
-//      to the same network run in global memory), which orders the tile by (depth, record) no
-//      matter in which order the atomics ranked its pairs.
+// Tile binning and a hand-written stable LSD radix sort (no CUB) for the tile-based
+// rasteriser. The pair order is that of the 64-bit key (tile id << 32 | depth bits), ties in
+// record order: the 32 depth-bit digits are sorted on the records before duplication (all
+// pairs of a record share its depth), the tile-id digits on the pairs afterwards.
 //
 // Every kernel reads its item count from device memory and sizes its work from it, so the
 // whole sequence needs no host synchronisation and can be captured in a CUDA graph; grids are
@@ -24,11 +16,18 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 2048 elements per scan block
 
-constexpr int kSortThreads = 512;         // threads of the per-tile sort CTA
-constexpr int kSortCap = 4096;            // longest tile list sorted by the per-tile kernel (32 KB)
-constexpr int kBigThreads = 1024;
-constexpr int kBigCap = 16384;            // longest list sorted in shared memory by the big-tile kernel (128 KB)
-constexpr int kBigBlocks = 152;
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096 keys per radix block
+constexpr int kMaxDigitBits = 9;
+constexpr int kMaxDigits = 1 << kMaxDigitBits;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
 
 // ----------------------------------------------------------------- exclusive scan (u32 -> u32)
 // Three passes: per-block sums, one-block scan of the sums (64-bit, also writes the total),
@@ -118,6 +117,173 @@ __global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t* __re
     }
 }
 
+// ----------------------------------------------------------------- radix sort passes
+
+__device__ __forceinline__ long long radix_nblocks(long long n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+// Per-block digit counts, digit-major: hist[d * nb + b].
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                   const long long* n_dev, uint32_t* __restrict__ hist,
+                                                                   long long* hist_len, int shift, int dbits) {
+    long long n = *n_dev;
+    long long nb = radix_nblocks(n);
+    int nd = 1 << dbits;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hist_len = nb * nd;
+    if ((long long)blockIdx.x >= nb) return;
+    __shared__ uint32_t sh[kMaxDigits];
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) sh[d] = 0;
+    __syncthreads();
+    unsigned mask = (unsigned)nd - 1u;
+    long long base = (long long)blockIdx.x * kRadixTile;
+    // all loads of the block are issued before any is used (one memory latency per block)
+    uint32_t kr[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        kr[r] = idx < n ? keys[idx] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        long long idx = base + r * kRadixThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&sh[(kr[r] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) hist[(long long)d * nb + blockIdx.x] = sh[d];
+}
+
+// Lanes of `among` whose digit equals this lane's (one ballot per digit bit; the cost does not
+// grow with the number of distinct digits in the warp).
+__device__ __forceinline__ unsigned digit_peers(unsigned digit, int dbits, unsigned among) {
+    unsigned peers = among;
+#pragma unroll
+    for (int b = 0; b < kMaxDigitBits; ++b) {
+        if (b < dbits) {
+            const bool bit = (digit >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+    }
+    return peers;
+}
+
+// Block-wide exclusive scan of v over the 256 threads (one value each); returns the prefix.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) woff += w < warp ? s_warp[w] : 0u;
+    return woff + incl - v;
+}
+
+// Stable scatter of one pass. Warp w owns the contiguous keys [w*kRadixItems*32, (w+1)*...) of
+// the block's tile (blocked arrangement: warp, then round, then lane is key order). A key's
+// rank among equal digits is its warp's running count (ballot-based peer masks per round) plus the counts of
+// the warps before it; a block-wide scan over digits gives each key its slot in a block-local
+// digit-sorted order. Keys and values are exchanged through shared memory into that order and
+// written out so that consecutive threads write consecutive positions of each digit's output
+// run (coalesced), at the block's scanned global digit offsets.
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const long long* n_dev, const uint32_t* __restrict__ hist_scanned, int shift,
+    int dbits) {
+    const long long n = *n_dev;
+    const long long nb = radix_nblocks(n);
+    if ((long long)blockIdx.x >= nb) return;
+    const int nd = 1 << dbits;
+    const unsigned mask = (unsigned)nd - 1u;
+    constexpr int kWarpItems = kRadixItems * 32;
+    // s_cnt (per-warp digit counts, then per-warp offsets) and later the exchanged keys/values
+    // share one buffer: the counts are dead once every key knows its local slot.
+    __shared__ uint32_t s_buf[2 * kRadixTile];
+    __shared__ uint32_t s_start[kMaxDigits];    // block-local start of each digit
+    __shared__ uint32_t s_gbase[kMaxDigits];    // global output start of each digit (this block)
+    __shared__ uint32_t s_warp[kRadixWarps];
+    uint32_t(*s_cnt)[kMaxDigits] = reinterpret_cast<uint32_t(*)[kMaxDigits]>(s_buf);
+    uint32_t* s_key = s_buf;
+    uint32_t* s_val = s_buf + kRadixTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long tile0 = (long long)blockIdx.x * kRadixTile;
+    const long long base = tile0 + (long long)warp * kWarpItems;
+    // the block's keys and values are requested first, so the global latency of the (strided)
+    // digit offsets below overlaps with them
+    uint32_t kr[kRadixItems], vr[kRadixItems], slot[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const long long idx = base + r * 32 + lane;
+        kr[r] = idx < n ? __ldcs(keys_in + idx) : 0u;
+        vr[r] = idx < n ? __ldcs(vals_in + idx) : 0u;
+    }
+    for (int d = threadIdx.x; d < nd; d += kRadixThreads) {
+        s_gbase[d] = hist_scanned[(long long)d * nb + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) s_cnt[w][d] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned digit = (kr[r] >> shift) & mask;
+        const unsigned peers = digit_peers(digit, dbits, __ballot_sync(0xffffffffu, valid));
+        const uint32_t before = valid ? s_cnt[warp][digit] : 0u;
+        slot[r] = before + (uint32_t)__popc(peers & lanemask_lt());
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][digit] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: warp offsets within the digit and the digit's total; 2 digits per thread
+    uint32_t tot = 0;
+    for (int d = 2 * threadIdx.x; d < 2 * threadIdx.x + 2 && d < nd; ++d) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) {
+            const uint32_t c = s_cnt[w][d];
+            s_cnt[w][d] = run;
+            run += c;
+        }
+        s_start[d] = run;     // digit total for now
+        tot += run;
+    }
+    const uint32_t pre = block_exclusive_scan(tot, s_warp);
+    if (2 * threadIdx.x < nd) {
+        const uint32_t t0 = s_start[2 * threadIdx.x];
+        s_start[2 * threadIdx.x] = pre;
+        if (2 * threadIdx.x + 1 < nd) s_start[2 * threadIdx.x + 1] = pre + t0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned digit = (kr[r] >> shift) & mask;
+        if (valid) slot[r] += s_start[digit] + s_cnt[warp][digit];
+    }
+    __syncthreads();    // counts are dead from here on: the buffer takes the keys and values
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        if (base + r * 32 + lane < n) {
+            s_key[slot[r]] = kr[r];
+            s_val[slot[r]] = vr[r];
+        }
+    }
+    __syncthreads();
+    const int cnt = (int)(n - tile0 < kRadixTile ? n - tile0 : kRadixTile);
+    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+        const uint32_t key = s_key[i];
+        const unsigned digit = (key >> shift) & mask;
+        const uint32_t pos = s_gbase[digit] + (uint32_t)i - s_start[digit];
+        keys_out[pos] = key;
+        vals_out[pos] = s_val[i];
+    }
+}
+
 // ----------------------------------------------------------------- binning kernels
 
 // Record -> (depth key, own index, number of tiles whose pixel centres the footprint ellipse
@@ -136,7 +302,8 @@ __device__ __forceinline__ bool record_footprint(const dass_splat* __restrict__ 
 }
 
 __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
-                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ counts) {
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                 uint32_t* __restrict__ counts) {
     long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (rec >= n_rec) return;
     const CamInfo& cam = ct.c[cam_of_record(ct, rec)];
@@ -151,8 +318,15 @@ __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long lon
             if (footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) cnt += r1 - r0 + 1;
         }
     }
-    keys[rec] = __float_as_uint(depth);     // positive depths: the bits order like the values
+    keys[rec] = cnt > 0 ? __float_as_uint(depth) : 0xffffffffu;
+    vals[rec] = (uint32_t)rec;
     counts[rec] = (uint32_t)cnt;
+}
+
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
+                                     uint32_t* __restrict__ out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = counts[order[i]];
 }
 
 // Warp-wide inclusive sum of v (all lanes take part).
@@ -165,9 +339,7 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, int lane) {
     return v;
 }
 
-// Emit the pairs of each record (record order) into its scanned slot range, each with its tile and
-// its rank within the tile (an atomic per-tile counter; the order of the ranks is arbitrary, the
-// per-tile sort restores the depth order). A warp owns 32
+// Emit the pairs of each record (depth order) into its scanned slot range. A warp owns 32
 // consecutive records and the contiguous output range their pairs fill. The work is balanced
 // over the lanes in three steps instead of each lane looping over its own record's tiles:
 //   1. each lane computes its record's footprint and tile-row range; a warp scan numbers the
@@ -176,16 +348,16 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, int lane) {
 //      over the lanes' first unit), solves that tile row's run of tiles (the same footprint_row
 //      that counted the pairs) and a warp scan gives the run's output offset;
 //   3. output slots are dealt to the lanes in order: a lane finds its slot's unit (binary search
-//      over the staged runs) and writes (tile, rank, record) -- consecutive lanes write consecutive
-//      slots, and their tiles are mostly distinct, which spreads the counter atomics.
+//      over the staged runs) and writes (tile, record) -- consecutive lanes write consecutive
+//      slots.
 // A warp whose records have more than kDupUnits tile rows (very large footprints) writes its
 // pairs lane by lane instead.
 constexpr int kDupThreads = 256;
 constexpr int kDupUnits = 128;
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const dass_splat* __restrict__ splats, long long n_rec, CamTable ct, const uint32_t* __restrict__ offsets,
-    const long long* total, long long capacity, uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rank,
-    uint32_t* __restrict__ pair_rec, uint32_t* __restrict__ tile_count, long long* counters) {
+    const dass_splat* __restrict__ splats, long long n_rec, CamTable ct, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ offsets, const long long* total, long long capacity,
+    uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rec, long long* counters) {
     constexpr int NW = kDupThreads / 32;
     __shared__ Footprint s_f[kDupThreads];
     __shared__ int s_y0[kDupThreads];
@@ -207,7 +379,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     uint32_t rec = 0;
     long long pos = 0;
     if (active) {
-        rec = (uint32_t)k;
+        rec = order[k];
         pos = offsets[k];
     }
     const long long wbase = __shfl_sync(0xffffffffu, pos, 0);
@@ -234,9 +406,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
                 if (!footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) continue;
                 for (int x = r0; x <= r1; ++x, ++pos)
                     if (pos < capacity && pos < wend) {
-                        const uint32_t t = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
-                        pair_tile[pos] = t;
-                        pair_rank[pos] = atomicAdd(tile_count + t, 1u);
+                        pair_tile[pos] = (uint32_t)(cam.tile_base + y * cam.tiles_x + x);
                         pair_rec[pos] = rec;
                     }
             }
@@ -291,127 +461,36 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
         }
         const long long p = wbase + i;
         if (p < capacity) {
-            const uint32_t t = s_utile[warp][lo] + (i - s_upos[warp][lo]);
-            pair_tile[p] = t;
-            pair_rank[p] = atomicAdd(tile_count + t, 1u);
+            pair_tile[p] = s_utile[warp][lo] + (i - s_upos[warp][lo]);
             pair_rec[p] = s_urec[warp][lo];
         }
     }
 }
 
-// [start, end) of every tile's run from the scanned tile counts (0, 0 for an empty tile).
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ start, const uint32_t* __restrict__ count, int tiles,
+// [start, end) of every tile's run in the sorted pair list. Grid-stride over groups of 4
+// consecutive pairs: one 16-byte load per group (the key buffer is 256-byte aligned and its
+// capacity a multiple of 64 keys, so the group never leaves the buffer; keys at or beyond n are
+// ignored) plus the keys just before and after it.
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const long long* n_dev,
                                    uint32_t* __restrict__ ranges) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tiles) return;
-    const uint32_t c = count[t], s0 = c ? start[t] : 0u;
-    ranges[2 * (long long)t] = s0;
-    ranges[2 * (long long)t + 1] = s0 + c;
-}
-
-// Pair p goes to slot start[tile] + rank of its tile's range, as the key depth bits << 32 | record.
-__global__ void bucket_scatter_kernel(const uint32_t* __restrict__ pair_tile, const uint32_t* __restrict__ pair_rank,
-                                      const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ depth_key,
-                                      const uint32_t* __restrict__ tile_start, const long long* stored,
-                                      unsigned long long* __restrict__ keys) {
-    const long long n = *stored;
+    const long long n = *n_dev;
+    const long long nq = (n + 3) / 4;
     const long long step = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += step) {
-        const uint32_t r = pair_rec[p];
-        keys[tile_start[pair_tile[p]] + pair_rank[p]] = ((unsigned long long)depth_key[r] << 32) | r;
-    }
-}
-
-__device__ __forceinline__ void cmp_swap(unsigned long long& a, unsigned long long& b) {
-    const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
-    a = lo;
-    b = hi;
-}
-
-// Ascending bitonic sorting network over positions [0, n2) (n2 a power of two) of `s`, with every
-// position >= len holding the largest key: for each block size k the first step compares position
-// i with its mirror k - 1 - i inside the block, the next steps compare i with i + j for j = k/4 ..
-// 1; every comparison puts the smaller key at the lower position, so the padding never moves below
-// len and comparisons whose upper position is >= len can be skipped. One barrier per step.
-// Comparison t of a step with distance j (j a power of two): positions lo = 2t - (t mod j) (the
-// t-th position whose bit j is clear) and, for the mirror step of block size k = 2j, hi = lo xor
-// (k - 1), else hi = lo + j. I is int for shared memory and long long in global memory.
-template <int NT, class I, class Keys>
-__device__ void bitonic_sort(Keys s, I len, I n2) {
-    for (I k = 2; k <= n2; k <<= 1) {
-        const I half = k >> 1;
-        for (I t = threadIdx.x; t < n2 / 2; t += NT) {
-            const I lo = 2 * t - (t & (half - 1)), hi = lo ^ (k - 1);
-            if (hi < len) cmp_swap(s[lo], s[hi]);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += step) {
+        const long long i0 = 4 * q;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(tiles + i0));
+        const uint32_t t[4] = {v.x, v.y, v.z, v.w};
+        uint32_t prev = i0 > 0 ? __ldg(tiles + i0 - 1) : 0xffffffffu;
+        const uint32_t after = i0 + 4 < n ? __ldg(tiles + i0 + 4) : 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            if (i >= n) break;
+            const uint32_t next = k < 3 ? (i + 1 < n ? t[k + 1] : 0xffffffffu) : after;
+            if (i == 0 || prev != t[k]) ranges[2 * (long long)t[k]] = (uint32_t)i;
+            if (next != t[k]) ranges[2 * (long long)t[k] + 1] = (uint32_t)(i + 1);
+            prev = t[k];
         }
-        __syncthreads();
-        for (I j = k >> 2; j > 0; j >>= 1) {
-            for (I t = threadIdx.x; t < n2 / 2; t += NT) {
-                const I lo = 2 * t - (t & (j - 1)), hi = lo + j;
-                if (hi < len) cmp_swap(s[lo], s[hi]);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-__device__ __forceinline__ long long pow2_at_least(long long n) {
-    long long p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
-// One CTA per tile: sort the tile's keys (depth bits << 32 | record) in shared memory and write
-// the records. Lists longer than kSortCap are queued for big_tile_sort_kernel.
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const unsigned long long* __restrict__ keys,
-                                                                 const uint32_t* __restrict__ ranges,
-                                                                 uint32_t* __restrict__ pair_rec,
-                                                                 uint32_t* __restrict__ big_list,
-                                                                 unsigned int* __restrict__ big_count) {
-    __shared__ unsigned long long s[kSortCap];
-    const int tile = blockIdx.x;
-    const uint32_t start = ranges[2 * (long long)tile];
-    const int len = (int)(ranges[2 * (long long)tile + 1] - start);
-    if (len <= 1) {
-        if (len == 1 && threadIdx.x == 0) pair_rec[start] = (uint32_t)keys[start];
-        return;
-    }
-    if (len > kSortCap) {
-        if (threadIdx.x == 0) big_list[atomicAdd(big_count, 1u)] = (uint32_t)tile;
-        return;
-    }
-    const int n2 = (int)pow2_at_least(len);
-    for (int i = threadIdx.x; i < n2; i += kSortThreads) s[i] = i < len ? keys[start + i] : ~0ull;
-    __syncthreads();
-    bitonic_sort<kSortThreads, int>(s, len, n2);
-    for (int i = threadIdx.x; i < len; i += kSortThreads) pair_rec[start + i] = (uint32_t)s[i];
-}
-
-// Tiles whose lists exceed kSortCap: up to kBigCap keys in dynamic shared memory, longer lists with
-// the same network run in place on the keys in global memory (positions beyond the list are never
-// touched). Persistent CTAs walk the queue.
-__global__ void __launch_bounds__(kBigThreads) big_tile_sort_kernel(unsigned long long* __restrict__ keys,
-                                                                    const uint32_t* __restrict__ ranges,
-                                                                    uint32_t* __restrict__ pair_rec,
-                                                                    const uint32_t* __restrict__ big_list,
-                                                                    const unsigned int* __restrict__ big_count) {
-    extern __shared__ unsigned long long sbig[];
-    const unsigned int nb = *big_count;
-    for (unsigned int b = blockIdx.x; b < nb; b += gridDim.x) {
-        const long long tile = big_list[b];
-        const uint32_t start = ranges[2 * tile];
-        const long long len = (long long)(ranges[2 * tile + 1] - start);
-        const long long n2 = pow2_at_least(len);
-        if (len <= kBigCap) {
-            for (int i = threadIdx.x; i < (int)n2; i += kBigThreads) sbig[i] = i < len ? keys[start + i] : ~0ull;
-            __syncthreads();
-            bitonic_sort<kBigThreads, int>(sbig, (int)len, (int)n2);
-            for (int i = threadIdx.x; i < (int)len; i += kBigThreads) pair_rec[start + i] = (uint32_t)sbig[i];
-        } else {
-            bitonic_sort<kBigThreads, long long>(keys + start, len, n2);
-            for (long long i = threadIdx.x; i < len; i += kBigThreads) pair_rec[start + i] = (uint32_t)keys[start + i];
-        }
-        __syncthreads();
     }
 }
 
@@ -433,37 +512,35 @@ struct Carver {
 };
 
 struct SortScratch {
-    long long* scal;             // [8] device scalars: 0 n_rec, 1 tiles, 2 total pairs
-    uint32_t* depth_key;         // record-sized
+    long long* scal;             // [8] device scalars: 0 n_rec, 1 hist_len, 2 total pairs, 3.. spare
+    uint32_t* kA; uint32_t* vA; uint32_t* kB; uint32_t* vB;   // record-sized
     uint32_t* counts;            // record-sized
     uint32_t* offsets;           // record-sized
+    uint32_t* hist;              // digits * max blocks
     unsigned long long* partial; // scan partials
-    uint32_t* tile_count;        // tile-sized
-    uint32_t* tile_start;        // tile-sized
-    uint32_t* big_list;          // tile-sized
-    unsigned int* big_count;
-    uint32_t* pair_tile;         // pair-sized
-    uint32_t* pair_rank;
-    uint32_t* pair_rec;
-    unsigned long long* keys;    // pair-sized
+    uint32_t* pk0; uint32_t* pk1; uint32_t* pv1;  // pair-sized
 };
 
-SortScratch carve(Carver& cv, long long n_rec, long long cap, long long tiles) {
+long long hist_capacity(long long n_max) {
+    return (long long)kMaxDigits * ((n_max + kRadixTile - 1) / kRadixTile + 1);
+}
+
+SortScratch carve(Carver& cv, long long n_rec, long long cap) {
     SortScratch s;
-    const long long scan_len = n_rec > tiles ? n_rec : tiles;
+    long long big = n_rec > cap ? n_rec : cap;
     s.scal = cv.take<long long>(8);
-    s.depth_key = cv.take<uint32_t>(n_rec);
+    s.kA = cv.take<uint32_t>(n_rec);
+    s.vA = cv.take<uint32_t>(n_rec);
+    s.kB = cv.take<uint32_t>(n_rec);
+    s.vB = cv.take<uint32_t>(n_rec);
     s.counts = cv.take<uint32_t>(n_rec);
     s.offsets = cv.take<uint32_t>(n_rec);
+    s.hist = cv.take<uint32_t>(hist_capacity(big));
+    long long scan_len = hist_capacity(big) > n_rec ? hist_capacity(big) : n_rec;
     s.partial = cv.take<unsigned long long>(scan_len / kScanTile + 2);
-    s.tile_count = cv.take<uint32_t>(tiles);
-    s.tile_start = cv.take<uint32_t>(tiles);
-    s.big_list = cv.take<uint32_t>(tiles);
-    s.big_count = cv.take<unsigned int>(1);
-    s.pair_tile = cv.take<uint32_t>(cap);
-    s.pair_rank = cv.take<uint32_t>(cap);
-    s.pair_rec = cv.take<uint32_t>(cap);
-    s.keys = cv.take<unsigned long long>(cap);
+    s.pk0 = cv.take<uint32_t>(cap);
+    s.pk1 = cv.take<uint32_t>(cap);
+    s.pv1 = cv.take<uint32_t>(cap);
     return s;
 }
 
@@ -477,66 +554,96 @@ int scan_u32(const uint32_t* in, uint32_t* out, const long long* len_dev, long l
     return check_launch("scan_u32");
 }
 
-}  // namespace
-
-size_t bin_sort_workspace_bytes(long long n_rec, long long cap, long long tiles) {
-    Carver cv{nullptr, 0, 0};
-    carve(cv, n_rec, cap, tiles);
-    return cv.used;
+// Stable sort of (keys, vals) by bits [0, bits) of the keys; n from *n_dev (<= n_cap).
+// Pass i reads buffer set i%2 and writes set (i+1)%2 of {(k0, v0), (k1, v1)}; returns the
+// index of the set holding the result.
+int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const long long* n_dev, long long n_cap,
+               int bits, SortScratch& s, cudaStream_t st, int* result_set) {
+    int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    if (passes < 1) passes = 1;
+    int dbits = (bits + passes - 1) / passes;
+    int nb = div_up(n_cap > 0 ? n_cap : 1, kRadixTile);
+    long long hist_cap = (long long)(1 << dbits) * nb;
+    uint32_t* kin = k0; uint32_t* vin = v0; uint32_t* kout = k1; uint32_t* vout = v1;
+    for (int p = 0; p < passes; ++p) {
+        int shift = p * dbits;
+        int db = dbits;
+        if (shift + db > bits) db = bits - shift;
+        radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kin, n_dev, s.hist, s.scal + 1, shift, db); count_launch();
+        int rc = scan_u32(s.hist, s.hist, s.scal + 1, hist_cap, s.partial, nullptr, st);
+        if (rc) return rc;
+        radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kin, vin, kout, vout, n_dev, s.hist, shift, db); count_launch();
+        int lc = check_launch("radix_pass");
+        if (lc) return lc;
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    *result_set = passes % 2;
+    return DASS_OK;
 }
 
-// Kernel attributes that must be set outside stream capture (the big-tile sort's shared memory).
-int sort_prepare() {
-    return allow_dynamic_smem(reinterpret_cast<const void*>(big_tile_sort_kernel),
-                              kBigCap * (int)sizeof(unsigned long long));
+int bits_for(long long values) {
+    int b = 1;
+    while ((1ll << b) < values) ++b;
+    return b;
+}
+
+}  // namespace
+
+size_t bin_sort_workspace_bytes(long long n_rec, long long cap) {
+    Carver cv{nullptr, 0, 0};
+    carve(cv, n_rec, cap);
+    return cv.used;
 }
 
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec,
                     long long cap, uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes,
                     cudaStream_t st) {
-    const long long tiles = ct.tiles_total;
     Carver cv{reinterpret_cast<char*>(ws), 0, ws_bytes};
-    SortScratch s = carve(cv, n_rec, cap, tiles);
+    SortScratch s = carve(cv, n_rec, cap);
     if (cv.used > ws_bytes) return DASS_ERR_OOM;
-    if (n_rec == 0 || tiles == 0) {
-        DASS_CHECK_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, st));
+    DASS_CHECK_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ct.tiles_total, st));
+    if (n_rec == 0) {
         DASS_CHECK_CUDA(cudaMemsetAsync(counters, 0, sizeof(long long) * 3, st));
         return DASS_OK;
     }
-    if (int rc = sort_prepare()) return rc;
-    DASS_CHECK_CUDA(cudaMemsetAsync(s.tile_count, 0, sizeof(uint32_t) * (size_t)tiles, st));
-    DASS_CHECK_CUDA(cudaMemsetAsync(s.big_count, 0, sizeof(unsigned int), st));
     set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec); count_launch();
-    set_len_kernel<<<1, 1, 0, st>>>(s.scal + 1, tiles); count_launch();
-    // 1) tiles per record and the records' pair slots
-    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.depth_key, s.counts); count_launch();
+    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.kA, s.vA, s.counts); count_launch();
     int rc = check_launch("bin_count");
     if (rc) return rc;
-    rc = scan_u32(s.counts, s.offsets, s.scal + 0, n_rec, s.partial, s.scal + 2, st);
+    // 1) depth digits on the records (32 bits)
+    int set = 0;
+    rc = radix_sort(s.kA, s.vA, s.kB, s.vB, s.scal + 0, n_rec, 32, s, st, &set);
     if (rc) return rc;
-    // 2) (tile, rank, record) per pair (stored count -> counters[2]), tile ranges, bucket scatter
-    duplicate_kernel<<<div_up(n_rec, kDupThreads), kDupThreads, 0, st>>>(splats, n_rec, ct, s.offsets, s.scal + 2,
-                                                                         cap, s.pair_tile, s.pair_rank, s.pair_rec,
-                                                                         s.tile_count, counters);
-    count_launch();
-    if ((rc = check_launch("duplicate"))) return rc;
-    rc = scan_u32(s.tile_count, s.tile_start, s.scal + 1, tiles, s.partial, nullptr, st);
+    uint32_t* order = set == 0 ? s.vA : s.vB;
+    // 2) pair offsets in depth order
+    gather_counts_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(order, s.counts, s.offsets, n_rec); count_launch();
+    rc = scan_u32(s.offsets, s.offsets, s.scal + 0, n_rec, s.partial, s.scal + 2, st);
     if (rc) return rc;
-    tile_ranges_kernel<<<div_up(tiles, 256), 256, 0, st>>>(s.tile_start, s.tile_count, (int)tiles, tile_ranges);
+    // 3) duplicate into tile-keyed pairs (stored count -> counters[2])
+    int tbits = bits_for(ct.tiles_total > 1 ? ct.tiles_total : 2);
+    int passes = (tbits + kMaxDigitBits - 1) / kMaxDigitBits;
+    // the sort must end in (pk?, pair_rec): pass i writes set (i+1)%2; choose the start set
+    uint32_t *k_out = s.pk0, *v_out = pair_rec, *k_tmp = s.pk1, *v_tmp = s.pv1;
+    uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
+    uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
+    duplicate_kernel<<<div_up(n_rec, kDupThreads), kDupThreads, 0, st>>>(splats, n_rec, ct, order, s.offsets,
+                                                                         s.scal + 2, cap, k_start, v_start, counters);
     count_launch();
-    const int sb = div_up(cap > 0 ? cap : 1, 256);
-    bucket_scatter_kernel<<<sb < 152 * 16 ? sb : 152 * 16, 256, 0, st>>>(s.pair_tile, s.pair_rank, s.pair_rec,
-                                                                         s.depth_key, s.tile_start, counters + 2,
-                                                                         s.keys);
+    rc = check_launch("duplicate");
+    if (rc) return rc;
+    // 4) tile digits on the pairs
+    const long long* m_dev = counters + 2;
+    if (passes % 2 == 0)
+        rc = radix_sort(k_out, v_out, k_tmp, v_tmp, m_dev, cap, tbits, s, st, &set);
+    else
+        rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
+    if (rc) return rc;
+    // 5) tile ranges
+    const int rq = div_up(div_up(cap, 4), 256);
+    tile_ranges_kernel<<<rq < 152 * 8 ? rq : 152 * 8, 256, 0, st>>>(k_out, m_dev, tile_ranges);
     count_launch();
-    if ((rc = check_launch("bucket_scatter"))) return rc;
-    // 3) per-tile sort by (depth, record)
-    tile_sort_kernel<<<(int)tiles, kSortThreads, 0, st>>>(s.keys, tile_ranges, pair_rec, s.big_list, s.big_count);
-    count_launch();
-    big_tile_sort_kernel<<<kBigBlocks, kBigThreads, kBigCap * sizeof(unsigned long long), st>>>(
-        s.keys, tile_ranges, pair_rec, s.big_list, s.big_count);
-    count_launch();
-    return check_launch("tile_sort");
+    return check_launch("tile_ranges");
 }
 
 // Generic pieces reused by other translation units.

@@ -102,7 +102,7 @@ struct RenderBufs {
 
 // Scratch of the render part (sort and loss workspaces, cached target statistics, tracking).
 void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long long cap, float lam, RenderBufs& b) {
-    b.bin_ws_bytes = bin_sort_workspace_bytes(n_rec, cap, ct.tiles_total);
+    b.bin_ws_bytes = bin_sort_workspace_bytes(n_rec, cap);
     b.bin_ws = a.take<char>((long long)b.bin_ws_bytes);
     b.loss_ws_bytes = loss_workspace_bytes(ct);
     b.loss_ws = a.take<char>((long long)b.loss_ws_bytes);
@@ -141,7 +141,6 @@ int stage_begin(const CamTable& ct, const float* targets, int batch, RenderBufs&
     DASS_CHECK_CUDA(cudaMemsetAsync(b.track, 0, 2 * sizeof(long long), st));
     if (b.ystats)
         if (int rc = target_stats_launch(targets, ct, const_cast<float*>(b.ystats), st)) return rc;
-    if (int rc = sort_prepare()) return rc;
     return render_prepare(ct.tile, batch);
 }
 
