@@ -125,6 +125,43 @@ def test_bin_sort_matches_oracle_binning(dass):
             assert s_t <= got <= (s_t | m_t), (tile, t, s_t - got, got - s_t - m_t)
 
 
+def test_bin_sort_long_tile_lists(dass):
+    """Tiles with long lists (about 6,000 and 20,000 pairs, far more than one compositing batch or one
+    sort block): order and tile sets as in the oracle's binning."""
+    from paper_2411_14847_gb300 import raster
+    cams = synth.arc_cameras(2, 4.0, 64, 48)
+    n = 24000
+    rng = np.random.default_rng(11)
+    rec = np.zeros((2 * n, 12), np.float32)
+    rec[:, 0] = rng.uniform(20.0, 27.0, 2 * n)
+    rec[:, 1] = rng.uniform(18.0, 25.0, 2 * n)
+    sig = rng.uniform(0.5, 1.5, 2 * n)
+    rec[:, 2], rec[:, 4] = 1.0 / sig ** 2, 1.0 / sig ** 2
+    rec[:, 5] = rng.uniform(0.05, 1.0, 2 * n)
+    rec[:, 9] = rng.integers(1, 200, 2 * n).astype(np.float32) * 0.125      # depth ties
+    rad = np.full(2 * n, 6, np.int32)
+    rad[n + 7000:] = 0                                                        # camera 1: 7,000 visible
+    rec[:, 10] = rad.view(np.float32)
+    fr = raster.Frame(cams, n, tile=8, batch=64)
+    fr.splats.copy_(torch.from_numpy(rec))
+    m = fr.bin_sort()
+    torch.cuda.synchronize()
+    cam_of = np.repeat(np.arange(2), n)
+    sure, maybe, total = binning.bin_records(rec[:, 0], rec[:, 1], rec[:, 2:5].astype(np.float64), rec[:, 5], rad,
+                                             cam_of, cams, 8)
+    pr = fr.pair_rec[:m].cpu().numpy().astype(np.int64)
+    rg = fr.tile_ranges.cpu().numpy().astype(np.int64)
+    lens = rg[:, 1] - rg[:, 0]
+    assert lens[:48].max() > 16384 and 4096 < lens[48:].max() <= 16384, (lens[:48].max(), lens[48:].max())
+    for t in range(total):
+        lst = pr[rg[t, 0]:rg[t, 1]].tolist()
+        keys = [binning.order_key(rec[r, 9], r) for r in lst]
+        assert keys == sorted(keys) and len(set(lst)) == len(lst), t
+        got = set(lst)
+        s_t, m_t = sure.get(t, set()), maybe.get(t, set())
+        assert s_t <= got <= (s_t | m_t), (t, len(s_t - got), len(got - s_t - m_t))
+
+
 def test_bin_sort_overflow_flag_and_regrow(dass):
     scene, cams = _small_multicam(n=2000)
     from paper_2411_14847_gb300 import raster
