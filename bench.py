@@ -337,7 +337,7 @@ def serve_load(rates, seconds, seed=1005):
     out = {"scenes": [int(n) for n in sizes]}
     import gc
     for rate in rates:
-        srv = RenderServer(tile=32, batch=256, max_batch=16, n_streams=3)
+        srv = RenderServer(tile=32, batch=32, max_batch=16, n_streams=3)
         for i in range(8):
             srv.set_scene(i, versions[i][0])
         warm = [srv.submit(i % 8, c) for i, c in enumerate(synth.sphere_cameras(16, seed, 3.0, 5.0, res))]

@@ -219,7 +219,9 @@ int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, const das
  * < 1/255 is skipped; before adding a Gaussian, T (1 - alpha) < 1e-4 stops the pixel and
  * the Gaussian is not added. Writes image (planar), T_final[pixels] and n_last[pixels]
  * (sorted-pair position of the last added Gaussian, -1 if none). bg: host float[3] or NULL
- * (black). batch in {64,128,256}: Gaussians staged in shared memory per round. */
+ * (black). batch in {32, 64, 128, 256}: list entries each compositing warp (one 8 x 16 pixel block,
+ * 8 x 8 at 8-pixel tiles) examines and stages in shared memory per round; the result does not
+ * depend on it. */
 int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                     const dass_camera* cams /* host */, int n_cams, int tile, int batch,
                     const float* bg /* host, 3 */, float* image, float* T_final, int32_t* n_last,
@@ -238,16 +240,14 @@ int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const u
                      int32_t* n_last, uint64_t* work, void* stream);
 
 /* Reverse-order backward of dass_render_fwd. Recomputes alpha from the saved T_final and
- * n_last (T_j = T_{j+1} / (1 - alpha_j)); per Gaussian the 9 gradients are reduced across the
- * warp with shuffles, then per block in shared memory, then added to splat_grads[record]
- * with global atomics. splat_grads (n_records entries) is zeroed by this call first.
+ * n_last (T_j = T_{j+1} / (1 - alpha_j)); per Gaussian the 9 gradients of each 8 x 16 pixel block
+ * are reduced across the block's warp with shuffles and added to splat_grads[record] with global
+ * vector atomics. splat_grads (n_records entries) is zeroed by this call first.
  * full_grad (optional, device uint8 per Gaussian g = record % rec_stride; NULL = all): Gaussians
  * with full_grad[g] == 0 only receive splat_grads.mean2d (what the densification statistics
  * read), their other fields stay 0 -- e.g. the static Gaussians of the shift stage (Sec. 3.3),
  * whose parameters are not optimised; transmittance and colours are propagated identically.
- * The first call for a (tile, batch) on a device opts the kernel in to more than 48 KB of
- * shared memory per CTA (a host-side attribute): make that first call outside CUDA stream
- * capture (dass_step does this itself before it captures). */
+ * batch as in dass_render_fwd. */
 int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
                     const uint32_t* tile_ranges, const dass_camera* cams /* host */, int n_cams,
                     int tile, int batch, const float* bg /* host, 3 */, const float* T_final,

@@ -12,7 +12,7 @@ import torch
 from . import dass as D
 from .timestep import ShiftStage
 
-CANDIDATES = [(t, b) for t in (8, 16, 32) for b in (64, 128, 256)]
+CANDIDATES = [(t, b) for t in (8, 16, 32) for b in (32, 64, 128, 256)]
 
 
 def autotune(g, cams, targets, dyn_idx, offsets, candidates=CANDIDATES, iters=4, lambda_dssim=0.2):

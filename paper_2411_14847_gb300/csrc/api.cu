@@ -224,7 +224,7 @@ DASS_API int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_o
                            workspace_bytes, as_stream(stream));
 }
 
-bool dass::batch_ok(int b) { return b == 64 || b == 128 || b == 256; }
+bool dass::batch_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
 DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                              const dass_camera* cams, int n_cams, int tile, int batch, const float* bg, float* image,

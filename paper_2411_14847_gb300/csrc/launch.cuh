@@ -77,7 +77,7 @@ int spawn_launch(long long n, int deg, float* means, float* ls, float* quats, fl
                  cudaStream_t st);
 
 size_t scan_partials_bytes(long long len);
-bool batch_ok(int batch);   // Gaussians staged per compositing round: 64, 128 or 256
+bool batch_ok(int batch);   // list entries a compositing warp examines per round: 32, 64, 128 or 256
 void set_error_message(const char* msg);
 
 }  // namespace dass

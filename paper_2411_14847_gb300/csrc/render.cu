@@ -1,47 +1,19 @@
 // Forward and backward alpha compositing (App. A.1) over every tile of every camera in one
-// launch. A CTA covers a CT x CT part of a binning tile; each warp owns an 8 x 4*PPL block of
-// pixels and each lane PPL pixels of one column (rows y + 4k), handled as pixel pairs with the
-// packed FP32x2 arithmetic of sm_100+ (two-lane add/mul/fma that round like their scalar forms,
-// so the packed alpha is bit-identical to a scalar evaluation). The tile's depth-sorted
-// Gaussians are staged through shared memory in batches; after each batch is staged, every
-// warp compacts (ballot + prefix popcount, order preserved) the entries whose alpha >= 1/255
-// footprint ellipse reaches its own block of pixels, and composites only those. The backward
-// walks the lists in reverse from the last contributor, recomputing alpha and
-// T_j = T_{j+1}/(1-alpha_j) from the saved T_final, and reduces per-Gaussian gradients
-// warp-wide (shuffles), then block-wide (shared-memory atomics), then into global memory
-// (vector atomics).
-#include "common.cuh"
+// launch. Each CTA is one warp that owns an 8 x 4*PPL block of pixels of a binning tile; each lane
+// owns PPL pixels of one column (rows y + 4k), handled as pixel pairs with the packed FP32x2
+// arithmetic of sm_100+ (two-lane add/mul/fma that round like their scalar forms, so the packed
+// alpha is bit-identical to a scalar evaluation). The warp walks its tile's depth-sorted list in
+// rounds: the lanes test the round's entries against the block (the alpha >= 1/255 footprint
+// ellipse against the rectangle of the block's pixel centres), compact the hits in list order
+// (ballot + prefix popcount) into the warp's shared memory and composite only those. Warps of the
+// same tile never wait for each other. The backward walks the lists in reverse from the block's last
+// contributor, recomputing alpha and T_j = T_{j+1}/(1-alpha_j) from the saved T_final, reduces each
+// Gaussian's gradient across the warp with shuffles and adds it to global memory with vector atomics.
+#include "launch.cuh"
 
 namespace dass {
 
 namespace {
-
-// Staged form of a splat: NG float4 groups in structure-of-arrays shared memory. Every scalar
-// of the per-pixel math is stored twice, so one shared load yields the operand pair of the
-// packed arithmetic without register moves:
-//   P0 = (-u, -u, -v, -v)     P1 = (a', a', b2', b2')     P2 = (c', c', o, o)
-//   P3 = (r, r, g, g)         P4 = (blue, blue, 0, 0)
-// with a' = a kNegHalfLog2e, b2' = 2 b kNegHalfLog2e, c' = c kNegHalfLog2e (see splat_gauss);
-// F = (a, b, c, k2) is the footprint ellipse d^T conic d <= k2 (k2 < 0: no footprint).
-// NEG (forward only): o, r, g and blue are staged negated, so that the forward works with -alpha
-// and forms T - alpha T with one packed FMA (the negations are exact: alpha is unchanged).
-template <int NG, int BATCH, bool NEG = false>
-__device__ __forceinline__ void stage_splat(const dass_splat* __restrict__ splats, uint32_t rec, int i,
-                                            float4 (&sP)[NG][BATCH], float4 (&sF)[BATCH]) {
-    const float4* sp = reinterpret_cast<const float4*>(splats + rec);
-    const float4 s0 = __ldg(sp);        // u, v, a, b
-    const float4 s1 = __ldg(sp + 1);    // c, o, r, g
-    const float bl = __ldg(reinterpret_cast<const float*>(sp + 2));
-    const float ap = __fmul_rn(s0.z, kNegHalfLog2e), b2p = __fmul_rn(2.f * s0.w, kNegHalfLog2e),
-                cp = __fmul_rn(s1.x, kNegHalfLog2e);
-    const float sg = NEG ? -1.f : 1.f;
-    sP[0][i] = make_float4(-s0.x, -s0.x, -s0.y, -s0.y);
-    sP[1][i] = make_float4(ap, ap, b2p, b2p);
-    sP[2][i] = make_float4(cp, cp, sg * s1.y, sg * s1.y);
-    sP[3][i] = make_float4(sg * s1.z, sg * s1.z, sg * s1.w, sg * s1.w);
-    sP[4][i] = make_float4(sg * bl, sg * bl, 0.f, 0.f);
-    sF[i] = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
-}
 
 __device__ __forceinline__ float2 lo2(const float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 v) { return make_float2(v.z, v.w); }
@@ -56,28 +28,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Compact the indices [0, cnt) of the staged batch whose footprint reaches this warp's 8 x BH
-// block into list[] (ascending), only indices <= jmax. Returns the count (warp-uniform).
-template <int BH, int BATCH>
-__device__ __forceinline__ int warp_compact(const float4* __restrict__ sP0, const float4* __restrict__ sF, int cnt,
-                                            int jmax, float bx, float by, unsigned short* list, int lane) {
-    int n = 0;
-    int lim = min(cnt, jmax + 1);
-    for (int j0 = 0; j0 < lim; j0 += 32) {
-        int j = j0 + lane;
-        bool hit = false;
-        if (j < lim) {
-            const float4 c = sP0[j];
-            hit = footprint_reaches_rect(c.x, c.z, sF[j], bx, by, 7.f, (float)(BH - 1));
-        }
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[n + __popc(m & lanemask_lt())] = (unsigned short)j;
-        n += __popc(m);
-    }
-    __syncwarp();
-    return n;
 }
 
 // Forward state of a lane's pixel pair (rows y and y + 4 of one column).
@@ -139,40 +89,33 @@ __device__ __forceinline__ void pix_fwd_store(float T, float C0, float C1, float
     n_last[cam.pix_base + pix] = last;
 }
 
-// One CTA per CT x CT part of a tile with CT*CT/PPL threads: warp w owns the 8 x 4*PPL block
-// (w % (CT/8), w / (CT/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, as PPL/2
-// packed pixel pairs. COUNT = true is a separate instantiation used only to measure the work of a
-// render (pairs evaluated, pairs added, list prefixes); the timed kernels are the COUNT = false
-// instantiations.
-template <int TILE, int BATCH, bool COUNT, int CT = TILE, int PPL = 2>
-__global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_splat* __restrict__ splats,
-                                                                     const uint32_t* __restrict__ pair_rec,
-                                                                     const uint32_t* __restrict__ ranges,
-                                                                     CamTable ct, float3 bg,
-                                                                     float* __restrict__ image,
-                                                                     float* __restrict__ T_final,
-                                                                     int* __restrict__ n_last,
-                                                                     unsigned long long* __restrict__ work,
-                                                                     const uint8_t* __restrict__ full_grad,
-                                                                     long long rec_stride) {
-    constexpr int NT = CT * CT / PPL;
-    constexpr int NW = NT / 32;
-    constexpr int WX = CT / 8;
+// Forward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile (blockIdx.x = tile * WPT
+// + block). The warp walks the tile's list in rounds of BATCH entries: lane i reads entries i,
+// i + 32, ... of the round, tests whether each footprint reaches the block and stages the entries
+// that do at their compacted slots (list order) in the warp's shared memory; the warp then
+// composites the round's compacted entries. Warps never wait for each other, a warp whose pixels
+// are all done exits at once, and the hardware gives its slot to the next block.
+template <int TILE, int BATCH, bool COUNT, int PPL = 4>
+__global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_splat* __restrict__ splats,
+                                                            const uint32_t* __restrict__ pair_rec,
+                                                            const uint32_t* __restrict__ ranges, CamTable ct,
+                                                            float3 bg, float* __restrict__ image,
+                                                            float* __restrict__ T_final, int* __restrict__ n_last,
+                                                            unsigned long long* __restrict__ work,
+                                                            const uint8_t* __restrict__ full_grad,
+                                                            long long rec_stride) {
     constexpr int BH = 4 * PPL;
-    constexpr int NP = PPL / 2;       // pixel pairs per lane
-    constexpr int S = TILE / CT;      // CTAs per tile side
-    static_assert(BH <= CT && PPL % 2 == 0, "warp block taller than the CTA tile, or odd pixels per lane");
+    constexpr int WX = TILE / 8, WY = TILE / BH, WPT = WX * WY;
+    constexpr int NP = PPL / 2;
+    static_assert(TILE % BH == 0 && BATCH % 32 == 0, "block taller than the tile, or a partial round");
     __shared__ float4 sP[5][BATCH];
-    __shared__ float4 sF[BATCH];
-    __shared__ unsigned short sList[NW][BATCH];
+    __shared__ int sPos[BATCH];
     __shared__ uint8_t sFullC[COUNT ? BATCH : 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile_id = blockIdx.x / (S * S);
-    const int sub = blockIdx.x % (S * S);
+    const int lane = threadIdx.x;
+    const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
-    const int tx0 = (local % cam.tiles_x) * TILE + (sub % S) * CT, ty0 = (local / cam.tiles_x) * TILE + (sub / S) * CT;
-    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * BH;
+    const int bxi = (local % cam.tiles_x) * TILE + (wb % WX) * 8, byi = (local / cam.tiles_x) * TILE + (wb / WX) * BH;
     const int px = bxi + (lane & 7);
     const int py = byi + (lane >> 3);
     const float bx = (float)bxi, by = (float)byi;
@@ -197,30 +140,54 @@ __global__ void __launch_bounds__(CT* CT / PPL) render_fwd_kernel(const dass_spl
         return d;
     };
     for (uint32_t base = start; base < end; base += BATCH) {
-        if (__syncthreads_count(all_done()) == NT) break;
-        const int cnt = min((uint32_t)BATCH, end - base);
-        for (int i = tid; i < cnt; i += NT) {
-            const uint32_t rec = pair_rec[base + i];
-            stage_splat<5, BATCH, true>(splats, rec, i, sP, sF);
-            if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
+        if (__all_sync(0xffffffffu, all_done())) break;
+        int nl = 0;
+#pragma unroll
+        for (int r = 0; r < BATCH / 32; ++r) {
+            const uint32_t j = base + 32 * r + lane;
+            bool hit = false;
+            float4 s0, s1;
+            float bl = 0.f;
+            uint32_t rec = 0;
+            if (j < end) {
+                rec = pair_rec[j];
+                const float4* sp = reinterpret_cast<const float4*>(splats + rec);
+                s0 = __ldg(sp);        // u, v, a, b
+                s1 = __ldg(sp + 1);    // c, o, r, g
+                bl = __ldg(reinterpret_cast<const float*>(sp + 2));
+                const float4 F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
+                hit = footprint_reaches_rect(-s0.x, -s0.y, F, bx, by, 7.f, (float)(BH - 1));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int i = nl + __popc(m & lanemask_lt());
+                const float ap = __fmul_rn(s0.z, kNegHalfLog2e), b2p = __fmul_rn(2.f * s0.w, kNegHalfLog2e),
+                            cp = __fmul_rn(s1.x, kNegHalfLog2e);
+                sP[0][i] = make_float4(-s0.x, -s0.x, -s0.y, -s0.y);
+                sP[1][i] = make_float4(ap, ap, b2p, b2p);
+                sP[2][i] = make_float4(cp, cp, -s1.y, -s1.y);
+                sP[3][i] = make_float4(-s1.z, -s1.z, -s1.w, -s1.w);
+                sP[4][i] = make_float4(-bl, -bl, 0.f, 0.f);
+                sPos[i] = (int)j;
+                if (COUNT) sFullC[i] = full_grad ? full_grad[rec % (unsigned long long)rec_stride] : (uint8_t)1;
+            }
+            nl += __popc(m);
         }
-        __syncthreads();
-        if (__all_sync(0xffffffffu, all_done())) continue;
-        const int nl = warp_compact<BH, BATCH>(sP[0], sF, cnt, BATCH, bx, by, sList[warp], lane);
-#pragma unroll 8
+        __syncwarp();
+#pragma unroll 4
         for (int t = 0; t < nl; ++t) {
-            // warp-uniform early exit, tested every 4 entries (pixels that are done blend alpha = 0)
-            if ((t & 3) == 0 && __all_sync(0xffffffffu, all_done())) break;
-            const int j = sList[warp][t];
-            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j];
-            const float2 nblue = lo2(sP[4][j]);
+            if ((t & 3) == 3 && __all_sync(0xffffffffu, all_done())) break;
+            const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t];
+            const float2 nblue = lo2(sP[4][t]);
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             float2 A, B;
             splat_column2(lo2(P1), hi2(P1), dx, A, B);
-            const bool full = COUNT ? sFullC[COUNT ? j : 0] != 0 : false;
+            const bool full = COUNT ? sFullC[COUNT ? t : 0] != 0 : false;
+            const int pos = sPos[t];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], (int)(base + j), A, B, P0, P2, P3, nblue, full);
+            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], pos, A, B, P0, P2, P3, nblue, full);
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -397,57 +364,37 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     return val0 || val1;
 }
 
-// Dynamic shared-memory layout of the backward CTA (byte offsets; every part 16-byte aligned).
-template <int BATCH, int NT, int NP>
-struct BwdSmem {
-    static constexpr int kP = 0;                                  // float4 [5][BATCH] staged splats
-    static constexpr int kF = kP + 5 * BATCH * 16;                // float4 [BATCH] footprints
-    static constexpr int kGp = kF + BATCH * 16;                   // float2 [NP][3][NT] dL/dC of the lanes' pixels
-    static constexpr int kG = kGp + NP * 3 * NT * 8;              // float [BATCH][9] block-reduced gradients
-    static constexpr int kRec = kG + ((BATCH * 9 * 4 + 15) / 16) * 16;   // uint32 [BATCH] record indices
-    static constexpr int kList = kRec + BATCH * 4;                // ushort [NT/32][BATCH] per-warp lists
-    static constexpr int kFull = kList + ((NT / 32) * BATCH * 2 + 15) / 16 * 16;   // uint8 [BATCH]
-    static constexpr int kBytes = kFull + ((BATCH + 15) / 16) * 16;
-};
-
-// One CTA per CT x CT part of a tile with CT*CT/PPL threads: warp w owns the 8 x 4*PPL block
-// (w % (CT/8), w / (CT/8)) and each lane the PPL pixels (x, y + 4k), k < PPL, of it, so the
-// per-Gaussian warp reduction is shared by 32*PPL pixels. full_grad (optional, per Gaussian of
-// the record stride) selects Gaussians whose complete splat gradient is wanted; the others only
-// receive dL/d(mean2D). With 4 pixels per lane the kernel is held to 64 registers (no spills) so
-// that four 256-thread CTAs share an SM (the upstream gradients live in shared memory for that
-// reason): warps waiting at a CTA's batch barrier leave issue slots to the other CTAs. Measured
-// on the 300k x 20-view backward: 3 CTAs per SM (80 registers) 5.31 ms, 4 CTAs 5.06 ms.
-template <int TILE, int BATCH, int PPL, int CT = TILE>
-__global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_kernel(
+// Backward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile. The warp walks the
+// tile's list in reverse from its pixels' last contributor, in rounds of BATCH entries: the lanes
+// read the round's entries (ascending), test each footprint against the block and stage the entries
+// that reach it (compacted, in list order) in the warp's shared memory; the warp then runs the
+// reverse pair steps over the round's entries from the last one down, reduces each Gaussian's
+// gradient across the warp with shuffles and adds it to splat_grads[record] with vector atomics (one
+// float2 for a mean-only Gaussian: dL/du = a X + b Y, dL/dv = b X + c Y of the block sums X, Y). The
+// upstream gradients of the lanes' pixels live in shared memory (the kernel is held to 64 registers
+// for 32 resident warps per SM).
+template <int TILE, int BATCH, int PPL = 4>
+__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
     dass_splat_grad* __restrict__ gsplat) {
-    constexpr int NT = CT * CT / PPL;
-    constexpr int NW = NT / 32;
-    constexpr int WX = CT / 8;
     constexpr int BH = 4 * PPL;
-    constexpr int NP = PPL / 2;       // pixel pairs per lane
-    constexpr int S = TILE / CT;      // CTAs per tile side
-    static_assert(BH <= CT && PPL % 2 == 0, "warp block taller than the CTA tile, or odd pixels per lane");
-    using L = BwdSmem<BATCH, NT, NP>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    auto& sP = *reinterpret_cast<float4(*)[5][BATCH]>(smem + L::kP);
-    auto& sF = *reinterpret_cast<float4(*)[BATCH]>(smem + L::kF);
-    float2* sGp = reinterpret_cast<float2*>(smem + L::kGp);        // [NP][3][NT] upstream gradients
-    auto& sG = *reinterpret_cast<float(*)[BATCH][9]>(smem + L::kG);
-    uint32_t* sRec = reinterpret_cast<uint32_t*>(smem + L::kRec);
-    auto& sList = *reinterpret_cast<unsigned short(*)[NW][BATCH]>(smem + L::kList);
-    uint8_t* sFull = smem + L::kFull;
-    __shared__ int s_maxlast;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile_id = blockIdx.x / (S * S);
-    const int sub = blockIdx.x % (S * S);
+    constexpr int WX = TILE / 8, WY = TILE / BH, WPT = WX * WY;
+    constexpr int NP = PPL / 2;
+    constexpr int NT = 32;
+    static_assert(TILE % BH == 0 && BATCH % 32 == 0, "block taller than the tile, or a partial round");
+    __shared__ float4 sP[5][BATCH];
+    __shared__ float4 sF[BATCH];
+    __shared__ uint32_t sRec[BATCH];
+    __shared__ int sPos[BATCH];
+    __shared__ uint8_t sFull[BATCH];
+    __shared__ float2 sGp[NP * 3 * NT];      // upstream gradients of the lanes' pixel pairs
+    const int lane = threadIdx.x;
+    const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
-    const int tx0 = (local % cam.tiles_x) * TILE + (sub % S) * CT, ty0 = (local / cam.tiles_x) * TILE + (sub / S) * CT;
-    const int bxi = tx0 + (warp % WX) * 8, byi = ty0 + (warp / WX) * BH;
+    const int bxi = (local % cam.tiles_x) * TILE + (wb % WX) * 8, byi = (local / cam.tiles_x) * TILE + (wb / WX) * BH;
     const int px = bxi + (lane & 7);
     const int py = byi + (lane >> 3);
     const float bx = (float)bxi, by = (float)byi;
@@ -461,34 +408,52 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
     int mylast = -1;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        pix_bwd_load2<NT>(pp[k], sGp + 3 * NT * k + tid, cam, px, py + 8 * k, bg, T_final, n_last, dL_dimage);
+        pix_bwd_load2<NT>(pp[k], sGp + 3 * NT * k + lane, cam, px, py + 8 * k, bg, T_final, n_last, dL_dimage);
         mylast = max(mylast, max(pp[k].last0, pp[k].last1));
     }
-    if (tid == 0) s_maxlast = -1;
-    __syncthreads();
     const int wlast = __reduce_max_sync(0xffffffffu, mylast);
-    if (lane == 0 && wlast >= 0) atomicMax(&s_maxlast, wlast);
-    __syncthreads();
-    const long long endpos = (long long)s_maxlast + 1;
-    for (long long hi = endpos; hi > (long long)start; hi -= BATCH) {
+    __syncwarp();
+    for (long long hi = (long long)wlast + 1; hi > (long long)start; hi -= BATCH) {
         const long long lo = hi - BATCH > (long long)start ? hi - BATCH : (long long)start;
-        const int cnt = (int)(hi - lo);
-        __syncthreads();
-        for (int i = tid; i < cnt; i += NT) {
-            const uint32_t rec = pair_rec[lo + i];
-            sRec[i] = rec;
-            sFull[i] = full_grad ? full_grad[rec % stride] : (uint8_t)1;
-            stage_splat<5, BATCH>(splats, rec, i, sP, sF);
+        int nl = 0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) sG[i][k] = 0.f;
+        for (int r = 0; r < BATCH / 32; ++r) {
+            const long long pos = lo + 32 * r + lane;
+            bool hit = false;
+            float4 s0, s1;
+            float bl = 0.f;
+            uint32_t rec = 0;
+            if (pos < hi) {
+                rec = pair_rec[pos];
+                const float4* sp = reinterpret_cast<const float4*>(splats + rec);
+                s0 = __ldg(sp);        // u, v, a, b
+                s1 = __ldg(sp + 1);    // c, o, r, g
+                bl = __ldg(reinterpret_cast<const float*>(sp + 2));
+                const float4 F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
+                hit = footprint_reaches_rect(-s0.x, -s0.y, F, bx, by, 7.f, (float)(BH - 1));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int i = nl + __popc(m & lanemask_lt());
+                const float ap = __fmul_rn(s0.z, kNegHalfLog2e), b2p = __fmul_rn(2.f * s0.w, kNegHalfLog2e),
+                            cp = __fmul_rn(s1.x, kNegHalfLog2e);
+                sP[0][i] = make_float4(-s0.x, -s0.x, -s0.y, -s0.y);
+                sP[1][i] = make_float4(ap, ap, b2p, b2p);
+                sP[2][i] = make_float4(cp, cp, s1.y, s1.y);
+                sP[3][i] = make_float4(s1.z, s1.z, s1.w, s1.w);
+                sP[4][i] = make_float4(bl, bl, 0.f, 0.f);
+                sF[i] = make_float4(s0.z, s0.w, s1.x, 0.f);
+                sRec[i] = rec;
+                sPos[i] = (int)pos;
+                sFull[i] = full_grad ? full_grad[rec % stride] : (uint8_t)1;
+            }
+            nl += __popc(m);
         }
-        __syncthreads();
-        const int jmax = (int)((long long)wlast - lo);   // entries beyond every lane's last are skipped
-        const int nl = jmax >= 0 ? warp_compact<BH, BATCH>(sP[0], sF, cnt, jmax, bx, by, sList[warp], lane) : 0;
+        __syncwarp();
         // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm); returns whether a
         // pixel of this lane took part
         auto mean_steps = [&](int j, float2* vm) {
-            const int pos = (int)(lo + j);
+            const int p = sPos[j];
             const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
             const float2 dx = __fadd2_rn(fx2, lo2(P0));
             float2 A, B;
@@ -496,17 +461,16 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
             bool c = false;
 #pragma unroll
             for (int k = 0; k < NP; ++k)
-                c |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4, vm,
+                c |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4, vm,
                                               nullptr);
             return c;
         };
         for (int t = nl - 1; t >= 0; --t) {
-            const int j = sList[warp][t];
             bool contrib = false;
             float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            if (sFull[j]) {          // warp-uniform: the same Gaussian for every lane
-                const int pos = (int)(lo + j);
-                const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
+            if (sFull[t]) {          // warp-uniform: the same Gaussian for every lane
+                const int p = sPos[t];
+                const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
                 const float2 dx = __fadd2_rn(fx2, lo2(P0));
                 float2 A, B;
                 splat_column2(lo2(P1), hi2(P1), dx, A, B);
@@ -515,100 +479,80 @@ __global__ void __launch_bounds__(CT* CT / PPL, PPL == 4 ? 4 : 1) render_bwd_ker
                 for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + tid, pos, dx, A, B, P0, P2, P3, P4,
+                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4,
                                                        vm, vf);
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float X = dx.x * (vm[0].x + vm[0].y), Y = vm[1].x + vm[1].y;
                     float r[8] = {X, Y, dx.x * X, dx.x * Y, vf[2].x + vf[2].y, vf[3].x + vf[3].y,
                                   vf[4].x + vf[4].y, vf[5].x + vf[5].y};
-                    float s = warp_reduce8(r, lane);
+                    const float sm = warp_reduce8(r, lane) * gscale;
                     const float e = warp_sum(vf[6].x + vf[6].y);
-                    // lanes 0 and 4 hold the moments X and Y (the conic is applied at the flush)
-                    if ((lane & 3) == 0) atomicAdd(&sG[j][gidx], s * gscale);
-                    if (lane == 1) atomicAdd(&sG[j][8], e);
+                    // lane 4 g (g < 8) holds reduced value g: X, Y, dL/da, dL/db, dL/dc, dL/do, dL/dr, dL/dg
+                    const float Xs = __shfl_sync(0xffffffffu, sm, 0), Ys = __shfl_sync(0xffffffffu, sm, 4);
+                    const float v2 = __shfl_sync(0xffffffffu, sm, 8), v3 = __shfl_sync(0xffffffffu, sm, 12);
+                    const float v4 = __shfl_sync(0xffffffffu, sm, 16), v5 = __shfl_sync(0xffffffffu, sm, 20);
+                    const float v6 = __shfl_sync(0xffffffffu, sm, 24), v7 = __shfl_sync(0xffffffffu, sm, 28);
+                    if (lane == 0) {
+                        const float4 F = sF[t];
+                        float4* dst = reinterpret_cast<float4*>(gsplat + sRec[t]);
+                        atomicAdd(dst, make_float4(F.x * Xs + F.y * Ys, F.y * Xs + F.z * Ys, v2, v3));
+                        atomicAdd(dst + 1, make_float4(v4, v5, v6, v7));
+                        atomicAdd(reinterpret_cast<float*>(dst + 2), e);
+                    }
                 }
             } else {
                 // mean-only entries are taken two at a time when the next one is mean-only too
                 // (warp-uniform), so that one 4-value reduction serves both
-                const int j2 = t >= 1 ? sList[warp][t - 1] : 0;
-                const bool two = t >= 1 && !sFull[j2];
-                contrib = mean_steps(j, vm);
+                const bool two = t >= 1 && !sFull[t - 1];
+                contrib = mean_steps(t, vm);
                 float2 vm2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                if (two) {
-                    contrib |= mean_steps(j2, vm2);
-                    --t;
-                }
+                if (two) contrib |= mean_steps(t - 1, vm2);
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     if (two) {
                         const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
                                                      vm2[1].x + vm2[1].y, lane);
-                        // lanes 0, 8 hold X, Y of j; lanes 16, 24 those of j2 (conic at the flush)
-                        if ((lane & 7) == 0) atomicAdd(&sG[(lane & 16) ? j2 : j][(lane >> 3) & 1], r);
+                        // lanes 0, 8 hold X, Y of entry t; lanes 16, 24 those of entry t - 1
+                        const float Yp = __shfl_down_sync(0xffffffffu, r, 8);
+                        if ((lane & 15) == 0) {
+                            const int e = (lane & 16) ? t - 1 : t;
+                            const float4 F = sF[e];
+                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
+                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                        }
                     } else {
                         const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                        // lane 0 holds X, lane 16 holds Y (the conic is applied at the flush)
-                        if ((lane & 15) == 0) atomicAdd(&sG[j][lane >> 4], r);
+                        // lane 0 holds X, lane 16 holds Y
+                        const float Yp = __shfl_sync(0xffffffffu, r, 16);
+                        if (lane == 0) {
+                            const float4 F = sF[t];
+                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[t]),
+                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                        }
                     }
                 }
+                if (two) --t;
             }
         }
-        __syncthreads();
-        for (int i = tid; i < cnt; i += NT) {
-            // block sums X = sum dpow dx, Y = sum dpow dy -> dL/du = a X + b Y, dL/dv = b X + c Y
-            const float4 F = sF[i];
-            const float X = sG[i][0], Y = sG[i][1];
-            float4 a = make_float4(F.x * X + F.y * Y, F.y * X + F.z * Y, sG[i][2], sG[i][3]);
-            float4 b = make_float4(sG[i][4], sG[i][5], sG[i][6], sG[i][7]);
-            float c = sG[i][8];
-            float4* dst = reinterpret_cast<float4*>(gsplat + sRec[i]);
-            if ((a.x != 0.f) | (a.y != 0.f) | (a.z != 0.f) | (a.w != 0.f)) atomicAdd(dst, a);
-            if ((b.x != 0.f) | (b.y != 0.f) | (b.z != 0.f) | (b.w != 0.f)) atomicAdd(dst + 1, b);
-            if (c != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 2), c);
-        }
+        __syncwarp();
     }
 }
-
-// CTA side and pixels per lane of the compositing kernels for a binning tile: a tile's list can
-// be composited by (TILE/CT)^2 independent CTAs, each covering a CT x CT part of the tile, and a
-// lane owns PPL pixels of a column. Measured on the 300k x 20-view workload: 32-pixel bins are
-// composited fastest by whole-tile CTAs with 4 pixels per lane (8 x 16 warp blocks) in both
-// passes; 16 x 16 forward CTAs were best with 2 pixels per lane (2.76 vs 2.69 ms).
-template <int TILE>
-constexpr int fwd_cta() { return TILE; }
-template <int TILE>
-constexpr int fwd_ppl() { return TILE == 32 ? 4 : 2; }
-template <int TILE>
-constexpr int bwd_cta() { return TILE; }
 
 template <int TILE, int BATCH>
 int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                float* img, float* tf, int* nl, unsigned long long* work, const uint8_t* full, long long stride,
                cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
-    constexpr int CT = fwd_cta<TILE>();
-    constexpr int PPL = fwd_ppl<TILE>();
-    constexpr int NB = (TILE / CT) * (TILE / CT);
+    constexpr int PPL = TILE == 8 ? 2 : 4;
+    constexpr int WPT = (TILE / 8) * (TILE / (4 * PPL));
+    const long long grid = (long long)ct.tiles_total * WPT;
     if (work)
-        render_fwd_kernel<TILE, BATCH, true, CT, PPL><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(
-            sp, pr, rg, ct, bg, img, tf, nl, work, full, stride);
+        render_fwd_warp_kernel<TILE, BATCH, true, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl, work,
+                                                                              full, stride);
     else
-        render_fwd_kernel<TILE, BATCH, false, CT, PPL><<<ct.tiles_total * NB, CT * CT / PPL, 0, st>>>(
-            sp, pr, rg, ct, bg, img, tf, nl, nullptr, nullptr, 1);
+        render_fwd_warp_kernel<TILE, BATCH, false, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
+                                                                               nullptr, nullptr, 1);
     count_launch();
-    return check_launch("render_fwd_kernel");
-}
-
-// Pixels per lane of the backward (measured on the 300k x 20-view workload): 2 for 8- and
-// 16-pixel tiles (8 x 8 warp blocks), 4 for 32-pixel tiles (8 x 16).
-template <int TILE>
-constexpr int bwd_ppl() { return TILE == 32 ? 4 : 2; }
-
-template <int TILE, int BATCH>
-int prepare_bwd() {
-    constexpr int PPL = bwd_ppl<TILE>();
-    constexpr int CT = bwd_cta<TILE>();
-    constexpr int bytes = BwdSmem<BATCH, CT * CT / PPL, PPL / 2>::kBytes;
-    return allow_dynamic_smem(reinterpret_cast<const void*>(render_bwd_kernel<TILE, BATCH, PPL, CT>), bytes);
+    return check_launch("render_fwd_warp_kernel");
 }
 
 template <int TILE, int BATCH>
@@ -616,28 +560,28 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
                const float* tf, const int* nl, const float* dimg, const uint8_t* full, long long stride,
                dass_splat_grad* gs, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
-    constexpr int PPL = bwd_ppl<TILE>();
-    constexpr int CT = bwd_cta<TILE>();
-    constexpr int NB = (TILE / CT) * (TILE / CT);
-    constexpr int NT = CT * CT / PPL;
-    constexpr int bytes = BwdSmem<BATCH, NT, PPL / 2>::kBytes;
-    if (int rc = prepare_bwd<TILE, BATCH>()) return rc;
-    render_bwd_kernel<TILE, BATCH, PPL, CT><<<ct.tiles_total * NB, NT, bytes, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
-                                                                                   full, stride, gs);
+    constexpr int PPL = TILE == 8 ? 2 : 4;
+    constexpr int WPT = (TILE / 8) * (TILE / (4 * PPL));
+    const long long grid = (long long)ct.tiles_total * WPT;
+    render_bwd_warp_kernel<TILE, BATCH, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg, full, stride,
+                                                                      gs);
     count_launch();
-    return check_launch("render_bwd_kernel");
+    return check_launch("render_bwd_warp_kernel");
 }
 
 }  // namespace
 
 #define DASS_DISPATCH(FN, ...)                                                        \
     switch (ct.tile * 1000 + batch) {                                                 \
+        case 8032: return FN<8, 32>(__VA_ARGS__);                                     \
         case 8064: return FN<8, 64>(__VA_ARGS__);                                     \
         case 8128: return FN<8, 128>(__VA_ARGS__);                                    \
         case 8256: return FN<8, 256>(__VA_ARGS__);                                    \
+        case 16032: return FN<16, 32>(__VA_ARGS__);                                   \
         case 16064: return FN<16, 64>(__VA_ARGS__);                                   \
         case 16128: return FN<16, 128>(__VA_ARGS__);                                  \
         case 16256: return FN<16, 256>(__VA_ARGS__);                                  \
+        case 32032: return FN<32, 32>(__VA_ARGS__);                                   \
         case 32064: return FN<32, 64>(__VA_ARGS__);                                   \
         case 32128: return FN<32, 128>(__VA_ARGS__);                                  \
         case 32256: return FN<32, 256>(__VA_ARGS__);                                  \
@@ -658,10 +602,10 @@ int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                   gsplat, st)
 }
 
-// Kernel attributes that must be set outside stream capture (dynamic shared memory above 48 KB).
+// Checks a (tile, batch) shape before a stage is captured. The compositing kernels use static shared
+// memory only (at most 48 KB), so no kernel attribute has to be set outside capture.
 int render_prepare(int tile, int batch) {
-    struct { int tile; } ct{tile};
-    DASS_DISPATCH(prepare_bwd)
+    return ((tile == 8 || tile == 16 || tile == 32) && batch_ok(batch)) ? DASS_OK : DASS_ERR_INVALID_ARG;
 }
 
 }  // namespace dass
