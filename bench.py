@@ -479,17 +479,21 @@ def main():
     n_eval, n_add, n_bwd, n_pix, n_add_dyn = (int(v) for v in work.tolist())
     s_ = torch.cuda.current_stream()
 
-    def timed(fn, reps=10):
+    def timed(fn, reps=10, rounds=3):
+        """Median over `rounds` of the mean launch time of `reps` back-to-back launches (CUDA events)."""
         for _ in range(2):
             fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(s_)
-        for _ in range(reps):
-            fn()
-        b.record(s_)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        per = []
+        for _ in range(rounds):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(s_)
+            for _ in range(reps):
+                fn()
+            b.record(s_)
+            torch.cuda.synchronize()
+            per.append(a.elapsed_time(b) / reps)
+        return statistics.median(per)
 
     # backward first (render_fwd recomputes the same T_final/n_last, so inputs stay consistent)
     bwd_ms = timed(lambda: D.dass_render_bwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,

@@ -5,8 +5,8 @@ The oracle cannot render 27M pixels against 300k Gaussians in FP64, so it comput
 outputs one by one: colours and transmittance of seeded pixel samples, and the parameter
 gradients of a loss whose upstream gradient is non-zero only on those pixels (so every
 Gaussian's gradient comes from the sampled pixels alone, on both sides). The GPU runs the
-launch configuration of the benchmark (all cameras in one launch, tile 32 x batch 256 and
-16 x 256). The graph-captured stage driver is checked at full size against the same
+launch configuration of the benchmark (all cameras in one launch, tile 32 x batch 32, and
+16 x 64). The graph-captured stage driver is checked at full size against the same
 iteration composed from the individual entry points.
 """
 import numpy as np
@@ -19,8 +19,11 @@ from paper_2411_14847_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# sampled cameras of each workload: the ends and the middle of the arc; three of the ring's four
-SAMPLE = {"arc_300k_20x1352x1014": (0, 9, 19), "ring_100k_4x960x540": (0, 1, 3)}
+# cameras of each workload whose pixels are sampled: every camera for the forward; for the
+# gradients (an FP64 autodiff through the projection of every Gaussian per camera) five cameras
+# spread over the arc and every camera of the ring
+SAMPLE = {"arc_300k_20x1352x1014": tuple(range(20)), "ring_100k_4x960x540": (0, 1, 2, 3)}
+GRAD_CAMS = {"arc_300k_20x1352x1014": (0, 5, 10, 14, 19), "ring_100k_4x960x540": (0, 1, 2, 3)}
 PIX_PER_CAM = 48
 
 
@@ -52,13 +55,13 @@ def workload(request):
         ys = np.concatenate([ys, rng.integers(0, cam.height, PIX_PER_CAM // 2)]).astype(np.float64)
         keep = np.unique(ys * cam.width + xs, return_index=True)[1]
         samples.append((xs[keep], ys[keep]))
-    return scene, cams, dyn_idx, offsets, projs, samples, sample_cams
+    return scene, cams, dyn_idx, offsets, projs, samples, sample_cams, GRAD_CAMS[request.param]
 
 
-@pytest.mark.parametrize("tile,batch", [(32, 256), (16, 256)])
+@pytest.mark.parametrize("tile,batch", [(32, 32), (16, 64)])
 def test_fullsize_sampled_forward(dass, workload, tile, batch):
     from paper_2411_14847_gb300 import raster
-    scene, cams, _, _, projs, samples, sample_cams = workload
+    scene, cams, _, _, projs, samples, sample_cams, _ = workload
     fr = raster.Frame(cams, scene.n, tile=tile, batch=batch)
     imgs = fr.render(raster.to_device(scene.arrays()))
     tfs = fr.pixel_views(fr.T_final)
@@ -88,8 +91,10 @@ def test_fullsize_sampled_forward(dass, workload, tile, batch):
 
 def test_fullsize_sampled_gradients(dass, workload):
     from paper_2411_14847_gb300 import dass as D, raster
-    scene, cams, _, _, projs, samples, sample_cams = workload
-    fr = raster.Frame(cams, scene.n, tile=32, batch=256)
+    scene, cams, _, _, projs, all_samples, all_cams, grad_cams = workload
+    samples = [all_samples[all_cams.index(c)] for c in grad_cams]
+    sample_cams = grad_cams
+    fr = raster.Frame(cams, scene.n, tile=32, batch=32)
     g = raster.to_device(scene.arrays())
     fr.render(g)
     rng = np.random.default_rng(5)
@@ -124,21 +129,21 @@ def test_fullsize_graph_step_equals_composed_calls(dass, workload):
     of the individual entry points (loss and dynamic-offset gradients)."""
     from paper_2411_14847_gb300 import dass as D, raster
     from paper_2411_14847_gb300.timestep import ShiftStage
-    scene, cams, dyn_idx, offsets, _, _, _ = workload
+    scene, cams, dyn_idx, offsets, _, _, _, _ = workload
     g = raster.to_device(scene.arrays())
-    tfr = raster.Frame(cams, scene.n, tile=32, batch=256)
+    tfr = raster.Frame(cams, scene.n, tile=32, batch=32)
     tfr.render(raster.to_device(synth.perturbed(scene, 2003).arrays()))
     targets = tfr.image.clone()
     del tfr
     dyn = torch.as_tensor(dyn_idx, dtype=torch.int32, device="cuda")
     off = torch.as_tensor(offsets, device="cuda")
-    st = ShiftStage(g, cams, targets, dyn, off.clone(), tile=32, batch=256, lambda_dssim=0.2)
+    st = ShiftStage(g, cams, targets, dyn, off.clone(), tile=32, batch=32, lambda_dssim=0.2)
     st.run(1, D.STEP_BATCHED)
     # composed: shift -> render -> loss -> backward -> preprocess backward (dynamic rows) -> shift backward
     rm, rq = g["means"].clone(), g["quats"].clone()
     D.dass_shift(dyn, off, g["means"], g["quats"], rm, rq)
     g2 = dict(g, means=rm, quats=rq)
-    fr = raster.Frame(cams, scene.n, tile=32, batch=256)
+    fr = raster.Frame(cams, scene.n, tile=32, batch=32)
     fr.render(g2)
     dimg = torch.empty_like(fr.image)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
