@@ -189,6 +189,48 @@ int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_offsets /*
                          int64_t pair_capacity, uint32_t* tile_ranges, int64_t* counters, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/* Incremental binning for the stage iterations (Sec. 3.2-3.4). A stage trains only a subset of the
+ * Gaussians -- the dynamic rows in the shift stage (Sec. 3.3), the var rows in the inheritance and
+ * densification stages (Sec. 3.2, 3.4) -- so the records of every other row are the same at every
+ * iteration of the stage. dass_bin_sort_split bins and sorts those static records once;
+ * dass_bin_sort_merge then bins and sorts only the moving rows' records and merges them into the
+ * static per-tile lists. Its pair_rec, tile_ranges and counters equal those of dass_bin_sort over
+ * all records, pair for pair (both follow the key (tile, depth bits, record id)).
+ *
+ * Records are camera-major, n_rows per camera (record c * n_rows + row, as dass_preprocess writes
+ * them with rec_stride = n_rows). moving[n_rows] (device, nonzero = moving row). Outputs of
+ * the split (device, caller-owned, kept for the merges):
+ *   static_rec[pair_capacity], static_depth[pair_capacity]: record and depth key (float bits) of each
+ *     static pair in sorted order;
+ *   tile_start[tiles_total + 1]: first static position of each tile;
+ *   static_counters[3]: as dass_bin_sort's counters, for the static pairs;
+ *   moving_rec[n_cams * n_rows]: records of the moving rows, camera by camera, ascending;
+ *   n_moving_rec[1] (int64): their count;
+ *   moving_rows[n_rows] (int32) and n_moving_rows[1] (int64): the moving rows, ascending.
+ * Workspace: dass_bin_sort_split_workspace. DASS_ERR_INVALID_ARG for n_rows <= 0 or
+ * n_cams * n_rows >= 2^32 or pair_capacity >= 2^31. */
+int dass_bin_sort_split_workspace(int64_t n_rows, int n_cams, int64_t pair_capacity, size_t* bytes);
+int dass_bin_sort_split(const dass_splat* splats, int64_t n_rows, const dass_camera* cams /* host */, int n_cams,
+                        int tile, const uint8_t* moving, int64_t pair_capacity, uint32_t* static_rec,
+                        uint32_t* static_depth, uint32_t* tile_start, int64_t* static_counters,
+                        uint32_t* moving_rec, int64_t* n_moving_rec, int32_t* moving_rows,
+                        int64_t* n_moving_rows, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The merge: splats hold the current records of every row (the static rows' unchanged since the
+ * split); moving_capacity >= *n_moving_rec (host bound: n_cams times the number of moving rows;
+ * larger counts are cut to it). Outputs as dass_bin_sort: pair_rec[pair_capacity], tile_ranges[2 *
+ * tiles_total], counters[3] (counters[1] = 1 when the static and moving pairs together exceed
+ * pair_capacity; positions beyond it are dropped and the ranges clamped). Workspace:
+ * dass_bin_sort_merge_workspace. The call enqueues work only (graph-capturable). */
+int dass_bin_sort_merge_workspace(int64_t moving_capacity, int64_t pair_capacity, int32_t tiles_total,
+                                  size_t* bytes);
+int dass_bin_sort_merge(const dass_splat* splats, int64_t n_rows, const dass_camera* cams /* host */, int n_cams,
+                        int tile, const uint32_t* moving_rec, const int64_t* n_moving_rec,
+                        int64_t moving_capacity, const uint32_t* static_rec, const uint32_t* static_depth,
+                        const uint32_t* tile_start, const int64_t* static_counters, uint32_t* pair_rec,
+                        int64_t pair_capacity, uint32_t* tile_ranges, int64_t* counters, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
 /* Size of the static device scratch array used by dass_bin_sort_static (64 MiB). */
 #define DASS_BIN_SORT_STATIC_BYTES (64ull << 20)
 
@@ -546,7 +588,13 @@ int dass_step_workspace(const dass_step_desc* d, size_t* bytes);
  * n_iters times; DASS_STEP_PLAIN launches per camera without a graph. With lambda_dssim > 0 the
  * call first computes the targets' SSIM window statistics into the workspace once
  * (dass_loss_target_stats) and every iteration's loss reads them (dass_loss_cached).
- * render_means/quats
+ * In DASS_STEP_BATCHED mode with n_dyn <= n / 2 the binning is incremental: only the dynamic rows
+ * move during the stage, so the other rows' pairs are binned and sorted once when the call starts
+ * (dass_bin_sort_split) and every iteration bins the dynamic rows' records and merges them in
+ * (dass_bin_sort_merge), with the same pair lists as a full dass_bin_sort; the workspace then also
+ * holds the static lists (2 * pair_capacity words and more: dass_step_workspace sizes it).
+ * The inheritance and densification stage drivers and dass_timestep do the same with their var
+ * rows as the moving set. render_means/quats
  * must hold a copy of means/quats before the first call. The call ends with one stream
  * synchronisation and a read of the pair-overflow flag: it returns DASS_ERR_CAPACITY if any
  * iteration overflowed pair_capacity (results of the stage are then unreliable). */

@@ -224,6 +224,65 @@ DASS_API int dass_bin_sort_packed(const dass_splat* splats, const int64_t* rec_o
                            workspace_bytes, as_stream(stream));
 }
 
+DASS_API int dass_bin_sort_split_workspace(int64_t n_rows, int n_cams, int64_t pair_capacity, size_t* bytes) {
+    if (n_rows <= 0 || n_cams <= 0 || pair_capacity < 1 || pair_capacity >= (1ll << 31) || !bytes)
+        return DASS_ERR_INVALID_ARG;
+    if ((long long)n_cams * n_rows >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    *bytes = bin_sort_split_workspace_bytes(n_rows, (long long)n_cams * n_rows, pair_capacity);
+    return DASS_OK;
+}
+
+DASS_API int dass_bin_sort_split(const dass_splat* splats, int64_t n_rows, const dass_camera* cams, int n_cams,
+                                 int tile, const uint8_t* moving, int64_t pair_capacity, uint32_t* static_rec,
+                                 uint32_t* static_depth, uint32_t* tile_start, int64_t* static_counters,
+                                 uint32_t* moving_rec, int64_t* n_moving_rec, int32_t* moving_rows,
+                                 int64_t* n_moving_rows, void* workspace, size_t workspace_bytes, void* stream) {
+    if (n_rows <= 0 || pair_capacity < 1 || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
+    if (!splats || !moving || !static_rec || !static_depth || !tile_start || !static_counters || !moving_rec ||
+        !n_moving_rec || !moving_rows || !n_moving_rows || !workspace)
+        return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, n_rows, &ct)) return DASS_ERR_INVALID_ARG;
+    if ((long long)n_cams * n_rows >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (workspace_bytes < bin_sort_split_workspace_bytes(n_rows, (long long)n_cams * n_rows, pair_capacity))
+        return DASS_ERR_OOM;
+    const StaticBins sb{static_rec, static_depth, tile_start, (long long*)static_counters, moving_rec,
+                        (long long*)n_moving_rec, moving_rows, (long long*)n_moving_rows};
+    return bin_sort_split_launch(splats, n_rows, ct, moving, pair_capacity, sb, workspace, workspace_bytes,
+                                 as_stream(stream));
+}
+
+DASS_API int dass_bin_sort_merge_workspace(int64_t moving_capacity, int64_t pair_capacity, int32_t tiles_total,
+                                           size_t* bytes) {
+    if (moving_capacity < 0 || moving_capacity >= (1ll << 32) || pair_capacity < 1 ||
+        pair_capacity >= (1ll << 31) || tiles_total < 0 || !bytes)
+        return DASS_ERR_INVALID_ARG;
+    *bytes = bin_sort_merge_workspace_bytes(moving_capacity, pair_capacity, tiles_total);
+    return DASS_OK;
+}
+
+DASS_API int dass_bin_sort_merge(const dass_splat* splats, int64_t n_rows, const dass_camera* cams, int n_cams,
+                                 int tile, const uint32_t* moving_rec, const int64_t* n_moving_rec,
+                                 int64_t moving_capacity, const uint32_t* static_rec, const uint32_t* static_depth,
+                                 const uint32_t* tile_start, const int64_t* static_counters, uint32_t* pair_rec,
+                                 int64_t pair_capacity, uint32_t* tile_ranges, int64_t* counters, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+    if (n_rows <= 0 || pair_capacity < 1 || pair_capacity >= (1ll << 31)) return DASS_ERR_INVALID_ARG;
+    if (moving_capacity < 0 || moving_capacity >= (1ll << 32)) return DASS_ERR_INVALID_ARG;
+    if (!splats || !moving_rec || !n_moving_rec || !static_rec || !static_depth || !tile_start || !static_counters ||
+        !pair_rec || !tile_ranges || !counters || !workspace)
+        return DASS_ERR_INVALID_ARG;
+    static thread_local CamTable ct;
+    if (!make_cam_table(cams, n_cams, tile, n_rows, &ct)) return DASS_ERR_INVALID_ARG;
+    if (workspace_bytes < bin_sort_merge_workspace_bytes(moving_capacity, pair_capacity, ct.tiles_total))
+        return DASS_ERR_OOM;
+    const StaticBins sb{const_cast<uint32_t*>(static_rec), const_cast<uint32_t*>(static_depth),
+                        const_cast<uint32_t*>(tile_start), (long long*)static_counters,
+                        const_cast<uint32_t*>(moving_rec), (long long*)n_moving_rec, nullptr, nullptr};
+    return bin_sort_merge_launch(splats, ct, sb, moving_capacity, pair_capacity, pair_rec, tile_ranges,
+                                 (long long*)counters, workspace, workspace_bytes, as_stream(stream));
+}
+
 bool dass::batch_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
 DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,

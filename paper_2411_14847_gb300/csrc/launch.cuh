@@ -22,6 +22,25 @@ int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* spla
 size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);
+// Incremental binning: the static part (the pairs of every row not flagged as moving, binned and sorted
+// once, with each pair's depth key and each tile's first position) and the moving rows' records.
+struct StaticBins {
+    uint32_t* rec;              // [cap] record of each static pair, in (tile, depth, record) order
+    uint32_t* depth;            // [cap] its depth key
+    uint32_t* start;            // [tiles_total + 1] first position of each tile
+    long long* counters;        // [3] as bin_sort_launch's
+    uint32_t* moving;           // [n_cams * n_rows] records of the moving rows, camera-major, ascending
+    long long* n_moving;        // [1] their count
+    int* rows;                  // [n_rows] moving rows, ascending
+    long long* n_rows_moving;   // [1]
+};
+size_t bin_sort_split_workspace_bytes(long long n_rows, long long n_rec, long long cap);
+int bin_sort_split_launch(const dass_splat* splats, long long n_rows, const CamTable& ct, const uint8_t* moving_rows,
+                          long long cap, const StaticBins& sb, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t bin_sort_merge_workspace_bytes(long long moving_cap, long long cap, int tiles_total);
+int bin_sort_merge_launch(const dass_splat* splats, const CamTable& ct, const StaticBins& sb, long long moving_cap,
+                          long long cap, uint32_t* pair_rec, uint32_t* tile_ranges, long long* counters, void* ws,
+                          size_t ws_bytes, cudaStream_t st);
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
                       unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,

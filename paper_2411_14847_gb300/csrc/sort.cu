@@ -6,7 +6,7 @@
 // Every kernel reads its item count from device memory and sizes its work from it, so the
 // whole sequence needs no host synchronisation and can be captured in a CUDA graph; grids are
 // launched for the capacity and surplus blocks exit at once.
-#include "common.cuh"
+#include "launch.cuh"
 
 namespace dass {
 
@@ -301,16 +301,20 @@ __device__ __forceinline__ bool record_footprint(const dass_splat* __restrict__ 
     return footprint_of(s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, f);
 }
 
-__global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long long n_rec, CamTable ct,
+// Item i is record list[i] (list null: record i), i < *n_dev. A record whose row (its index within
+// its camera's segment) is flagged in skip_rows emits no pairs, like a culled one.
+__global__ void bin_count_kernel(const dass_splat* __restrict__ splats, const long long* __restrict__ n_dev,
+                                 const uint32_t* __restrict__ list, const uint8_t* __restrict__ skip_rows, CamTable ct,
                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                  uint32_t* __restrict__ counts) {
-    long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (rec >= n_rec) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_dev) return;
+    const long long rec = list ? (long long)list[i] : i;
     const CamInfo& cam = ct.c[cam_of_record(ct, rec)];
     Footprint f;
     float depth;
     int cnt = 0;
-    if (record_footprint(splats, rec, f, depth)) {
+    if (!(skip_rows && skip_rows[rec - cam.rec_base]) && record_footprint(splats, rec, f, depth)) {
         int x0, x1, y0, y1;
         footprint_tiles(f, cam.tiles_x, cam.tiles_y, ct.tile, x0, x1, y0, y1);
         for (int y = y0; y <= y1; ++y) {
@@ -318,15 +322,21 @@ __global__ void bin_count_kernel(const dass_splat* __restrict__ splats, long lon
             if (footprint_row(f, y, ct.tile, cam.tiles_x, r0, r1)) cnt += r1 - r0 + 1;
         }
     }
-    keys[rec] = cnt > 0 ? __float_as_uint(depth) : 0xffffffffu;
-    vals[rec] = (uint32_t)rec;
-    counts[rec] = (uint32_t)cnt;
+    keys[i] = cnt > 0 ? __float_as_uint(depth) : 0xffffffffu;
+    vals[i] = (uint32_t)i;
+    counts[i] = (uint32_t)cnt;
 }
 
+// out[i] = counts[order[i]], and rec[i] = list[order[i]] when there is a list (else the record ids in
+// depth order are order itself): the pair counts and record ids in depth order.
 __global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
-                                     uint32_t* __restrict__ out, long long n) {
+                                     const uint32_t* __restrict__ list, uint32_t* __restrict__ out,
+                                     uint32_t* __restrict__ rec, const long long* __restrict__ n_dev) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = counts[order[i]];
+    if (i >= *n_dev) return;
+    const uint32_t o = order[i];
+    out[i] = counts[o];
+    if (list) rec[i] = list[o];
 }
 
 // Warp-wide inclusive sum of v (all lanes take part).
@@ -355,9 +365,9 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, int lane) {
 constexpr int kDupThreads = 256;
 constexpr int kDupUnits = 128;
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const dass_splat* __restrict__ splats, long long n_rec, CamTable ct, const uint32_t* __restrict__ order,
-    const uint32_t* __restrict__ offsets, const long long* total, long long capacity,
-    uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rec, long long* counters) {
+    const dass_splat* __restrict__ splats, const long long* __restrict__ n_dev, CamTable ct,
+    const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets, const long long* total,
+    long long capacity, uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_rec, long long* counters) {
     constexpr int NW = kDupThreads / 32;
     __shared__ Footprint s_f[kDupThreads];
     __shared__ int s_y0[kDupThreads];
@@ -368,6 +378,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long m = *total;
+    const long long n_rec = *n_dev;
     if (k == 0) {
         counters[0] = m;
         counters[1] = m > capacity ? 1 : 0;
@@ -496,6 +507,179 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const lon
 
 __global__ void set_len_kernel(long long* dst, long long v) { *dst = v; }
 
+// ----------------------------------------------------------------- incremental binning
+// A stage trains a subset of the Gaussians (the dynamic rows in the shift stage, the var rows in
+// the inheritance and densification stages); the records of the other rows do not change over the
+// stage's iterations. Their pairs are binned and sorted once (the static lists, with each pair's
+// depth key and each tile's first position), and every iteration bins and sorts only the moving
+// rows' records and merges the two lists tile by tile: the result is the full binning's, pair for
+// pair, because both orders are the one of the key (tile, depth bits, record id).
+
+// First index of the sorted keys [0, n) that is >= v.
+__device__ __forceinline__ long long lower_bound_u32(const uint32_t* __restrict__ keys, long long n, uint32_t v) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (__ldg(keys + mid) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// start[t] = first sorted position of tile t (t = 0 .. tiles_total; start[tiles_total] = stored count).
+__global__ void tile_start_kernel(const uint32_t* __restrict__ keys, const long long* __restrict__ n_dev,
+                                  int tiles_total, uint32_t* __restrict__ start) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles_total) return;
+    start[t] = (uint32_t)lower_bound_u32(keys, *n_dev, (uint32_t)t);
+}
+
+// depth[i] = the sort key (depth bits) of the record of pair i, i < *n_dev.
+__global__ void pair_depth_kernel(const dass_splat* __restrict__ splats, const uint32_t* __restrict__ rec,
+                                  const long long* __restrict__ n_dev, uint32_t* __restrict__ depth) {
+    const long long n = *n_dev;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
+        depth[i] = __float_as_uint(__ldg(&splats[rec[i]].depth));
+}
+
+// Records of the moving rows, camera-major and ascending: list[c m + k] = rec_base(c) + rows[k] for the
+// m = *m_dev rows (ascending); *n_list = n_cams m.
+__global__ void moving_list_kernel(const int* __restrict__ rows, const long long* __restrict__ m_dev, CamTable ct,
+                                   uint32_t* __restrict__ list, long long* __restrict__ n_list) {
+    const long long m = *m_dev;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *n_list = m * ct.n;
+    if (i >= m * ct.n) return;
+    const long long c = i / m, k = i - c * m;
+    list[i] = (uint32_t)(ct.c[c].rec_base + rows[k]);
+}
+
+// *dst = min(*src, cap).
+__global__ void copy_len_kernel(long long* __restrict__ dst, const long long* __restrict__ src, long long cap) {
+    const long long v = *src;
+    *dst = v < cap ? v : cap;
+}
+
+// One warp per tile: the tile's static pairs [s_start[t], s_start[t + 1]) and moving pairs
+// [d_start[t], d_start[t + 1]) are merged by (depth bits, record id) into out_rec from the tile's
+// first position, the static count of earlier tiles plus the moving count of earlier tiles. Keys are
+// distinct (record ids are). The warp takes the static list in blocks of kMergeBlock keys staged in
+// shared memory. The moving pairs below the block's last key (all remaining ones at the last block)
+// are taken 32 at a time, one per lane: a binary search over the staged block gives the number p of
+// static keys below it, so it goes to its own index plus the static pairs before the block plus p,
+// and it adds one to the block's insertion count at p. A static key k of the block is then above
+// the moving pairs of earlier blocks and above those of this block with p <= k (an inclusive scan of
+// the insertion counts). Positions at or beyond cap are dropped and the ranges clamped to cap (the
+// counters flag the overflow, as in the full binning); empty tiles get the range (0, 0).
+constexpr int kMergeWarps = 8;
+constexpr int kMergeBlock = 256;     // static keys staged per step
+__global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
+    int tiles_total, const uint32_t* __restrict__ s_rec, const uint32_t* __restrict__ s_depth,
+    const uint32_t* __restrict__ s_start, const long long* __restrict__ s_counters,
+    const uint32_t* __restrict__ d_rec, const uint32_t* __restrict__ d_depth, const uint32_t* __restrict__ d_start,
+    const long long* __restrict__ d_counters, long long cap, uint32_t* __restrict__ out_rec,
+    uint32_t* __restrict__ ranges, long long* __restrict__ counters) {
+    constexpr int B = kMergeBlock, PER = B / 32;
+    __shared__ uint32_t sh_d[kMergeWarps][B];
+    __shared__ uint32_t sh_r[kMergeWarps][B];
+    __shared__ uint32_t sh_c[kMergeWarps][B + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long t = (long long)blockIdx.x * kMergeWarps + w;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long total = s_counters[0] + d_counters[0];
+        counters[0] = total;
+        counters[1] = total > cap ? 1 : 0;
+        counters[2] = total > cap ? cap : total;
+    }
+    if (t >= tiles_total) return;
+    const uint32_t ss = s_start[t], se = s_start[t + 1], ds = d_start[t], de = d_start[t + 1];
+    const long long base = (long long)ss + ds;
+    const long long total = (long long)(se - ss) + (de - ds);
+    if (lane == 0) {
+        const long long b0 = base < cap ? base : cap, b1 = base + total < cap ? base + total : cap;
+        ranges[2 * t] = total > 0 ? (uint32_t)b0 : 0u;
+        ranges[2 * t + 1] = total > 0 ? (uint32_t)b1 : 0u;
+    }
+    if (total == 0) return;
+    uint32_t* kd = sh_d[w];
+    uint32_t* kr = sh_r[w];
+    uint32_t* cnt = sh_c[w];
+    uint32_t q = ds;                  // next moving pair to place
+    for (uint32_t g0 = ss; g0 < se; g0 += B) {
+        const uint32_t nS = se - g0 < (uint32_t)B ? se - g0 : (uint32_t)B;
+        const bool last_block = g0 + B >= se;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const uint32_t k = lane + 32 * m;
+            kd[k] = k < nS ? __ldg(s_depth + g0 + k) : 0xffffffffu;
+            kr[k] = k < nS ? __ldg(s_rec + g0 + k) : 0xffffffffu;
+            cnt[k] = 0u;
+        }
+        if (lane == 0) cnt[B] = 0u;
+        __syncwarp();
+        const uint32_t ld = kd[nS - 1], lr = kr[nS - 1];
+        const uint32_t q0 = q;
+        while (q < de) {
+            const uint32_t j = q + lane;
+            const bool valid = j < de;
+            const uint32_t dd = valid ? __ldg(d_depth + j) : 0xffffffffu;
+            const uint32_t dr = valid ? __ldg(d_rec + j) : 0xffffffffu;
+            const bool in_block = valid && (last_block || dd < ld || (dd == ld && dr < lr));
+            const unsigned bal = __ballot_sync(0xffffffffu, in_block);    // a prefix of the lanes
+            if (in_block) {
+                uint32_t lo = 0, hi = nS;            // static keys of the block below (dd, dr)
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    const uint32_t md = kd[mid];
+                    if (md < dd || (md == dd && kr[mid] < dr)) lo = mid + 1;
+                    else hi = mid;
+                }
+                const long long pos = base + (j - ds) + (g0 - ss) + lo;
+                if (pos < cap) out_rec[pos] = dr;
+                atomicAdd(&cnt[lo], 1u);
+            }
+            const uint32_t n_in = (uint32_t)__popc(bal);
+            q += n_in;
+            if (n_in < 32u) break;
+        }
+        __syncwarp();
+        // inclusive scan of the insertion counts: lane l owns keys [PER l, PER l + PER)
+        uint32_t v[PER];
+        uint32_t run = 0;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            run += cnt[PER * lane + m];
+            v[m] = run;
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - run;
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) cnt[PER * lane + m] = excl + v[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const uint32_t k = lane + 32 * m;
+            if (k < nS) {
+                const long long pos = base + (g0 - ss) + k + (q0 - ds) + cnt[k];
+                if (pos < cap) out_rec[pos] = kr[k];
+            }
+        }
+        __syncwarp();
+    }
+    // moving pairs above every static pair (all of them when the tile has no static pair)
+    for (uint32_t j = q + lane; j < de; j += 32) {
+        const long long pos = base + (j - ds) + (se - ss);
+        if (pos < cap) out_rec[pos] = __ldg(d_rec + j);
+    }
+}
+
 // ----------------------------------------------------------------- host-side orchestration
 
 struct Carver {
@@ -596,6 +780,51 @@ size_t bin_sort_workspace_bytes(long long n_rec, long long cap) {
     return cv.used;
 }
 
+// Binning and sort of the items i < *s.scal (capacity n_cap; item i is record list[i], or record i
+// when list is null; rows flagged in skip_rows emit nothing) into pair_rec[cap] and counters[3];
+// *keys_out points at the sorted tile keys (workspace) on return.
+int bin_sort_core(const dass_splat* splats, long long n_cap, const uint32_t* list, const uint8_t* skip_rows,
+                  const CamTable& ct, uint32_t* pair_rec, long long cap, long long* counters, SortScratch& s,
+                  cudaStream_t st, uint32_t** keys_out) {
+    const long long* n_dev = s.scal + 0;
+    bin_count_kernel<<<div_up(n_cap, 256), 256, 0, st>>>(splats, n_dev, list, skip_rows, ct, s.kA, s.vA, s.counts);
+    count_launch();
+    int rc = check_launch("bin_count");
+    if (rc) return rc;
+    // 1) depth digits on the records (32 bits)
+    int set = 0;
+    rc = radix_sort(s.kA, s.vA, s.kB, s.vB, n_dev, n_cap, 32, s, st, &set);
+    if (rc) return rc;
+    uint32_t* order = set == 0 ? s.vA : s.vB;
+    uint32_t* recs = list ? (set == 0 ? s.vB : s.vA) : order;   // the other value buffer is free now
+    // 2) pair offsets and record ids in depth order
+    gather_counts_kernel<<<div_up(n_cap, 256), 256, 0, st>>>(order, s.counts, list, s.offsets, recs, n_dev);
+    count_launch();
+    rc = scan_u32(s.offsets, s.offsets, n_dev, n_cap, s.partial, s.scal + 2, st);
+    if (rc) return rc;
+    // 3) duplicate into tile-keyed pairs (stored count -> counters[2])
+    int tbits = bits_for(ct.tiles_total > 1 ? ct.tiles_total : 2);
+    int passes = (tbits + kMaxDigitBits - 1) / kMaxDigitBits;
+    // the sort must end in (pk?, pair_rec): pass i writes set (i+1)%2; choose the start set
+    uint32_t *k_out = s.pk0, *v_out = pair_rec, *k_tmp = s.pk1, *v_tmp = s.pv1;
+    uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
+    uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
+    duplicate_kernel<<<div_up(n_cap, kDupThreads), kDupThreads, 0, st>>>(splats, n_dev, ct, recs, s.offsets,
+                                                                         s.scal + 2, cap, k_start, v_start, counters);
+    count_launch();
+    rc = check_launch("duplicate");
+    if (rc) return rc;
+    // 4) tile digits on the pairs
+    const long long* m_dev = counters + 2;
+    if (passes % 2 == 0)
+        rc = radix_sort(k_out, v_out, k_tmp, v_tmp, m_dev, cap, tbits, s, st, &set);
+    else
+        rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
+    if (rc) return rc;
+    *keys_out = k_out;
+    return DASS_OK;
+}
+
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec,
                     long long cap, uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes,
                     cudaStream_t st) {
@@ -608,42 +837,92 @@ int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& c
         return DASS_OK;
     }
     set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec); count_launch();
-    bin_count_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(splats, n_rec, ct, s.kA, s.vA, s.counts); count_launch();
-    int rc = check_launch("bin_count");
-    if (rc) return rc;
-    // 1) depth digits on the records (32 bits)
-    int set = 0;
-    rc = radix_sort(s.kA, s.vA, s.kB, s.vB, s.scal + 0, n_rec, 32, s, st, &set);
-    if (rc) return rc;
-    uint32_t* order = set == 0 ? s.vA : s.vB;
-    // 2) pair offsets in depth order
-    gather_counts_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(order, s.counts, s.offsets, n_rec); count_launch();
-    rc = scan_u32(s.offsets, s.offsets, s.scal + 0, n_rec, s.partial, s.scal + 2, st);
-    if (rc) return rc;
-    // 3) duplicate into tile-keyed pairs (stored count -> counters[2])
-    int tbits = bits_for(ct.tiles_total > 1 ? ct.tiles_total : 2);
-    int passes = (tbits + kMaxDigitBits - 1) / kMaxDigitBits;
-    // the sort must end in (pk?, pair_rec): pass i writes set (i+1)%2; choose the start set
-    uint32_t *k_out = s.pk0, *v_out = pair_rec, *k_tmp = s.pk1, *v_tmp = s.pv1;
-    uint32_t *k_start = (passes % 2 == 0) ? k_out : k_tmp;
-    uint32_t *v_start = (passes % 2 == 0) ? v_out : v_tmp;
-    duplicate_kernel<<<div_up(n_rec, kDupThreads), kDupThreads, 0, st>>>(splats, n_rec, ct, order, s.offsets,
-                                                                         s.scal + 2, cap, k_start, v_start, counters);
-    count_launch();
-    rc = check_launch("duplicate");
-    if (rc) return rc;
-    // 4) tile digits on the pairs
-    const long long* m_dev = counters + 2;
-    if (passes % 2 == 0)
-        rc = radix_sort(k_out, v_out, k_tmp, v_tmp, m_dev, cap, tbits, s, st, &set);
-    else
-        rc = radix_sort(k_tmp, v_tmp, k_out, v_out, m_dev, cap, tbits, s, st, &set);
+    uint32_t* keys = nullptr;
+    int rc = bin_sort_core(splats, n_rec, nullptr, nullptr, ct, pair_rec, cap, counters, s, st, &keys);
     if (rc) return rc;
     // 5) tile ranges
     const int rq = div_up(div_up(cap, 4), 256);
-    tile_ranges_kernel<<<rq < 152 * 8 ? rq : 152 * 8, 256, 0, st>>>(k_out, m_dev, tile_ranges);
+    tile_ranges_kernel<<<rq < 152 * 8 ? rq : 152 * 8, 256, 0, st>>>(keys, counters + 2, tile_ranges);
     count_launch();
     return check_launch("tile_ranges");
+}
+
+size_t bin_sort_split_workspace_bytes(long long n_rows, long long n_rec, long long cap) {
+    const size_t a = bin_sort_workspace_bytes(n_rec, cap), b = mask_rows_workspace_bytes(n_rows);
+    return a > b ? a : b;
+}
+
+int bin_sort_split_launch(const dass_splat* splats, long long n_rows, const CamTable& ct, const uint8_t* moving_rows,
+                          long long cap, const StaticBins& sb, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const long long n_rec = (long long)ct.n * n_rows;
+    if (n_rows <= 0 || ws_bytes < bin_sort_split_workspace_bytes(n_rows, n_rec, cap)) return DASS_ERR_OOM;
+    // the moving rows (ascending), then their records camera by camera
+    int rc = mask_rows_launch(moving_rows, n_rows, sb.rows, sb.n_rows_moving, ws, ws_bytes, st);
+    if (rc) return rc;
+    moving_list_kernel<<<div_up(n_rec, 256), 256, 0, st>>>(sb.rows, sb.n_rows_moving, ct, sb.moving, sb.n_moving);
+    count_launch();
+    if ((rc = check_launch("moving_list_kernel"))) return rc;
+    // the static pairs: every record but the moving rows'
+    Carver cv{reinterpret_cast<char*>(ws), 0, ws_bytes};
+    SortScratch s = carve(cv, n_rec, cap);
+    set_len_kernel<<<1, 1, 0, st>>>(s.scal + 0, n_rec); count_launch();
+    uint32_t* keys = nullptr;
+    if ((rc = bin_sort_core(splats, n_rec, nullptr, moving_rows, ct, sb.rec, cap, sb.counters, s, st, &keys)))
+        return rc;
+    tile_start_kernel<<<div_up(ct.tiles_total + 1, 256), 256, 0, st>>>(keys, sb.counters + 2, ct.tiles_total,
+                                                                       sb.start);
+    count_launch();
+    pair_depth_kernel<<<152 * 8, 256, 0, st>>>(splats, sb.rec, sb.counters + 2, sb.depth);
+    count_launch();
+    return check_launch("bin_sort_split");
+}
+
+namespace {
+struct MergeScratch {
+    SortScratch s;
+    uint32_t* rec;
+    uint32_t* depth;
+    uint32_t* start;
+    long long* counters;
+};
+MergeScratch carve_merge(Carver& cv, long long moving_cap, long long cap, int tiles_total) {
+    MergeScratch m;
+    m.s = carve(cv, moving_cap, cap);
+    m.rec = cv.take<uint32_t>(cap);
+    m.depth = cv.take<uint32_t>(cap);
+    m.start = cv.take<uint32_t>((long long)tiles_total + 1);
+    m.counters = cv.take<long long>(4);
+    return m;
+}
+}  // namespace
+
+size_t bin_sort_merge_workspace_bytes(long long moving_cap, long long cap, int tiles_total) {
+    Carver cv{nullptr, 0, 0};
+    carve_merge(cv, moving_cap > 0 ? moving_cap : 1, cap, tiles_total);
+    return cv.used;
+}
+
+int bin_sort_merge_launch(const dass_splat* splats, const CamTable& ct, const StaticBins& sb, long long moving_cap,
+                          long long cap, uint32_t* pair_rec, uint32_t* tile_ranges, long long* counters, void* ws,
+                          size_t ws_bytes, cudaStream_t st) {
+    if (moving_cap < 1) moving_cap = 1;
+    Carver cv{reinterpret_cast<char*>(ws), 0, ws_bytes};
+    MergeScratch m = carve_merge(cv, moving_cap, cap, ct.tiles_total);
+    if (cv.used > ws_bytes) return DASS_ERR_OOM;
+    copy_len_kernel<<<1, 1, 0, st>>>(m.s.scal + 0, sb.n_moving, moving_cap);
+    count_launch();
+    uint32_t* keys = nullptr;
+    int rc = bin_sort_core(splats, moving_cap, sb.moving, nullptr, ct, m.rec, cap, m.counters, m.s, st, &keys);
+    if (rc) return rc;
+    pair_depth_kernel<<<152 * 4, 256, 0, st>>>(splats, m.rec, m.counters + 2, m.depth);
+    count_launch();
+    tile_start_kernel<<<div_up(ct.tiles_total + 1, 256), 256, 0, st>>>(keys, m.counters + 2, ct.tiles_total, m.start);
+    count_launch();
+    merge_pairs_kernel<<<div_up(ct.tiles_total, kMergeWarps), 32 * kMergeWarps, 0, st>>>(
+        ct.tiles_total, sb.rec, sb.depth, sb.start, sb.counters, m.rec, m.depth, m.start, m.counters, cap, pair_rec,
+        tile_ranges, counters);
+    count_launch();
+    return check_launch("bin_sort_merge");
 }
 
 // Generic pieces reused by other translation units.

@@ -98,17 +98,74 @@ struct RenderBufs {
     void* loss_ws;
     size_t loss_ws_bytes;
     const float* ystats;     // the targets' SSIM window statistics (lambda > 0), else null
+    // incremental binning of a stage whose moving rows are few (inc_on): the static lists are built
+    // once by inc_begin and every iteration merges the moving rows' pairs into them
+    bool inc_on;
+    long long inc_rows;      // most moving rows the scratch holds (0: no incremental scratch)
+    long long moving_cap;    // records of the current stage's moving rows (host bound)
+    StaticBins sb;
+    uint8_t* moving;         // [n] moving-row mask built for the shift stage
+    void* merge_ws;
+    size_t merge_ws_bytes;
 };
 
-// Scratch of the render part (sort and loss workspaces, cached target statistics, tracking).
-void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long long cap, float lam, RenderBufs& b) {
+// Scratch of the render part (sort and loss workspaces, cached target statistics, tracking) and,
+// when inc_rows > 0, of the incremental binning for stages that move at most inc_rows of the n rows.
+void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long long cap, float lam, RenderBufs& b,
+                          long long n = 0, long long inc_rows = 0) {
     b.bin_ws_bytes = bin_sort_workspace_bytes(n_rec, cap);
+    if (inc_rows > 0) {
+        const size_t sp = bin_sort_split_workspace_bytes(n, n_rec, cap);
+        b.bin_ws_bytes = sp > b.bin_ws_bytes ? sp : b.bin_ws_bytes;
+    }
     b.bin_ws = a.take<char>((long long)b.bin_ws_bytes);
     b.loss_ws_bytes = loss_workspace_bytes(ct);
     b.loss_ws = a.take<char>((long long)b.loss_ws_bytes);
     float* ys = a.take<float>(lam > 0.f ? 6 * ct.pixels_total : 1);
     b.ystats = lam > 0.f ? ys : nullptr;
     b.track = a.take<long long>(2);
+    b.inc_on = false;
+    b.inc_rows = inc_rows;
+    b.moving_cap = 0;
+    b.sb = StaticBins{};
+    b.moving = nullptr;
+    b.merge_ws = nullptr;
+    b.merge_ws_bytes = 0;
+    if (inc_rows > 0) {
+        b.sb.rec = a.take<uint32_t>(cap);
+        b.sb.depth = a.take<uint32_t>(cap);
+        b.sb.start = a.take<uint32_t>((long long)ct.tiles_total + 1);
+        b.sb.counters = a.take<long long>(4);
+        b.sb.moving = a.take<uint32_t>(n_rec);
+        b.sb.n_moving = a.take<long long>(1);
+        b.sb.rows = a.take<int>(n);
+        b.sb.n_rows_moving = a.take<long long>(1);
+        b.moving = a.take<uint8_t>(n);
+        b.merge_ws_bytes = bin_sort_merge_workspace_bytes((long long)ct.n * inc_rows, cap, ct.tiles_total);
+        b.merge_ws = a.take<char>((long long)b.merge_ws_bytes);
+    }
+}
+
+// Rows a stage may move and still bin incrementally: beyond half of the rows the full binning costs
+// less than the static lists plus the merge.
+long long inc_rows_bound(long long n) { return n / 2; }
+
+// Start of the incremental binning of a stage: when the stage moves at most b.inc_rows rows (host
+// bound n_moving) and its records are camera-major with stride g.n, project every row once and build
+// the static lists of the rows not flagged in moving; else the stage bins fully at every iteration.
+int inc_begin(const Scene& g, const CamTable& ct, const uint8_t* moving, long long n_moving, RenderBufs& b,
+              cudaStream_t st) {
+    b.inc_on = false;
+    if (b.inc_rows <= 0 || n_moving > b.inc_rows || ct.rec_stride != g.n || !moving) return DASS_OK;
+    int rc = preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, nullptr, ct, b.splats, st);
+    if (rc) return rc;
+    rc = bin_sort_split_launch(b.splats, g.n, ct, moving, b.cap, b.sb, b.bin_ws, b.bin_ws_bytes, st);
+    if (rc) return rc;
+    track_pairs_kernel<<<1, 1, 0, st>>>(b.sb.counters, b.track);   // a static overflow fails the stage
+    count_launch();
+    b.moving_cap = (long long)ct.n * (n_moving > 0 ? n_moving : 1);
+    b.inc_on = true;
+    return check_launch("inc_begin");
 }
 
 // preprocess -> bin/sort -> forward -> fidelity loss (Eq. 3) -> backward: the part every stage
@@ -120,7 +177,12 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
     const float3 bg = make_float3(0.f, 0.f, 0.f);
     int rc = preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st);
     if (rc) return rc;
-    rc = bin_sort_launch(b.splats, n_rec, ct, b.pair_rec, b.cap, b.ranges, b.counters, b.bin_ws, b.bin_ws_bytes, st);
+    if (b.inc_on)
+        rc = bin_sort_merge_launch(b.splats, ct, b.sb, b.moving_cap, b.cap, b.pair_rec, b.ranges, b.counters,
+                                   b.merge_ws, b.merge_ws_bytes, st);
+    else
+        rc = bin_sort_launch(b.splats, n_rec, ct, b.pair_rec, b.cap, b.ranges, b.counters, b.bin_ws, b.bin_ws_bytes,
+                             st);
     if (rc) return rc;
     track_pairs_kernel<<<1, 1, 0, st>>>(b.counters, b.track);
     count_launch();
@@ -405,8 +467,9 @@ size_t step_scratch(const dass_step_desc* d, const CamTable& ct, int mode, char*
     Arena a{base};
     RenderBufs tmp{};
     RenderBufs& r = b ? *b : tmp;
+    const bool inc = mode == DASS_STEP_BATCHED && d->n_dyn <= inc_rows_bound(d->n);
     carve_render_scratch(a, ct, mode == DASS_STEP_PLAIN ? d->n : (long long)d->n_cams * d->n, d->pair_capacity,
-                         d->lambda_dssim, r);
+                         d->lambda_dssim, r, d->n, inc ? (d->n_dyn > 0 ? d->n_dyn : 1) : 0);
     return a.used;
 }
 
@@ -441,6 +504,16 @@ DASS_API int dass_step(const dass_step_desc* d, int n_iters, int mode, void* str
                  d->beta1, d->beta2, d->eps, d->render_means, d->render_quats, d->d_means_dyn, d->d_quats_dyn,
                  d->stat_accum, d->stat_count};
     if (mode == DASS_STEP_BATCHED) {
+        if (b.inc_rows > 0) {     // the dynamic rows move; the others keep their records all stage
+            DASS_CHECK_CUDA(cudaMemsetAsync(b.moving, 0, (size_t)d->n, st));
+            if (d->n_dyn > 0) {
+                mark_rows_kernel<<<div_up(d->n_dyn, 256), 256, 0, st>>>(d->dyn_idx, d->n_dyn, d->n, b.moving);
+                count_launch();
+            }
+            const Scene gr{d->n, d->sh_degree, d->render_means, d->log_scales, d->render_quats, d->opacity_logit,
+                           d->sh};
+            if (int rc = inc_begin(gr, ct, b.moving, d->n_dyn, b, st)) return rc;
+        }
         if (int rc = replay(st, n_iters, [&] { return shift_iteration(g, ct, d->targets, d->lambda_dssim, d->batch, s,
                                                                        b, st); }))
             return rc;
@@ -471,7 +544,9 @@ bool inherit_desc_ok(const dass_inherit_step_desc* d) {
 size_t inherit_scratch(const dass_inherit_step_desc* d, const CamTable& ct, char* base, RenderBufs* b) {
     Arena a{base};
     RenderBufs tmp{};
-    carve_render_scratch(a, ct, (long long)d->n_cams * d->n, d->pair_capacity, d->lambda_dssim, b ? *b : tmp);
+    const long long inc = d->n_var <= inc_rows_bound(d->n) ? (d->n_var > 0 ? d->n_var : 1) : 0;
+    carve_render_scratch(a, ct, (long long)d->n_cams * d->n, d->pair_capacity, d->lambda_dssim, b ? *b : tmp, d->n,
+                         inc);
     return a.used;
 }
 
@@ -499,6 +574,8 @@ DASS_API int dass_inherit_step(const dass_inherit_step_desc* d, int n_iters, voi
     const Scene g{d->n, d->sh_degree, d->means, d->log_scales, d->quats, d->opacity_logit, d->sh};
     const InheritState s{d->is_var, d->n_var, d->var_rows, d->m, d->keep, d->m_grad, d->adam_m, d->adam_v,
                          d->adam_step, d->d_keep, d->lr, d->beta1, d->beta2, d->eps, d->lambda_inher};
+    // the var rows' masks change; the base rows (keep = 1) keep their records all stage
+    if (int rc = inc_begin(g, ct, d->is_var, d->n_var, b, st)) return rc;
     if (int rc = replay(st, n_iters, [&] { return inherit_iteration(g, ct, d->targets, d->lambda_dssim, d->batch, s, b,
                                                                      st); }))
         return rc;
@@ -531,8 +608,10 @@ size_t densify_scratch(const dass_densify_step_desc* d, const CamTable& ct, char
                        DensifyScratch* ds) {
     Arena a{base};
     RenderBufs tmp{};
-    carve_render_scratch(a, ct, (long long)d->n_cams * d->n, d->pair_capacity, d->lambda_dssim, b ? *b : tmp);
     const long long nv = d->n - d->n_base;
+    const long long inc = nv <= inc_rows_bound(d->n) ? (nv > 0 ? nv : 1) : 0;
+    carve_render_scratch(a, ct, (long long)d->n_cams * d->n, d->pair_capacity, d->lambda_dssim, b ? *b : tmp, d->n,
+                         inc);
     const int K = (d->sh_degree + 1) * (d->sh_degree + 1);
     int* vr = a.take<int>(nv);
     int* dc = a.take<int>(nv);
@@ -576,6 +655,8 @@ DASS_API int dass_densify_step(const dass_densify_step_desc* d, int n_iters, voi
                          d->is_var, d->grad, d->adam_m, d->adam_v, d->adam_step, ds.dc_rows, ds.rest_rows,
                          {d->lr_means, d->lr_log_scales, d->lr_quats, d->lr_opacity, d->lr_sh_dc, d->lr_sh_rest},
                          d->beta1, d->beta2, d->eps};
+    // the var tail is trained; the base rows keep their records all stage
+    if (int rc = inc_begin(g, ct, d->is_var, nv, b, st)) return rc;
     if (int rc = replay(st, n_iters, [&] { return densify_iteration(g, ct, d->targets, d->lambda_dssim, d->batch, s, b,
                                                                      st); }))
         return rc;
@@ -627,7 +708,7 @@ size_t carve_timestep(const dass_timestep_desc* d, const CamTable& ct, char* bas
     t.r.n_last = a.take<int>(ct.pixels_total);
     t.r.dL = a.take<float>(3 * ct.pixels_total);
     t.r.loss = a.take<double>(1);
-    carve_render_scratch(a, ct, n_rec, d->pair_capacity, d->lambda_dssim, t.r);
+    carve_render_scratch(a, ct, n_rec, d->pair_capacity, d->lambda_dssim, t.r, N, inc_rows_bound(N));
     t.render_means = a.take<float>(3 * N); t.render_quats = a.take<float>(4 * N);
     t.stat_accum = a.take<float>(N); t.stat_count = a.take<int>(N); t.dyn_mask = a.take<uint8_t>(N);
     t.off_grad = a.take<float>(7 * nd); t.off_m = a.take<float>(7 * nd); t.off_v = a.take<float>(7 * nd);
@@ -723,6 +804,7 @@ int timestep_run(const dass_timestep_desc* d, const CamTable& ct, TsBufs& w, das
         const Scene g{n0, deg, d->means, d->log_scales, d->quats, d->opacity_logit, d->sh};
         const InheritState s{d->is_var, n_var, w.var_rows, w.m, w.keep, w.m_grad, w.m_am, w.m_av, w.steps + 0,
                              w.d_keep, d->lr_inherit, d->beta1, d->beta2, d->eps, d->lambda_inher};
+        if ((rc = inc_begin(g, ct, d->is_var, n_var, r, st))) return rc;
         rc = replay(st, d->n_inherit, [&] { return inherit_iteration(g, ct, d->targets, lam, d->batch, s, r, st); });
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemcpyAsync(w.losses + 0, r.loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -765,6 +847,8 @@ int timestep_run(const dass_timestep_desc* d, const CamTable& ct, TsBufs& w, das
                   w.stat_accum, w.stat_count};
     if (d->n_shift > 0) {
         DASS_CHECK_CUDA(cudaMemsetAsync(r.track, 0, 2 * sizeof(long long), st));
+        const Scene g1r{n1, deg, w.render_means, w.ls, w.render_quats, w.logit, w.sh};
+        if ((rc = inc_begin(g1r, ct1, w.dyn_mask, d->n_dyn, r, st))) return rc;
         rc = replay(st, d->n_shift, [&] { return shift_iteration(g1, ct1, d->targets, lam, d->batch, ss, r, st); });
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemcpyAsync(w.losses + 1, r.loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -815,6 +899,7 @@ int timestep_run(const dass_timestep_desc* d, const CamTable& ct, TsBufs& w, das
                              {d->lr_means, d->lr_log_scales, d->lr_quats, d->lr_opacity, d->lr_sh_dc, d->lr_sh_rest},
                              d->beta1, d->beta2, d->eps};
         DASS_CHECK_CUDA(cudaMemsetAsync(r.track, 0, 2 * sizeof(long long), st));
+        if ((rc = inc_begin(g2, ct2, w.is_var, nv2, r, st))) return rc;
         rc = replay(st, d->n_densify, [&] { return densify_iteration(g2, ct2, d->targets, lam, d->batch, s, r, st); });
         if (rc) return rc;
         DASS_CHECK_CUDA(cudaMemcpyAsync(w.losses + 2, r.loss, sizeof(double), cudaMemcpyDeviceToDevice, st));

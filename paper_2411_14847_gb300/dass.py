@@ -138,6 +138,12 @@ _SIGS = {
     "dass_bin_sort_packed": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_bin_sort_static": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]),
+    "dass_bin_sort_split_workspace": (C.c_int, [C.c_int64, C.c_int, C.c_int64, _P]),
+    "dass_bin_sort_split": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                      _P, _P, _P, C.c_size_t, _P]),
+    "dass_bin_sort_merge_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
+    "dass_bin_sort_merge": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
+                                      C.c_int64, _P, _P, _P, C.c_size_t, _P]),
     "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, C.c_int64,
                                   _P, _P]),
@@ -329,6 +335,37 @@ def dass_bin_sort_static(splats, rec_stride, cams, tile, pair_rec, tile_ranges, 
     arr = cameras(cams)
     _call("dass_bin_sort_static", _ptr(splats, F32), rec_stride, arr, len(cams), tile, _ptr(pair_rec, I32),
           pair_rec.numel(), _ptr(tile_ranges, I32), _ptr(counters, I64), _stream(stream))
+
+
+def dass_bin_sort_split_workspace(n_rows, n_cams, pair_capacity):
+    b = C.c_size_t(0)
+    _call("dass_bin_sort_split_workspace", n_rows, n_cams, pair_capacity, C.byref(b))
+    return b.value
+
+
+def dass_bin_sort_split(splats, n_rows, cams, tile, moving, static_rec, static_depth, tile_start, static_counters,
+                        moving_rec, n_moving_rec, moving_rows, n_moving_rows, workspace, stream=None):
+    """Static lists of an incremental binning (every row not flagged in `moving`); see include/dass.h."""
+    _call("dass_bin_sort_split", _ptr(splats, F32), n_rows, cameras(cams), len(cams), tile, _ptr(moving, U8),
+          static_rec.numel(), _ptr(static_rec, I32), _ptr(static_depth, I32), _ptr(tile_start, I32),
+          _ptr(static_counters, I64), _ptr(moving_rec, I32), _ptr(n_moving_rec, I64), _ptr(moving_rows, I32),
+          _ptr(n_moving_rows, I64), _ptr(workspace, U8), workspace.numel(), _stream(stream))
+
+
+def dass_bin_sort_merge_workspace(moving_capacity, pair_capacity, tiles_total):
+    b = C.c_size_t(0)
+    _call("dass_bin_sort_merge_workspace", moving_capacity, pair_capacity, tiles_total, C.byref(b))
+    return b.value
+
+
+def dass_bin_sort_merge(splats, n_rows, cams, tile, moving_rec, n_moving_rec, moving_capacity, static_rec,
+                        static_depth, tile_start, static_counters, pair_rec, tile_ranges, counters, workspace,
+                        stream=None):
+    """The moving rows' pairs merged into the static lists: dass_bin_sort's outputs; see include/dass.h."""
+    _call("dass_bin_sort_merge", _ptr(splats, F32), n_rows, cameras(cams), len(cams), tile, _ptr(moving_rec, I32),
+          _ptr(n_moving_rec, I64), moving_capacity, _ptr(static_rec, I32), _ptr(static_depth, I32),
+          _ptr(tile_start, I32), _ptr(static_counters, I64), _ptr(pair_rec, I32), pair_rec.numel(),
+          _ptr(tile_ranges, I32), _ptr(counters, I64), _ptr(workspace, U8), workspace.numel(), _stream(stream))
 
 
 def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, bg=None, stream=None):
