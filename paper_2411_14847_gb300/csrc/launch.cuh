@@ -7,9 +7,12 @@
 
 namespace dass {
 
+// rows (optional, with the device count n_rows and a host bound rows_cap): project only those
+// Gaussians; every other record keeps its contents.
 int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
-                      dass_splat* splats, cudaStream_t st);
+                      dass_splat* splats, cudaStream_t st, const int* rows = nullptr,
+                      const long long* n_rows = nullptr, long long rows_cap = 0);
 int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
                              cudaStream_t st, long long n_max = 0);
 int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,

@@ -164,10 +164,18 @@ __device__ __forceinline__ void write_record(const CamInfo& cam, int tile, int d
 }
 
 template <int K>
+// Thread i projects Gaussian i, or Gaussian rows[i] for i < *n_rows when a row list is given (the
+// other records keep their contents).
 __global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, Params prm, CamTable ct,
-                                                         dass_splat* __restrict__ out) {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+                                                         dass_splat* __restrict__ out, const int* __restrict__ rows,
+                                                         const long long* __restrict__ n_rows) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long g = i;
+    if (rows) {
+        if (i >= *n_rows) return;
+        g = rows[i];
+    }
+    if (g < 0 || g >= n) return;
     float p[3], o, Sig[6], coef[3 * K];
     gaussian_setup<K>(prm, g, p, o, Sig, coef);
     for (int ci = 0; ci < ct.n; ++ci) write_record<K>(ct.c[ci], ct.tile, deg, p, o, Sig, coef, out + ct.c[ci].rec_base + g);
@@ -463,9 +471,12 @@ __global__ void densify_stats_kernel(long long n, CamTable ct, const dass_splat*
 }
 
 template <int K>
-int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass_splat* out, cudaStream_t st) {
+int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass_splat* out, cudaStream_t st,
+               const int* rows, const long long* n_rows, long long rows_cap) {
     int threads = 128;
-    preprocess_kernel<K><<<div_up(n, threads), threads, 0, st>>>(n, deg, prm, ct, out); count_launch();
+    preprocess_kernel<K><<<div_up(rows ? rows_cap : n, threads), threads, 0, st>>>(n, deg, prm, ct, out, rows,
+                                                                                    n_rows);
+    count_launch();
     return check_launch("preprocess_kernel");
 }
 
@@ -491,13 +502,15 @@ int launch_pre_bwd(long long n, int deg, const Params& prm, const CamTable& ct, 
 
 int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
-                      dass_splat* splats, cudaStream_t st) {
+                      dass_splat* splats, cudaStream_t st, const int* rows, const long long* n_rows,
+                      long long rows_cap) {
     Params prm{means, log_scales, quats, opacity_logit, sh, keep};
+    if (rows && (!n_rows || rows_cap <= 0)) return DASS_ERR_INVALID_ARG;
     switch (deg) {
-        case 0: return launch_pre<1>(n, deg, prm, ct, splats, st);
-        case 1: return launch_pre<4>(n, deg, prm, ct, splats, st);
-        case 2: return launch_pre<9>(n, deg, prm, ct, splats, st);
-        case 3: return launch_pre<16>(n, deg, prm, ct, splats, st);
+        case 0: return launch_pre<1>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
+        case 1: return launch_pre<4>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
+        case 2: return launch_pre<9>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
+        case 3: return launch_pre<16>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
     }
     return DASS_ERR_INVALID_ARG;
 }

@@ -175,7 +175,11 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
                      const uint8_t* full_grad, int batch, RenderBufs& b, cudaStream_t st) {
     const long long n_rec = (long long)ct.n * g.n;
     const float3 bg = make_float3(0.f, 0.f, 0.f);
-    int rc = preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st);
+    // incremental binning: the static rows' records are those inc_begin wrote; only the moving rows
+    // are projected again
+    int rc = b.inc_on ? preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st,
+                                          b.sb.rows, b.sb.n_rows_moving, b.moving_cap / ct.n)
+                      : preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st);
     if (rc) return rc;
     if (b.inc_on)
         rc = bin_sort_merge_launch(b.splats, ct, b.sb, b.moving_cap, b.cap, b.pair_rec, b.ranges, b.counters,
