@@ -39,6 +39,13 @@ import numpy as np
 SORT_REC_BYTES = 220
 SORT_PAIR_BYTES = 52
 LOSS_PIX_BYTES = 52
+# Incremental binning of a stage iteration (dass_bin_sort_merge): the moving records and pairs cost
+# what bin_sort charges per record (220 B, plus 4 B for the record list) and per pair (52 B, plus
+# a 4-byte depth key written and read again), and the merge reads every static pair's record and
+# depth key and writes every output pair's record (12 B per pair of the merged list).
+MERGE_REC_BYTES = 224
+MERGE_MOVING_PAIR_BYTES = 60
+MERGE_PAIR_BYTES = 12
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -504,6 +511,32 @@ def main():
     n_pairs = int(sfr.counters[0].item())
     sort_ms = timed(lambda: D.dass_bin_sort(sfr.splats, sfr.n, cams, tile, sfr.pair_rec, sfr.tile_ranges,
                                             sfr.counters, sfr.workspace), reps=5)
+    # the incremental form the stage iterations run: static lists of every non-dynamic row built
+    # once, then the dynamic rows' pairs binned and merged in (same pair lists as dass_bin_sort)
+    mv = torch.zeros(sfr.n, dtype=torch.uint8, device=dev)
+    mv[stage.dyn_idx.long()] = 1
+    cap_ = sfr.pair_capacity
+    i32, i64 = torch.int32, torch.int64
+    sb = dict(rec=torch.empty(cap_, dtype=i32, device=dev), depth=torch.empty(cap_, dtype=i32, device=dev),
+              start=torch.empty(sfr.tiles_total + 1, dtype=i32, device=dev),
+              counters=torch.zeros(4, dtype=i64, device=dev),
+              mrec=torch.empty(len(cams) * sfr.n, dtype=i32, device=dev), nm=torch.zeros(1, dtype=i64, device=dev),
+              rows=torch.empty(sfr.n, dtype=i32, device=dev), nr=torch.zeros(1, dtype=i64, device=dev))
+    sws = torch.empty(D.dass_bin_sort_split_workspace(sfr.n, len(cams), cap_), dtype=torch.uint8, device=dev)
+    D.dass_bin_sort_split(sfr.splats, sfr.n, cams, tile, mv, sb["rec"], sb["depth"], sb["start"], sb["counters"],
+                          sb["mrec"], sb["nm"], sb["rows"], sb["nr"], sws)
+    del sws
+    m_cap = len(cams) * max(1, int(stage.n_dyn))
+    mws = torch.empty(D.dass_bin_sort_merge_workspace(m_cap, cap_, sfr.tiles_total), dtype=torch.uint8, device=dev)
+    m_rec, m_rg = torch.empty(cap_, dtype=i32, device=dev), torch.empty_like(sfr.tile_ranges)
+    m_ct = torch.zeros(4, dtype=i64, device=dev)
+    merge_ms = timed(lambda: D.dass_bin_sort_merge(sfr.splats, sfr.n, cams, tile, sb["mrec"], sb["nm"], m_cap,
+                                                   sb["rec"], sb["depth"], sb["start"], sb["counters"], m_rec, m_rg,
+                                                   m_ct, mws), reps=5)
+    torch.cuda.synchronize()
+    merge_equal = bool(torch.equal(m_rec[:n_pairs], sfr.pair_rec[:n_pairs]) and torch.equal(m_rg, sfr.tile_ranges))
+    n_static_pairs, n_moving_rec = int(sb["counters"][0].item()), int(sb["nm"].item())
+    del mws, sb, m_rec
     # the other stages of one iteration, each timed alone on the same buffers
     gs = {k: v for k, v in stage.g.items()}
     gs["means"], gs["quats"] = stage.render_means, stage.render_quats
@@ -571,7 +604,10 @@ def main():
     deg_bytes = 4 * (3 + 3 + 4 + 1 + 3 * stage.g["sh"].shape[1])
     n_px = sum(c.width * c.height for c in cams)
     hbm = {}
+    merge_bytes = (MERGE_REC_BYTES * n_moving_rec + MERGE_MOVING_PAIR_BYTES * (n_pairs - n_static_pairs)
+                   + MERGE_PAIR_BYTES * n_pairs)
     for name, nbytes, ms_ in (("bin_sort", SORT_REC_BYTES * n_rec + SORT_PAIR_BYTES * n_pairs, sort_ms),
+                              ("bin_sort_merge", merge_bytes, merge_ms),
                               ("loss", LOSS_PIX_BYTES * 3 * n_px, loss_ms),
                               ("preprocess", deg_bytes * sfr.n + 48 * n_rec, pre_ms),
                               ("shift", SHIFT_DYN_BYTES * n_dyn, shift_ms),
@@ -583,6 +619,8 @@ def main():
         hbm[name] = {"bytes": int(nbytes), "ms": round(ms_, 4), "achieved_gbs": round(gbs, 1),
                      "frac": round(gbs / hbm_peak, 4) if hbm_peak else None}
     kernels = {"render_fwd_ms": round(fwd_ms, 3), "render_bwd_ms": round(bwd_ms, 3), "bin_sort_ms": round(sort_ms, 3),
+               "bin_sort_merge_ms": round(merge_ms, 3), "bin_sort_merge_equal": merge_equal,
+               "merge_static_pairs": n_static_pairs, "merge_moving_records": n_moving_rec,
                "preprocess_ms": round(pre_ms, 3), "loss_ms": round(loss_ms, 3),
                "preprocess_bwd_dyn_ms": round(pbwd_ms, 3), "densify_stats_ms": round(stats_ms, 3),
                "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3), "pairs": n_pairs,
