@@ -17,6 +17,7 @@ extrapolates to seconds per timestep.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import math
 import os
@@ -361,7 +362,7 @@ def serve_load(rates, seconds, seed=1005):
         # collection walks it and stalls the scheduler thread for ~35 ms (measured), which set p99
         gc.collect()
         gc.freeze()
-        futs = []
+        pending = collections.deque()     # a client that drops each result once it is ready
         t0 = time.perf_counter()
         nxt = t0
         swap_at = t0 + 1.0
@@ -376,9 +377,11 @@ def serve_load(rates, seconds, seed=1005):
                 for i in range(8):
                     srv.set_scene(i, versions[i][ver])
                 swap_at += 1.0
-            futs.append(srv.submit(int(scene_of[k]), cams[k]))
-        for f in futs:
-            f.result(timeout=300)
+            pending.append(srv.submit(int(scene_of[k]), cams[k]))
+            while pending and pending[0].done():
+                pending.popleft().result()
+        while pending:
+            pending.popleft().result(timeout=300)
         t1 = time.perf_counter()
         lat = srv.stats.latencies_ms
         out[str(rate)] = {"requests": n_req, "p50_ms": round(percentile(lat, 0.5), 3),

@@ -14,7 +14,9 @@ depend on the batch they ran in: every pixel's blend only involves its own camer
 
 Device memory: each launch slot keeps grow-only buffers (records, pairs, sort scratch, image,
 transmittance, last index) sized to the largest batch it has run, so steady-state serving
-allocates only the per-request result images. Stream order: `set_scene` records an event on the
+allocates only the per-request result images; the slot streams are shared by every server of the
+process, so what a closed server leaves in the allocator's per-stream cache serves the next one.
+Stream order: `set_scene` records an event on the
 caller's current stream and every batch using that version waits for it; each result is
 recorded on the submitting thread's current stream before it is handed out, so the allocator
 does not reuse its memory while the caller's work on it is pending.
@@ -37,6 +39,21 @@ from . import dass as D
 
 SPLAT_BYTES = 48
 PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+# Launch-slot streams are shared by every server of the process (per device): the caching allocator
+# keeps freed blocks per stream, so the slot buffers and result images a closed server leaves behind
+# serve the next server instead of staying reserved for streams nobody uses again.
+_SLOT_STREAMS = {}
+_SLOT_LOCK = threading.Lock()
+
+
+def _slot_streams(device, n):
+    with _SLOT_LOCK:
+        pool = _SLOT_STREAMS.setdefault(device, [])
+        while len(pool) < n:
+            pool.append(torch.cuda.Stream(device))
+        return pool[:n]
 
 
 @dataclass
@@ -100,7 +117,7 @@ class RenderServer:
         self._lock = threading.Lock()
         self._cv = threading.Condition(self._lock)
         self._queue = collections.deque()
-        self._streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+        self._streams = _slot_streams(self.device, n_streams)
         self._arenas = [_Arena(self.device) for _ in range(n_streams)]
         self._slots = [None] * n_streams
         self._ids = itertools.count()

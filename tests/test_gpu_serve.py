@@ -195,3 +195,28 @@ def test_serving_mixed_batch_matches_oracle(dass):
             n_flag += 1
         assert covered >= 8
     assert n_flag <= 0.1 * n_tot
+
+
+def test_next_server_reuses_the_cached_blocks(dass):
+    """Servers share their launch-slot streams, so the device memory a closed server leaves in the
+    allocator's per-stream cache (slot buffers, freed result images) serves the next server: running
+    the same requests again needs no new device allocation (a long-lived process that restarts its
+    server does not grow its reserved memory until the allocator must flush and synchronise)."""
+    from paper_2411_14847_gb300.serve import RenderServer
+    scenes = _scenes()
+    reqs = _requests(24, 77)
+
+    def run():
+        with RenderServer(max_batch=1, n_streams=1) as srv:
+            for sid, (_, g) in scenes.items():
+                srv.set_scene(sid, g, copy=False)
+            futs = [srv.submit(sid, cam) for sid, cam in reqs]
+            sums = [float(f.result(timeout=60).sum()) for f in futs]   # each result dropped once read
+        torch.cuda.synchronize()
+        return sums
+
+    first = run()
+    n_alloc = torch.cuda.memory_stats()["num_device_alloc"]
+    second = run()
+    assert second == first
+    assert torch.cuda.memory_stats()["num_device_alloc"] == n_alloc
