@@ -12,7 +12,8 @@ namespace dass {
 int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                       dass_splat* splats, cudaStream_t st, const int* rows = nullptr,
-                      const long long* n_rows = nullptr, long long rows_cap = 0);
+                      const long long* n_rows = nullptr, long long rows_cap = 0,
+                      unsigned long long* vis = nullptr);
 int preprocess_scenes_launch(const dass_scene* scenes, int deg, const CamTable& ct, dass_splat* splats,
                              cudaStream_t st, long long n_max = 0);
 int preprocess_bwd_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
@@ -22,6 +23,9 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
                           float* d_opacity_logit, float* d_sh, float* d_keep, cudaStream_t st);
 int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,
                          float* accum, int* count, cudaStream_t st);
+// The same statistics from the per-Gaussian visibility masks preprocess_launch writes (vis).
+int densify_stats_vis_launch(long long n, const CamTable& ct, const unsigned long long* vis,
+                             const dass_splat_grad* gsp, float* accum, int* count, cudaStream_t st);
 size_t bin_sort_workspace_bytes(long long n_rec, long long cap);
 int bin_sort_launch(const dass_splat* splats, long long n_rec, const CamTable& ct, uint32_t* pair_rec, long long cap,
                     uint32_t* tile_ranges, long long* counters, void* ws, size_t ws_bytes, cudaStream_t st);

@@ -120,7 +120,10 @@ __device__ __forceinline__ void gaussian_setup(const Params& prm, long long g, f
 
 // Project one Gaussian into one camera and write its record (culled records: radius 0).
 template <int K>
-__device__ __forceinline__ void write_record(const CamInfo& cam, int tile, int deg, const float* p, float o,
+// Writes the record and returns whether the densification statistics count it: radius > 0 and the
+// square of that radius around (u, v) reaching [0, W - 1] x [0, H - 1] (the rule the statistics
+// kernel applies to a stored record).
+__device__ __forceinline__ bool write_record(const CamInfo& cam, int tile, int deg, const float* p, float o,
                                              const float* Sig, const float* coef, dass_splat* __restrict__ rec) {
     Proj P;
     project_one(cam, p, Sig, P);
@@ -161,14 +164,19 @@ __device__ __forceinline__ void write_record(const CamInfo& cam, int tile, int d
         dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         dst[2] = make_float4(0.f, P.Z, __int_as_float(0), __int_as_float(0));
     }
+    const float rf = (float)radius;
+    return radius > 0 && !(P.u + rf < 0.f || P.u - rf > (float)(cam.W - 1) || P.v + rf < 0.f ||
+                           P.v - rf > (float)(cam.H - 1));
 }
 
-template <int K>
 // Thread i projects Gaussian i, or Gaussian rows[i] for i < *n_rows when a row list is given (the
-// other records keep their contents).
+// other records keep their contents). vis (optional): bit c of vis[g] = camera c's record counts in
+// the densification statistics.
+template <int K>
 __global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, Params prm, CamTable ct,
                                                          dass_splat* __restrict__ out, const int* __restrict__ rows,
-                                                         const long long* __restrict__ n_rows) {
+                                                         const long long* __restrict__ n_rows,
+                                                         unsigned long long* __restrict__ vis) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long g = i;
     if (rows) {
@@ -178,7 +186,11 @@ __global__ void __launch_bounds__(128) preprocess_kernel(long long n, int deg, P
     if (g < 0 || g >= n) return;
     float p[3], o, Sig[6], coef[3 * K];
     gaussian_setup<K>(prm, g, p, o, Sig, coef);
-    for (int ci = 0; ci < ct.n; ++ci) write_record<K>(ct.c[ci], ct.tile, deg, p, o, Sig, coef, out + ct.c[ci].rec_base + g);
+    unsigned long long m = 0ull;
+    for (int ci = 0; ci < ct.n; ++ci)
+        if (write_record<K>(ct.c[ci], ct.tile, deg, p, o, Sig, coef, out + ct.c[ci].rec_base + g))
+            m |= 1ull << ci;
+    if (vis) vis[g] = m;
 }
 
 // Serving form: camera c shows its own scene; thread (g, c) writes record rec_base_c + g. With a
@@ -221,13 +233,15 @@ struct Grads {
     float* d_keep;
 };
 
+// Gradient of the projection for the rows [rows] (or all rows): one thread per row, cameras in
+// order, each camera's record radius and splat gradient requested one camera ahead.
 template <int K>
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int deg, Params prm, CamTable ct,
                                                              const dass_splat* __restrict__ splats,
                                                              const dass_splat_grad* __restrict__ gsp,
                                                              const int* __restrict__ rows, long long n_rows,
                                                              unsigned flags, int accumulate, Grads out) {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
     long long g = rows ? (long long)rows[r] : r;
     float p[3], ls[3], q[4];
@@ -267,13 +281,26 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // gradient w.r.t. symmetric entries (off-diag counted once)
     float d_o = 0.f;
 
+    // the next camera's radius and splat gradient are requested before this camera's work
+    int nx_radius = 0;
+    float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0, nx2 = nx0;
+    if (ct.n > 0) {
+        const long long rec = ct.c[0].rec_base + g;
+        nx_radius = __float_as_int(__ldg(reinterpret_cast<const float*>(splats + rec) + 10));
+        const float4* gp = reinterpret_cast<const float4*>(gsp + rec);
+        nx0 = __ldg(gp); nx1 = __ldg(gp + 1); nx2 = __ldg(gp + 2);
+    }
     for (int ci = 0; ci < ct.n; ++ci) {
         const CamInfo& cam = ct.c[ci];
-        long long rec = cam.rec_base + g;
-        int radius = __float_as_int(__ldg(reinterpret_cast<const float*>(splats + rec) + 10));
+        const int radius = nx_radius;
+        const float4 g0 = nx0, g1 = nx1, g2 = nx2;
+        if (ci + 1 < ct.n) {
+            const long long rn = ct.c[ci + 1].rec_base + g;
+            nx_radius = __float_as_int(__ldg(reinterpret_cast<const float*>(splats + rn) + 10));
+            const float4* gp = reinterpret_cast<const float4*>(gsp + rn);
+            nx0 = __ldg(gp); nx1 = __ldg(gp + 1); nx2 = __ldg(gp + 2);
+        }
         if (radius <= 0) continue;
-        const float4* gp = reinterpret_cast<const float4*>(gsp + rec);
-        float4 g0 = __ldg(gp), g1 = __ldg(gp + 1), g2 = __ldg(gp + 2);
         float du = g0.x, dv = g0.y, dA = g0.z, dB = g0.w, dC = g1.x;
         float dop = g1.y;
         float drgb[3] = {g1.z, g1.w, g2.x};
@@ -373,7 +400,6 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(long long n, int de
         dp[1] += W[1] * dX + W[4] * dY + W[7] * dZ;
         dp[2] += W[2] * dX + W[5] * dY + W[8] * dZ;
     }
-
     long long orow = r;
     if (flags & DASS_GRAD_OPACITY && out.d_opacity_logit) {
         float v = d_o * kp * o_raw * (1.f - o_raw);
@@ -470,12 +496,47 @@ __global__ void densify_stats_kernel(long long n, CamTable ct, const dass_splat*
     }
 }
 
+// Densification statistics from the visibility masks the preprocess wrote: only the counted
+// cameras' gradients are read (8 of the 48 bytes of each), eight cameras' loads issued at a time.
+// The sum runs over the cameras in order, as in densify_stats_kernel, so the results are equal.
+__global__ void densify_stats_vis_kernel(long long n, CamTable ct, const unsigned long long* __restrict__ vis,
+                                         const dass_splat_grad* __restrict__ gsp, float* accum, int* count) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const unsigned long long m = vis[g];
+    if (!m) return;
+    float sum = 0.f;
+    int cnt = 0;
+    for (int c0 = 0; c0 < ct.n; c0 += 8) {
+        float2 gm[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int ci = c0 + k;
+            gm[k] = (ci < ct.n && ((m >> ci) & 1ull))
+                        ? __ldg(reinterpret_cast<const float2*>(gsp + ct.c[ci].rec_base + g))
+                        : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int ci = c0 + k;
+            if (ci < ct.n && ((m >> ci) & 1ull)) {
+                const CamInfo& cam = ct.c[ci];
+                const float gu = gm[k].x * (0.5f * cam.W), gv = gm[k].y * (0.5f * cam.H);
+                sum += sqrtf(gu * gu + gv * gv);
+                cnt += 1;
+            }
+        }
+    }
+    accum[g] += sum;
+    count[g] += cnt;
+}
+
 template <int K>
 int launch_pre(long long n, int deg, const Params& prm, const CamTable& ct, dass_splat* out, cudaStream_t st,
-               const int* rows, const long long* n_rows, long long rows_cap) {
+               const int* rows, const long long* n_rows, long long rows_cap, unsigned long long* vis) {
     int threads = 128;
     preprocess_kernel<K><<<div_up(rows ? rows_cap : n, threads), threads, 0, st>>>(n, deg, prm, ct, out, rows,
-                                                                                    n_rows);
+                                                                                    n_rows, vis);
     count_launch();
     return check_launch("preprocess_kernel");
 }
@@ -492,9 +553,10 @@ template <int K>
 int launch_pre_bwd(long long n, int deg, const Params& prm, const CamTable& ct, const dass_splat* sp,
                    const dass_splat_grad* gsp, const int* rows, long long n_rows, unsigned flags, int acc,
                    const Grads& gr, cudaStream_t st) {
-    int threads = 128;
-    preprocess_bwd_kernel<K><<<div_up(n_rows, threads), threads, 0, st>>>(n, deg, prm, ct, sp, gsp, rows, n_rows,
-                                                                          flags, acc, gr); count_launch();
+    constexpr int threads = 128;
+    preprocess_bwd_kernel<K><<<div_up(n_rows, threads), threads, 0, st>>>(n, deg, prm, ct, sp, gsp, rows,
+                                                                                  n_rows, flags, acc, gr);
+    count_launch();
     return check_launch("preprocess_bwd_kernel");
 }
 
@@ -503,14 +565,15 @@ int launch_pre_bwd(long long n, int deg, const Params& prm, const CamTable& ct, 
 int preprocess_launch(long long n, int deg, const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logit, const float* sh, const uint8_t* keep, const CamTable& ct,
                       dass_splat* splats, cudaStream_t st, const int* rows, const long long* n_rows,
-                      long long rows_cap) {
+                      long long rows_cap, unsigned long long* vis) {
     Params prm{means, log_scales, quats, opacity_logit, sh, keep};
     if (rows && (!n_rows || rows_cap <= 0)) return DASS_ERR_INVALID_ARG;
+    if (vis && ct.n > 64) return DASS_ERR_INVALID_ARG;
     switch (deg) {
-        case 0: return launch_pre<1>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
-        case 1: return launch_pre<4>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
-        case 2: return launch_pre<9>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
-        case 3: return launch_pre<16>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap);
+        case 0: return launch_pre<1>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap, vis);
+        case 1: return launch_pre<4>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap, vis);
+        case 2: return launch_pre<9>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap, vis);
+        case 3: return launch_pre<16>(n, deg, prm, ct, splats, st, rows, n_rows, rows_cap, vis);
     }
     return DASS_ERR_INVALID_ARG;
 }
@@ -550,6 +613,13 @@ int preprocess_bwd_launch(long long n, int deg, const float* means, const float*
         case 3: return launch_pre_bwd<16>(n, deg, prm, ct, splats, gsp, rows, n_rows, flags, accumulate, gr, st);
     }
     return DASS_ERR_INVALID_ARG;
+}
+
+int densify_stats_vis_launch(long long n, const CamTable& ct, const unsigned long long* vis,
+                             const dass_splat_grad* gsp, float* accum, int* count, cudaStream_t st) {
+    if (n <= 0) return DASS_OK;
+    densify_stats_vis_kernel<<<div_up(n, 256), 256, 0, st>>>(n, ct, vis, gsp, accum, count); count_launch();
+    return check_launch("densify_stats_vis_kernel");
 }
 
 int densify_stats_launch(long long n, const CamTable& ct, const dass_splat* splats, const dass_splat_grad* gsp,

@@ -107,6 +107,7 @@ struct RenderBufs {
     uint8_t* moving;         // [n] moving-row mask built for the shift stage
     void* merge_ws;
     size_t merge_ws_bytes;
+    unsigned long long* vis; // [n] cameras whose record the densification statistics count (or null)
 };
 
 // Scratch of the render part (sort and loss workspaces, cached target statistics, tracking) and,
@@ -131,6 +132,7 @@ void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long lo
     b.moving = nullptr;
     b.merge_ws = nullptr;
     b.merge_ws_bytes = 0;
+    b.vis = (n > 0 && ct.n <= 64) ? a.take<unsigned long long>(n) : nullptr;
     if (inc_rows > 0) {
         b.sb.rec = a.take<uint32_t>(cap);
         b.sb.depth = a.take<uint32_t>(cap);
@@ -157,7 +159,8 @@ int inc_begin(const Scene& g, const CamTable& ct, const uint8_t* moving, long lo
               cudaStream_t st) {
     b.inc_on = false;
     if (b.inc_rows <= 0 || n_moving > b.inc_rows || ct.rec_stride != g.n || !moving) return DASS_OK;
-    int rc = preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, nullptr, ct, b.splats, st);
+    int rc = preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, nullptr, ct, b.splats, st, nullptr,
+                               nullptr, 0, b.vis);
     if (rc) return rc;
     rc = bin_sort_split_launch(b.splats, g.n, ct, moving, b.cap, b.sb, b.bin_ws, b.bin_ws_bytes, st);
     if (rc) return rc;
@@ -178,8 +181,9 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
     // incremental binning: the static rows' records are those inc_begin wrote; only the moving rows
     // are projected again
     int rc = b.inc_on ? preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st,
-                                          b.sb.rows, b.sb.n_rows_moving, b.moving_cap / ct.n)
-                      : preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st);
+                                          b.sb.rows, b.sb.n_rows_moving, b.moving_cap / ct.n, b.vis)
+                      : preprocess_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, keep, ct, b.splats, st,
+                                          nullptr, nullptr, 0, b.vis);
     if (rc) return rc;
     if (b.inc_on)
         rc = bin_sort_merge_launch(b.splats, ct, b.sb, b.moving_cap, b.cap, b.pair_rec, b.ranges, b.counters,
@@ -287,7 +291,8 @@ int shift_iteration(const Scene& g, const CamTable& ct, const float* targets, fl
                                nullptr, s.d_quats_dyn, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
     if (s.stat_accum && s.stat_count) {
-        rc = densify_stats_launch(g.n, ct, b.splats, b.grads, s.stat_accum, s.stat_count, st);
+        rc = b.vis ? densify_stats_vis_launch(g.n, ct, b.vis, b.grads, s.stat_accum, s.stat_count, st)
+                   : densify_stats_launch(g.n, ct, b.splats, b.grads, s.stat_accum, s.stat_count, st);
         if (rc) return rc;
     }
     rc = shift_bwd_launch(s.n_dyn, s.dyn_idx, s.offsets, g.quats, s.d_means_dyn, s.d_quats_dyn, s.offset_grad,

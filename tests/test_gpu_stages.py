@@ -227,6 +227,26 @@ def test_step_plain_equals_batched(dass):
     assert float(a.loss) == pytest.approx(float(b.loss), rel=1e-3)
 
 
+@pytest.mark.parametrize("n_cams", [2, 11])
+def test_step_statistics_equal_the_record_form(dass, n_cams):
+    """The stage iterations count the densification statistics from the visibility masks their
+    projection writes (only the counted cameras' gradients are read); after one iteration they equal,
+    bit for bit, dass_densify_stats applied to the iteration's records and splat gradients (the
+    visibility rule read from the stored records: radius > 0, radius square reaching the image)."""
+    from paper_2411_14847_gb300 import dass as D
+    _, cams, _, _, _, st = _step_setup(dass, n_cams=n_cams, w=80, h=60)
+    st.run(1, D.STEP_BATCHED)
+    torch.cuda.synchronize()
+    fr = st.frame
+    acc = torch.zeros(st.n, device="cuda")
+    cnt = torch.zeros(st.n, dtype=torch.int32, device="cuda")
+    D.dass_densify_stats(st.n, fr.splats, fr.splat_grads, cams, acc, cnt)
+    torch.cuda.synchronize()
+    assert int(cnt.sum()) > 0
+    assert torch.equal(cnt, st.stat_count)
+    assert torch.equal(acc, st.stat_accum)
+
+
 def _oracle_iteration(scene, cams, deg, targets, lam, idx, off, m, v, step, lr=(1e-3,) * 7):
     """One shift-stage iteration of the oracle from a given state: loss and offset gradient of
     Eq. 3 at `off`, then the masked Adam step of the offsets (step count `step`)."""
