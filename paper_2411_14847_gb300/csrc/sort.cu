@@ -581,9 +581,10 @@ __global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
     const long long* __restrict__ d_counters, long long cap, uint32_t* __restrict__ out_rec,
     uint32_t* __restrict__ ranges, long long* __restrict__ counters) {
     constexpr int B = kMergeBlock, PER = B / 32;
+    constexpr int BC = B + B / 32 + 1;     // insertion counts, one pad word per 32 (conflict-free scan)
     __shared__ uint32_t sh_d[kMergeWarps][B];
     __shared__ uint32_t sh_r[kMergeWarps][B];
-    __shared__ uint32_t sh_c[kMergeWarps][B + 1];
+    __shared__ uint32_t sh_c[kMergeWarps][BC];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long t = (long long)blockIdx.x * kMergeWarps + w;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -605,18 +606,35 @@ __global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
     uint32_t* kd = sh_d[w];
     uint32_t* kr = sh_r[w];
     uint32_t* cnt = sh_c[w];
+    auto cix = [](uint32_t k) { return k + (k >> 5); };   // padded index of insertion count k
     uint32_t q = ds;                  // next moving pair to place
+    // the static block in flight: its keys are requested one block ahead
+    uint32_t nd_[PER], nr_[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const uint32_t k = lane + 32 * m;
+        nd_[m] = ss + k < se ? __ldg(s_depth + ss + k) : 0xffffffffu;
+        nr_[m] = ss + k < se ? __ldg(s_rec + ss + k) : 0xffffffffu;
+    }
     for (uint32_t g0 = ss; g0 < se; g0 += B) {
         const uint32_t nS = se - g0 < (uint32_t)B ? se - g0 : (uint32_t)B;
         const bool last_block = g0 + B >= se;
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const uint32_t k = lane + 32 * m;
-            kd[k] = k < nS ? __ldg(s_depth + g0 + k) : 0xffffffffu;
-            kr[k] = k < nS ? __ldg(s_rec + g0 + k) : 0xffffffffu;
-            cnt[k] = 0u;
+            kd[k] = nd_[m];
+            kr[k] = nr_[m];
+            cnt[cix(k)] = 0u;
         }
-        if (lane == 0) cnt[B] = 0u;
+        if (lane == 0) cnt[cix(B)] = 0u;
+        if (!last_block) {
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const uint32_t k = g0 + B + lane + 32 * m;
+                nd_[m] = k < se ? __ldg(s_depth + k) : 0xffffffffu;
+                nr_[m] = k < se ? __ldg(s_rec + k) : 0xffffffffu;
+            }
+        }
         __syncwarp();
         const uint32_t ld = kd[nS - 1], lr = kr[nS - 1];
         const uint32_t q0 = q;
@@ -637,7 +655,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
                 }
                 const long long pos = base + (j - ds) + (g0 - ss) + lo;
                 if (pos < cap) out_rec[pos] = dr;
-                atomicAdd(&cnt[lo], 1u);
+                atomicAdd(&cnt[cix(lo)], 1u);
             }
             const uint32_t n_in = (uint32_t)__popc(bal);
             q += n_in;
@@ -649,7 +667,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
         uint32_t run = 0;
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            run += cnt[PER * lane + m];
+            run += cnt[cix(PER * lane + m)];
             v[m] = run;
         }
         uint32_t incl = run;
@@ -661,13 +679,13 @@ __global__ void __launch_bounds__(32 * kMergeWarps) merge_pairs_kernel(
         const uint32_t excl = incl - run;
         __syncwarp();
 #pragma unroll
-        for (int m = 0; m < PER; ++m) cnt[PER * lane + m] = excl + v[m];
+        for (int m = 0; m < PER; ++m) cnt[cix(PER * lane + m)] = excl + v[m];
         __syncwarp();
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const uint32_t k = lane + 32 * m;
             if (k < nS) {
-                const long long pos = base + (g0 - ss) + k + (q0 - ds) + cnt[k];
+                const long long pos = base + (g0 - ss) + k + (q0 - ds) + cnt[cix(k)];
                 if (pos < cap) out_rec[pos] = kr[k];
             }
         }
