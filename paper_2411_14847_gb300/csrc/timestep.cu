@@ -153,8 +153,9 @@ void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long lo
 long long inc_rows_bound(long long n) { return n / 2; }
 
 // Start of the incremental binning of a stage: when the stage moves at most b.inc_rows rows (host
-// bound n_moving) and its records are camera-major with stride g.n, project every row once and build
-// the static lists of the rows not flagged in moving; else the stage bins fully at every iteration.
+// bound n_moving, then the count the mask flags) and its records are camera-major with stride g.n,
+// project every row once and build the static lists of the rows not flagged in moving; else the
+// stage bins fully at every iteration. Ends with one stream synchronisation.
 int inc_begin(const Scene& g, const CamTable& ct, const uint8_t* moving, long long n_moving, RenderBufs& b,
               cudaStream_t st) {
     b.inc_on = false;
@@ -166,9 +167,15 @@ int inc_begin(const Scene& g, const CamTable& ct, const uint8_t* moving, long lo
     if (rc) return rc;
     track_pairs_kernel<<<1, 1, 0, st>>>(b.sb.counters, b.track);   // a static overflow fails the stage
     count_launch();
-    b.moving_cap = (long long)ct.n * (n_moving > 0 ? n_moving : 1);
+    if ((rc = check_launch("inc_begin"))) return rc;
+    // the iterations are sized by the moving rows the mask actually flags (one read per stage)
+    long long m = 0;
+    DASS_CHECK_CUDA(cudaMemcpyAsync(&m, b.sb.n_rows_moving, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    DASS_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (m > b.inc_rows) return DASS_OK;      // more than the scratch holds: full binning
+    b.moving_cap = (long long)ct.n * (m > 0 ? m : 1);
     b.inc_on = true;
-    return check_launch("inc_begin");
+    return DASS_OK;
 }
 
 // preprocess -> bin/sort -> forward -> fidelity loss (Eq. 3) -> backward: the part every stage

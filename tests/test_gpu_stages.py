@@ -187,11 +187,11 @@ def test_densify_stats_accumulation(dass):
     assert rel_l2(accum.cpu().numpy(), racc) < 1e-3
 
 
-def _step_setup(dass, n=2000, deg=1, n_cams=2, w=64, h=48, lam=0.2, seed=31, tile=16, batch=128):
+def _step_setup(dass, n=2000, deg=1, n_cams=2, w=64, h=48, lam=0.2, seed=31, tile=16, batch=128, dyn_frac=0.1):
     from paper_2411_14847_gb300 import dass as D, raster, timestep
     scene = synth.random_scene(n, deg, seed, box=synth.ARC_BOX, log_scale_mean=-3.0)
     cams = synth.arc_cameras(n_cams, 4.0, w, h)
-    idx, off = synth.dynamic_split(n, 0.1, seed + 1, dmu_std=1e-3, dq_std=1e-3)
+    idx, off = synth.dynamic_split(n, dyn_frac, seed + 1, dmu_std=1e-3, dq_std=1e-3)
     tgt_scene = synth.perturbed(scene, seed + 2)
     targets = [t["image"].numpy() for t in og.render(tgt_scene.arrays(), cams, deg)]
     st = timestep.ShiftStage(raster.to_device(scene.arrays()), cams, cu(np.concatenate([t.reshape(-1) for t in targets])),
@@ -214,10 +214,14 @@ def test_step_gradient_parity_and_update(dass):
     np.testing.assert_allclose(moved[strong], -1e-3 * np.sign(rg[strong]), rtol=1e-3)
 
 
-def test_step_plain_equals_batched(dass):
+@pytest.mark.parametrize("dyn_frac", [0.1, 0.6])
+def test_step_plain_equals_batched(dass, dyn_frac):
+    """The batched, graph-replayed stage against the plain per-camera form (full binning per
+    camera): with 10% dynamic rows the batched stage bins incrementally, with 60% (more than half
+    the rows move) it bins fully at every iteration."""
     from paper_2411_14847_gb300 import dass as D
-    _, _, _, off, _, a = _step_setup(dass, n_cams=3)
-    _, _, _, _, _, b = _step_setup(dass, n_cams=3)
+    _, _, _, off, _, a = _step_setup(dass, n_cams=3, dyn_frac=dyn_frac)
+    _, _, _, _, _, b = _step_setup(dass, n_cams=3, dyn_frac=dyn_frac)
     a.run(1, D.STEP_BATCHED)
     b.run(1, D.STEP_PLAIN)
     assert float(a.loss) == pytest.approx(float(b.loss), rel=1e-5)
