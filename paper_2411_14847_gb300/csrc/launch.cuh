@@ -53,9 +53,12 @@ int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
                       unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,
                       long long rec_stride = 1);
 int render_prepare(int tile, int batch);
+// mean_grads false (with a full_grad mask): the Gaussians outside the mask get no gradient at all
+// (their dL/dmean2D is left as it was), the pixels' state still passes them exactly.
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
-                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st);
+                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st,
+                      bool mean_grads = true);
 size_t loss_workspace_bytes(const CamTable& ct);
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
                 double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr);

@@ -364,6 +364,29 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     return val0 || val1;
 }
 
+// Reverse step of staged entry P0..P4 that only carries the pixels' state past it (T and S, the
+// same operations as pix_bwd_step2), for a Gaussian whose gradient nobody needs.
+template <int NT>
+__device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, int pos, float2 dx, float2 A, float2 B,
+                                               const float4 P0, const float4 P2, const float4 P3,
+                                               const float4 P4) {
+    bool val0 = pos <= p.last0, val1 = pos <= p.last1;
+    const float2 dy = __fadd2_rn(p.fy, hi2(P0));
+    const float2 G = splat_gauss2(lo2(P2), dy, A, B);
+    const float2 oG = __fmul2_rn(hi2(P2), G);
+    const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+    val0 = val0 && !(alpha.x < kAlphaMin);
+    val1 = val1 && !(alpha.y < kAlphaMin);
+    const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
+    const float2 om = one_minus2(am);
+    const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+    const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
+    const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
+    const float2 d = sub2(gc, p.S);
+    p.S = __ffma2_rn(am, d, p.S);
+    p.T = Tj;
+}
+
 // Backward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile. The warp walks the
 // tile's list in reverse from its pixels' last contributor, in rounds of BATCH entries: the lanes
 // read the round's entries (ascending), test each footprint against the block and stage the entries
@@ -373,7 +396,9 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
 // float2 for a mean-only Gaussian: dL/du = a X + b Y, dL/dv = b X + c Y of the block sums X, Y). The
 // upstream gradients of the lanes' pixels live in shared memory (the kernel is held to 64 registers
 // for 32 resident warps per SM).
-template <int TILE, int BATCH, int PPL = 4>
+// MEANS: every entry not flagged in full_grad still gets dL/dmean2D (the shift stage's
+// densification statistics need it); else those entries only carry the recurrence past them.
+template <int TILE, int BATCH, int PPL = 4, bool MEANS = true>
 __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
@@ -500,6 +525,15 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
                         atomicAdd(reinterpret_cast<float*>(dst + 2), e);
                     }
                 }
+            } else if constexpr (!MEANS) {
+                const int p = sPos[t];
+                const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
+                const float2 dx = __fadd2_rn(fx2, lo2(P0));
+                float2 A, B;
+                splat_column2(lo2(P1), hi2(P1), dx, A, B);
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    pix_bwd_recur2<NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4);
             } else {
                 // mean-only entries are taken two at a time when the next one is mean-only too
                 // (warp-uniform), so that one 4-value reduction serves both
@@ -558,13 +592,17 @@ int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
 template <int TILE, int BATCH>
 int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                const float* tf, const int* nl, const float* dimg, const uint8_t* full, long long stride,
-               dass_splat_grad* gs, cudaStream_t st) {
+               dass_splat_grad* gs, cudaStream_t st, bool means) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int PPL = TILE == 8 ? 2 : 4;
     constexpr int WPT = (TILE / 8) * (TILE / (4 * PPL));
     const long long grid = (long long)ct.tiles_total * WPT;
-    render_bwd_warp_kernel<TILE, BATCH, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg, full, stride,
-                                                                      gs);
+    if (means || !full)
+        render_bwd_warp_kernel<TILE, BATCH, PPL, true><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
+                                                                                  full, stride, gs);
+    else
+        render_bwd_warp_kernel<TILE, BATCH, PPL, false><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
+                                                                                   full, stride, gs);
     count_launch();
     return check_launch("render_bwd_warp_kernel");
 }
@@ -597,9 +635,10 @@ int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const 
 
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
-                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st) {
+                      const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st,
+                      bool mean_grads) {
     DASS_DISPATCH(launch_bwd, splats, pair_rec, ranges, ct, bg, T_final, n_last, dL_dimage, full_grad, rec_stride,
-                  gsplat, st)
+                  gsplat, st, mean_grads)
 }
 
 // Checks a (tile, batch) shape before a stage is captured. The compositing kernels use static shared

@@ -182,7 +182,7 @@ int inc_begin(const Scene& g, const CamTable& ct, const uint8_t* moving, long lo
 // iteration shares. keep: Eq. 1 mask or null; full_grad: Gaussians whose complete splat gradient is
 // wanted (null: all).
 int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, const float* targets, float lam,
-                     const uint8_t* full_grad, int batch, RenderBufs& b, cudaStream_t st) {
+                     const uint8_t* full_grad, int batch, RenderBufs& b, cudaStream_t st, bool mean_grads = true) {
     const long long n_rec = (long long)ct.n * g.n;
     const float3 bg = make_float3(0.f, 0.f, 0.f);
     // incremental binning: the static rows' records are those inc_begin wrote; only the moving rows
@@ -209,7 +209,7 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
     if (rc) return rc;
     DASS_CHECK_CUDA(cudaMemsetAsync(b.grads, 0, sizeof(dass_splat_grad) * (size_t)n_rec, st));
     return render_bwd_launch(b.splats, b.pair_rec, b.ranges, ct, batch, bg, b.T, b.n_last, b.dL, full_grad, g.n,
-                             b.grads, st);
+                             b.grads, st, mean_grads);
 }
 
 // Start of a stage: tracking cleared, the targets' window statistics computed once (the targets are
@@ -377,7 +377,8 @@ int inherit_iteration(const Scene& g, const CamTable& ct, const float* targets, 
                       const InheritState& s, RenderBufs& b, cudaStream_t st) {
     int rc = inherit_keep_launch(g.n, s.is_var, s.m, s.keep, st);
     if (rc) return rc;
-    rc = render_iteration(g, s.keep, ct, targets, lam, s.is_var, batch, b, st);
+    // only the var rows' gradients are used: the base rows need no dL/dmean2D here
+    rc = render_iteration(g, s.keep, ct, targets, lam, s.is_var, batch, b, st, false);
     if (rc || s.n_var == 0) return rc;
     rc = preprocess_bwd_launch(g.n, g.deg, g.means, g.ls, g.quats, g.logit, g.sh, s.keep, ct, b.splats, b.grads,
                                s.var_rows, s.n_var, 0u, 0, nullptr, nullptr, nullptr, nullptr, nullptr, s.d_keep, st);
@@ -412,7 +413,8 @@ struct DensifyState {
 // parameter slice of the tail; the SH degree-0 band and the higher bands take their own rates.
 int densify_iteration(const Scene& g, const CamTable& ct, const float* targets, float lam, int batch,
                       const DensifyState& s, RenderBufs& b, cudaStream_t st) {
-    int rc = render_iteration(g, nullptr, ct, targets, lam, s.is_var, batch, b, st);
+    // only the var tail is trained and no statistics are gathered: the base rows need no gradient
+    int rc = render_iteration(g, nullptr, ct, targets, lam, s.is_var, batch, b, st, false);
     if (rc || s.n_var == 0) return rc;
     const long long nv = s.n_var, nb = s.n_base;
     const int K = (g.deg + 1) * (g.deg + 1);
