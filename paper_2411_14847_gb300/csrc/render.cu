@@ -9,6 +9,12 @@
 // same tile never wait for each other. The backward walks the lists in reverse from the block's last
 // contributor, recomputing alpha and T_j = T_{j+1}/(1-alpha_j) from the saved T_final, reduces each
 // Gaussian's gradient across the warp with shuffles and adds it to global memory with vector atomics.
+// A round in which no staged entry can reach the 0.99 alpha clamp (the usual case: it needs an
+// opacity near 0.99) runs a loop instantiation without the clamp's selects, and a backward round
+// whose entries all lie at or before every pixel's last contributor one without the position test;
+// both give the same bits as the general loop.
+#include <type_traits>
+
 #include "launch.cuh"
 
 namespace dass {
@@ -30,6 +36,22 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Whether the alpha clamp at 0.99 can take effect for some pixel of the block [bx, bx + wm1] x
+// [by, by + hm1] (pixel centres). Exactly, alpha = o G with G = exp(-q/2) <= 1 for a positive definite
+// conic, so only o >= 0.99 could clamp. In FP32 the exponent q' = -(log2 e / 2) q is evaluated with
+// four roundings, each off by at most 2^-24 of a value bounded by 0.722 M, where M = a DX^2 +
+// 2|b| DX DY + c DY^2 and DX, DY are the block's largest offsets from the mean; so q' <= 1.72e-7 M,
+// and with ex2.approx's relative error (below 2^-22) G <= (1 + 1.3e-7 M)(1 + 2.4e-7) for M <= 1e6.
+// Then o (1 + 5e-7 M) < 0.985 keeps o G below 0.99 at every pixel of the block. Returns true (the
+// clamp may act) otherwise, and for a conic that is not positive definite or not finite.
+__device__ __forceinline__ bool clamp_possible(float nu, float nv, float a, float b, float c, float o, float bx,
+                                               float by, float wm1, float hm1) {
+    const float DX = fmaxf(fabsf(bx + nu), fabsf((bx + wm1) + nu));
+    const float DY = fmaxf(fabsf(by + nv), fabsf((by + hm1) + nv));
+    const float M = a * DX * DX + 2.f * fabsf(b) * DX * DY + c * DY * DY;
+    return !(a > 0.f) || !(M <= 1e6f) || !(o * (1.f + 5e-7f * M) < 0.985f);
+}
+
 // Forward state of a lane's pixel pair (rows y and y + 4 of one column).
 struct PixFwd2 {
     float2 fy, T, C0, C1, C2;
@@ -43,13 +65,14 @@ struct PixFwd2 {
 // blue), so the step carries na = -alpha and forms T - alpha T = fma(na, T, T) in one rounding. A
 // pixel that skips or is done gets alpha = 0 in the packed blend, which leaves its colour and
 // transmittance exactly unchanged.
-template <bool COUNT>
+// CLAMP = false: no entry of the round can reach the clamp (clamp_possible), so -o G is used as is.
+template <bool CLAMP, bool COUNT>
 __device__ __forceinline__ void pix_fwd_step2(PixFwd2& p, int pos, float2 A, float2 B, const float4 P0,
                                               const float4 P2, const float4 P3, float2 nblue, bool full) {
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P2), dy, A, B);
     const float2 noG = __fmul2_rn(hi2(P2), G);                 // -o G
-    float2 na = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
+    float2 na = CLAMP ? make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y)) : noG;
     const float2 test = __ffma2_rn(na, p.T, p.T);
     bool ok0 = !p.done0 && !(na.x > -kAlphaMin);
     bool ok1 = !p.done1 && !(na.y > -kAlphaMin);
@@ -142,11 +165,12 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
     for (uint32_t base = start; base < end; base += BATCH) {
         if (__all_sync(0xffffffffu, all_done())) break;
         int nl = 0;
+        bool clamp = false;
 #pragma unroll
         for (int r = 0; r < BATCH / 32; ++r) {
             const uint32_t j = base + 32 * r + lane;
-            bool hit = false;
-            float4 s0, s1;
+            bool hit = false, cl = false;
+            float4 s0, s1, F;
             float bl = 0.f;
             uint32_t rec = 0;
             if (j < end) {
@@ -155,9 +179,11 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
                 s0 = __ldg(sp);        // u, v, a, b
                 s1 = __ldg(sp + 1);    // c, o, r, g
                 bl = __ldg(reinterpret_cast<const float*>(sp + 2));
-                const float4 F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
+                F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
                 hit = footprint_reaches_rect(-s0.x, -s0.y, F, bx, by, 7.f, (float)(BH - 1));
+                cl = hit && clamp_possible(-s0.x, -s0.y, s0.z, s0.w, s1.x, s1.y, bx, by, 7.f, (float)(BH - 1));
             }
+            clamp = clamp || __any_sync(0xffffffffu, cl);
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int i = nl + __popc(m & lanemask_lt());
@@ -174,19 +200,25 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
             nl += __popc(m);
         }
         __syncwarp();
+        // the round's entries, with the clamp only where some entry of the round may reach it
+        auto composite = [&](auto clamp_tag) {
+            constexpr bool CL = decltype(clamp_tag)::value;
 #pragma unroll 4
-        for (int t = 0; t < nl; ++t) {
-            if ((t & 3) == 3 && __all_sync(0xffffffffu, all_done())) break;
-            const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t];
-            const float2 nblue = lo2(sP[4][t]);
-            const float2 dx = __fadd2_rn(fx2, lo2(P0));
-            float2 A, B;
-            splat_column2(lo2(P1), hi2(P1), dx, A, B);
-            const bool full = COUNT ? sFullC[COUNT ? t : 0] != 0 : false;
-            const int pos = sPos[t];
+            for (int t = 0; t < nl; ++t) {
+                if ((t & 3) == 3 && __all_sync(0xffffffffu, all_done())) break;
+                const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t];
+                const float2 nblue = lo2(sP[4][t]);
+                const float2 dx = __fadd2_rn(fx2, lo2(P0));
+                float2 A, B;
+                splat_column2(lo2(P1), hi2(P1), dx, A, B);
+                const bool full = COUNT ? sFullC[COUNT ? t : 0] != 0 : false;
+                const int pos = sPos[t];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pix_fwd_step2<COUNT>(pp[k], pos, A, B, P0, P2, P3, nblue, full);
-        }
+                for (int k = 0; k < NP; ++k) pix_fwd_step2<CL, COUNT>(pp[k], pos, A, B, P0, P2, P3, nblue, full);
+            }
+        };
+        if (clamp) composite(std::true_type{});
+        else composite(std::false_type{});
         __syncwarp();
     }
 #pragma unroll
@@ -291,10 +323,11 @@ __device__ __forceinline__ void pix_bwd_load1(const CamInfo& cam, int px, int py
     }
 }
 
-// Loads the pair's state; its upstream gradient goes to shared memory, gp[0], gp[NT], gp[2 NT]
-// (per-thread slots, read back at every step instead of being held in registers).
-template <int NT>
-__device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamInfo& cam, int px, int py, float3 bg,
+// Loads the pair's state; its upstream gradient goes to shared memory, the red and green pairs as one
+// float4 at *g01p and the blue pair at *gp (per-thread slots, read back at every step with two loads
+// instead of being held in registers).
+__device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, float4* g01p, const CamInfo& cam, int px, int py,
+                                              float3 bg,
                                               const float* __restrict__ T_final, const int* __restrict__ n_last,
                                               const float* __restrict__ dL_dimage) {
     float2 g0, g1, g2;
@@ -303,9 +336,8 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
     pix_bwd_load1(cam, px, py + 4, T_final, n_last, dL_dimage, p.T.y, g0.y, g1.y, g2.y, p.last1);
     p.S = __ffma2_rn(g2, make_float2(bg.z, bg.z),
                      __ffma2_rn(g1, make_float2(bg.y, bg.y), __fmul2_rn(g0, make_float2(bg.x, bg.x))));
-    gp[0] = g0;
-    gp[NT] = g1;
-    gp[2 * NT] = g2;
+    *g01p = make_float4(g0.x, g0.y, g1.x, g1.y);
+    *gp = g2;
 }
 
 // Reverse step of staged entry P0..P4 (list position pos) for both pixels of the pair; adds the
@@ -320,15 +352,18 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, const CamI
 // branch-free (no early exit when neither pixel takes part: under SIMT the warp runs the body
 // whenever any lane needs it, and the divergent exits cost more than the masked work; measured
 // 5.95 -> 5.31 ms on the 300k x 20-view backward). Returns whether either pixel took part.
-template <bool FULL, int NT>
-__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int pos, float2 dx, float2 A, float2 B,
-                                              const float4 P0, const float4 P2, const float4 P3, const float4 P4,
-                                              float2* vm, float2* vf) {
-    bool val0 = pos <= p.last0, val1 = pos <= p.last1;
+// CLAMP = false: no entry of the round can reach the clamp (clamp_possible), so alpha = o G and the
+// clamp's derivative mask equals the blend mask. VALID: pos is at or before both pixels' last
+// contributor (the caller checked it for the whole round), so the position test is dropped.
+template <bool FULL, bool CLAMP, bool VALID>
+__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, const float4* g01p, int pos, float2 dx,
+                                              float2 A, float2 B, const float4 P0, const float4 P2, const float4 P3,
+                                              const float4 P4, float2* vm, float2* vf) {
+    bool val0 = VALID || pos <= p.last0, val1 = VALID || pos <= p.last1;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P2), dy, A, B);
     const float2 oG = __fmul2_rn(hi2(P2), G);
-    const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+    const float2 alpha = CLAMP ? make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y)) : oG;
     val0 = val0 && !(alpha.x < kAlphaMin);
     val1 = val1 && !(alpha.y < kAlphaMin);
     const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
@@ -336,15 +371,17 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
     // a pixel that takes no part has om = 1 exactly, and rcp.approx(1) = 1 exactly (checked on
     // sm_103), so its T passes through unchanged without a select
     const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-    const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
+    const float4 g01 = *g01p;
+    const float2 g0 = lo2(g01), g1 = hi2(g01), g2 = *gp;
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
     const float2 d = sub2(gc, p.S);
     const float2 dLda = __fmul2_rn(Tj, d);
     p.S = __ffma2_rn(am, d, p.S);       // alpha gc + (1 - alpha) S = S + alpha (gc - S)
     p.T = Tj;
     // the clamp alpha = 0.99 has zero derivative
-    const bool cm0 = val0 && oG.x < kAlphaMax, cm1 = val1 && oG.y < kAlphaMax;
-    const float2 dpow = __fmul2_rn(dLda, make_float2(cm0 ? alpha.x : 0.f, cm1 ? alpha.y : 0.f));
+    const bool cm0 = CLAMP ? val0 && oG.x < kAlphaMax : val0, cm1 = CLAMP ? val1 && oG.y < kAlphaMax : val1;
+    const float2 dpow = CLAMP ? __fmul2_rn(dLda, make_float2(cm0 ? alpha.x : 0.f, cm1 ? alpha.y : 0.f))
+                              : __fmul2_rn(dLda, am);
     if (FULL) {
         // a lane's pixels share dx: vm[0] collects sum dpow (times dx, and dx^2, once per entry)
         // and vm[1], vf[2] the sums of dpow dy and dpow dy^2; sum dpow dx dy = dx sum dpow dy
@@ -366,21 +403,22 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, int 
 
 // Reverse step of staged entry P0..P4 that only carries the pixels' state past it (T and S, the
 // same operations as pix_bwd_step2), for a Gaussian whose gradient nobody needs.
-template <int NT>
-__device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, int pos, float2 dx, float2 A, float2 B,
-                                               const float4 P0, const float4 P2, const float4 P3,
+template <bool CLAMP, bool VALID>
+__device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, const float4* g01p, int pos, float2 dx,
+                                               float2 A, float2 B, const float4 P0, const float4 P2, const float4 P3,
                                                const float4 P4) {
-    bool val0 = pos <= p.last0, val1 = pos <= p.last1;
+    bool val0 = VALID || pos <= p.last0, val1 = VALID || pos <= p.last1;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P2), dy, A, B);
     const float2 oG = __fmul2_rn(hi2(P2), G);
-    const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+    const float2 alpha = CLAMP ? make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y)) : oG;
     val0 = val0 && !(alpha.x < kAlphaMin);
     val1 = val1 && !(alpha.y < kAlphaMin);
     const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
     const float2 om = one_minus2(am);
     const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-    const float2 g0 = gp[0], g1 = gp[NT], g2 = gp[2 * NT];
+    const float4 g01 = *g01p;
+    const float2 g0 = lo2(g01), g1 = hi2(g01), g2 = *gp;
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
     const float2 d = sub2(gc, p.S);
     p.S = __ffma2_rn(am, d, p.S);
@@ -414,7 +452,8 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     __shared__ uint32_t sRec[BATCH];
     __shared__ int sPos[BATCH];
     __shared__ uint8_t sFull[BATCH];
-    __shared__ float2 sGp[NP * 3 * NT];      // upstream gradients of the lanes' pixel pairs
+    __shared__ float4 sG01[NP * NT];     // upstream gradients of the lanes' pixel pairs: red and green
+    __shared__ float2 sGp[NP * NT];      // blue
     const int lane = threadIdx.x;
     const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
@@ -433,19 +472,27 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     int mylast = -1;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        pix_bwd_load2<NT>(pp[k], sGp + 3 * NT * k + lane, cam, px, py + 8 * k, bg, T_final, n_last, dL_dimage);
+        pix_bwd_load2(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, cam, px, py + 8 * k, bg, T_final, n_last,
+                      dL_dimage);
         mylast = max(mylast, max(pp[k].last0, pp[k].last1));
     }
     const int wlast = __reduce_max_sync(0xffffffffu, mylast);
+    int myfirst = 0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) myfirst = min(myfirst, min(pp[k].last0, pp[k].last1));
+    // smallest last contributor of the block (-1 where a pixel has none or lies outside the image, so
+    // such a block never takes the rounds without the position test)
+    const int wmin = __reduce_min_sync(0xffffffffu, myfirst);
     __syncwarp();
     for (long long hi = (long long)wlast + 1; hi > (long long)start; hi -= BATCH) {
         const long long lo = hi - BATCH > (long long)start ? hi - BATCH : (long long)start;
         int nl = 0;
+        bool clamp = false;
 #pragma unroll
         for (int r = 0; r < BATCH / 32; ++r) {
             const long long pos = lo + 32 * r + lane;
-            bool hit = false;
-            float4 s0, s1;
+            bool hit = false, cl = false;
+            float4 s0, s1, F;
             float bl = 0.f;
             uint32_t rec = 0;
             if (pos < hi) {
@@ -454,9 +501,11 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
                 s0 = __ldg(sp);        // u, v, a, b
                 s1 = __ldg(sp + 1);    // c, o, r, g
                 bl = __ldg(reinterpret_cast<const float*>(sp + 2));
-                const float4 F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
+                F = make_float4(s0.z, s0.w, s1.x, footprint_k2(s0.z, s0.w, s1.x, s1.y));
                 hit = footprint_reaches_rect(-s0.x, -s0.y, F, bx, by, 7.f, (float)(BH - 1));
+                cl = hit && clamp_possible(-s0.x, -s0.y, s0.z, s0.w, s1.x, s1.y, bx, by, 7.f, (float)(BH - 1));
             }
+            clamp = clamp || __any_sync(0xffffffffu, cl);
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int i = nl + __popc(m & lanemask_lt());
@@ -475,97 +524,137 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
             nl += __popc(m);
         }
         __syncwarp();
-        // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm); returns whether a
-        // pixel of this lane took part
-        auto mean_steps = [&](int j, float2* vm) {
-            const int p = sPos[j];
-            const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
-            const float2 dx = __fadd2_rn(fx2, lo2(P0));
-            float2 A, B;
-            splat_column2(lo2(P1), hi2(P1), dx, A, B);
-            bool c = false;
-#pragma unroll
-            for (int k = 0; k < NP; ++k)
-                c |= pix_bwd_step2<false, NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4, vm,
-                                              nullptr);
-            return c;
-        };
-        for (int t = nl - 1; t >= 0; --t) {
-            bool contrib = false;
-            float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            if (sFull[t]) {          // warp-uniform: the same Gaussian for every lane
-                const int p = sPos[t];
-                const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
+        // the round's entries, with the clamp only where some entry of the round may reach it
+        auto reverse_round = [&](auto clamp_tag, auto valid_tag) {
+            constexpr bool CL = decltype(clamp_tag)::value;
+            constexpr bool VA = decltype(valid_tag)::value;
+            // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm); returns whether a
+            // pixel of this lane took part
+            auto mean_steps = [&](int j, float2* vm) {
+                const int p = sPos[j];
+                const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
                 const float2 dx = __fadd2_rn(fx2, lo2(P0));
                 float2 A, B;
                 splat_column2(lo2(P1), hi2(P1), dx, A, B);
-                float2 vf[7];      // vf[0], vf[1] unused: formed from vm below
-#pragma unroll
-                for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
+                bool c = false;
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    contrib |= pix_bwd_step2<true, NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4,
-                                                       vm, vf);
-                if (__ballot_sync(0xffffffffu, contrib)) {
-                    const float X = dx.x * (vm[0].x + vm[0].y), Y = vm[1].x + vm[1].y;
-                    float r[8] = {X, Y, dx.x * X, dx.x * Y, vf[2].x + vf[2].y, vf[3].x + vf[3].y,
-                                  vf[4].x + vf[4].y, vf[5].x + vf[5].y};
-                    const float sm = warp_reduce8(r, lane) * gscale;
-                    const float e = warp_sum(vf[6].x + vf[6].y);
-                    // lane 4 g (g < 8) holds reduced value g: X, Y, dL/da, dL/db, dL/dc, dL/do, dL/dr, dL/dg
-                    const float Xs = __shfl_sync(0xffffffffu, sm, 0), Ys = __shfl_sync(0xffffffffu, sm, 4);
-                    const float v2 = __shfl_sync(0xffffffffu, sm, 8), v3 = __shfl_sync(0xffffffffu, sm, 12);
-                    const float v4 = __shfl_sync(0xffffffffu, sm, 16), v5 = __shfl_sync(0xffffffffu, sm, 20);
-                    const float v6 = __shfl_sync(0xffffffffu, sm, 24), v7 = __shfl_sync(0xffffffffu, sm, 28);
-                    if (lane == 0) {
-                        const float4 F = sF[t];
-                        float4* dst = reinterpret_cast<float4*>(gsplat + sRec[t]);
-                        atomicAdd(dst, make_float4(F.x * Xs + F.y * Ys, F.y * Xs + F.z * Ys, v2, v3));
-                        atomicAdd(dst + 1, make_float4(v4, v5, v6, v7));
-                        atomicAdd(reinterpret_cast<float*>(dst + 2), e);
-                    }
-                }
-            } else if constexpr (!MEANS) {
-                const int p = sPos[t];
-                const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
-                const float2 dx = __fadd2_rn(fx2, lo2(P0));
-                float2 A, B;
-                splat_column2(lo2(P1), hi2(P1), dx, A, B);
+                    c |= pix_bwd_step2<false, CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p, dx, A, B,
+                                                      P0, P2, P3, P4, vm, nullptr);
+                return c;
+            };
+            for (int t = nl - 1; t >= 0; --t) {
+                bool contrib = false;
+                float2 vm[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                if (sFull[t]) {          // warp-uniform: the same Gaussian for every lane
+                    const int p = sPos[t];
+                    const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
+                    const float2 dx = __fadd2_rn(fx2, lo2(P0));
+                    float2 A, B;
+                    splat_column2(lo2(P1), hi2(P1), dx, A, B);
+                    float2 vf[7];      // vf[0], vf[1] unused: formed from vm below
 #pragma unroll
-                for (int k = 0; k < NP; ++k)
-                    pix_bwd_recur2<NT>(pp[k], sGp + 3 * NT * k + lane, p, dx, A, B, P0, P2, P3, P4);
-            } else {
-                // mean-only entries are taken two at a time when the next one is mean-only too
-                // (warp-uniform), so that one 4-value reduction serves both
-                const bool two = t >= 1 && !sFull[t - 1];
-                contrib = mean_steps(t, vm);
-                float2 vm2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                if (two) contrib |= mean_steps(t - 1, vm2);
-                if (__ballot_sync(0xffffffffu, contrib)) {
-                    if (two) {
-                        const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
-                                                     vm2[1].x + vm2[1].y, lane);
-                        // lanes 0, 8 hold X, Y of entry t; lanes 16, 24 those of entry t - 1
-                        const float Yp = __shfl_down_sync(0xffffffffu, r, 8);
-                        if ((lane & 15) == 0) {
-                            const int e = (lane & 16) ? t - 1 : t;
-                            const float4 F = sF[e];
-                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
-                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
-                        }
-                    } else {
-                        const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                        // lane 0 holds X, lane 16 holds Y
-                        const float Yp = __shfl_sync(0xffffffffu, r, 16);
+                    for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k)
+                        contrib |= pix_bwd_step2<true, CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p,
+                                                               dx, A, B, P0, P2, P3, P4, vm, vf);
+                    if (__ballot_sync(0xffffffffu, contrib)) {
+                        const float X = dx.x * (vm[0].x + vm[0].y), Y = vm[1].x + vm[1].y;
+                        float r[8] = {X, Y, dx.x * X, dx.x * Y, vf[2].x + vf[2].y, vf[3].x + vf[3].y,
+                                      vf[4].x + vf[4].y, vf[5].x + vf[5].y};
+                        const float sm = warp_reduce8(r, lane) * gscale;
+                        const float e = warp_sum(vf[6].x + vf[6].y);
+                        // lane 4 g (g < 8) holds reduced value g: X, Y, dL/da, dL/db, dL/dc, dL/do, dL/dr, dL/dg
+                        const float Xs = __shfl_sync(0xffffffffu, sm, 0), Ys = __shfl_sync(0xffffffffu, sm, 4);
+                        const float v2 = __shfl_sync(0xffffffffu, sm, 8), v3 = __shfl_sync(0xffffffffu, sm, 12);
+                        const float v4 = __shfl_sync(0xffffffffu, sm, 16), v5 = __shfl_sync(0xffffffffu, sm, 20);
+                        const float v6 = __shfl_sync(0xffffffffu, sm, 24), v7 = __shfl_sync(0xffffffffu, sm, 28);
                         if (lane == 0) {
                             const float4 F = sF[t];
-                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[t]),
-                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                            float4* dst = reinterpret_cast<float4*>(gsplat + sRec[t]);
+                            atomicAdd(dst, make_float4(F.x * Xs + F.y * Ys, F.y * Xs + F.z * Ys, v2, v3));
+                            atomicAdd(dst + 1, make_float4(v4, v5, v6, v7));
+                            atomicAdd(reinterpret_cast<float*>(dst + 2), e);
                         }
                     }
+                } else if constexpr (!MEANS) {
+                    const int p = sPos[t];
+                    const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t], P4 = sP[4][t];
+                    const float2 dx = __fadd2_rn(fx2, lo2(P0));
+                    float2 A, B;
+                    splat_column2(lo2(P1), hi2(P1), dx, A, B);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k)
+                        pix_bwd_recur2<CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p, dx, A, B, P0, P2,
+                                               P3, P4);
+                } else {
+                    // mean-only entries are taken four at a time when the next three are mean-only too
+                    // (warp-uniform), so that one 8-value reduction serves all four
+                    if (t >= 3 && !sFull[t - 1] && !sFull[t - 2] && !sFull[t - 3]) {
+                        float r8[8];
+                        bool c4 = false;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                            c4 |= mean_steps(t - e, v);
+                            r8[2 * e] = v[0].x + v[0].y;
+                            r8[2 * e + 1] = v[1].x + v[1].y;
+                        }
+                        if (__ballot_sync(0xffffffffu, c4)) {
+                            // lane 8 e holds X of entry t - e, lane 8 e + 4 its Y
+                            const float r = warp_reduce8(r8, lane);
+                            const float Yp = __shfl_down_sync(0xffffffffu, r, 4);
+                            if ((lane & 7) == 0) {
+                                const int e = t - (lane >> 3);
+                                const float4 F = sF[e];
+                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
+                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                            }
+                        }
+                        t -= 3;
+                        continue;
+                    }
+                    // else two at a time when the next one is mean-only too
+                    const bool two = t >= 1 && !sFull[t - 1];
+                    contrib = mean_steps(t, vm);
+                    float2 vm2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    if (two) contrib |= mean_steps(t - 1, vm2);
+                    if (__ballot_sync(0xffffffffu, contrib)) {
+                        if (two) {
+                            const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
+                                                         vm2[1].x + vm2[1].y, lane);
+                            // lanes 0, 8 hold X, Y of entry t; lanes 16, 24 those of entry t - 1
+                            const float Yp = __shfl_down_sync(0xffffffffu, r, 8);
+                            if ((lane & 15) == 0) {
+                                const int e = (lane & 16) ? t - 1 : t;
+                                const float4 F = sF[e];
+                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
+                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                            }
+                        } else {
+                            const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
+                            // lane 0 holds X, lane 16 holds Y
+                            const float Yp = __shfl_sync(0xffffffffu, r, 16);
+                            if (lane == 0) {
+                                const float4 F = sF[t];
+                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[t]),
+                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                            }
+                        }
+                    }
+                    if (two) --t;
                 }
-                if (two) --t;
             }
+        };
+        // every pixel of the block has its last contributor at or after the round's last entry
+        const bool all_valid = hi - 1 <= (long long)wmin;
+        if (clamp) {
+            if (all_valid) reverse_round(std::true_type{}, std::true_type{});
+            else reverse_round(std::true_type{}, std::false_type{});
+        } else {
+            if (all_valid) reverse_round(std::false_type{}, std::true_type{});
+            else reverse_round(std::false_type{}, std::false_type{});
         }
         __syncwarp();
     }

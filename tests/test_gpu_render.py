@@ -294,6 +294,55 @@ def test_gradient_parity_multicam_sh3_dssim(dass):
         assert rel_l2(params[k].grad.cpu().numpy(), ref[k].numpy()) < 1e-3, k
 
 
+def _opaque_mix_scene(seed, n, deg=3):
+    """A scene where one Gaussian in six has opacity above 0.99 (logit 5 to 7), so the 0.99 alpha clamp
+    acts at many pixels and the compositing rounds mix entries that may clamp with entries that cannot."""
+    scene, cams = _small_multicam(seed=seed, n=n, deg=deg, w=64, h=48)
+    rng = np.random.default_rng(seed + 100)
+    hot = rng.random(scene.n) < 1.0 / 6.0
+    scene.opacity_logit = np.where(hot, rng.uniform(5.0, 7.0, scene.n), scene.opacity_logit).astype(np.float32)
+    return scene, cams
+
+
+@pytest.mark.parametrize("tile,batch", [(32, 32), (16, 64), (8, 256)])
+def test_alpha_clamp_rounds_parity(dass, tile, batch):
+    """Rounds with and without a possible clamp (App. A.1: alpha = min(0.99, o G)) against the oracle:
+    images, and the gradients of every parameter (the clamp has zero derivative)."""
+    scene, cams = _opaque_mix_scene(17, 1500)
+    params, ref, loss = _grad_case(dass, scene, cams, 3, 0.2, tile=tile, batch=batch)
+    assert loss == pytest.approx(ref["loss"], rel=1e-4)
+    for k in og.PARAMS:
+        assert rel_l2(params[k].grad.cpu().numpy(), ref[k].numpy()) < 1e-3, k
+    from paper_2411_14847_gb300 import raster
+    fr = _frame(dass, cams, scene.n, tile=tile, batch=batch)
+    imgs = fr.render(raster.to_device(scene.arrays()))
+    torch.cuda.synchronize()
+    projs = og.project_all(scene.arrays(), cams, 3)
+    n_clamped = 0
+    for img, p, cam in zip(imgs, projs, cams):
+        bad, resolved, _, maxerr = _check_image(img, p, cam)
+        assert bad == 0, (bad, resolved, maxerr)
+        n_clamped += int((p["opacity"] >= 0.99).sum())
+    assert n_clamped > 100
+
+
+def test_alpha_clamp_images_bit_identical_across_tiles_and_batches(dass):
+    """The clamp-free and general round forms give the same bits, whatever mix of entries a round holds."""
+    scene, cams = _opaque_mix_scene(19, 2500)
+    from paper_2411_14847_gb300 import raster
+    g = raster.to_device(scene.arrays())
+    ref = None
+    for tile in (8, 16, 32):
+        for batch in (32, 64, 128, 256):
+            fr = _frame(dass, cams, scene.n, tile=tile, batch=batch)
+            fr.render(g)
+            out = torch.cat([fr.image, fr.T_final])
+            if ref is None:
+                ref = out.clone()
+            else:
+                assert torch.equal(out, ref), (tile, batch)
+
+
 def test_loss_parity(dass):
     from paper_2411_14847_gb300 import dass as D
     cams = synth.arc_cameras(2, 4.0, 53, 37)
