@@ -304,6 +304,7 @@ __device__ __forceinline__ float warp_reduce2(float a, float b, int lane) {
 // so one scalar replaces the three channels.
 struct PixBwd2 {
     float2 fy, T, S;
+    float2 g0, g1, g2;
     int last0, last1;
 };
 
@@ -323,11 +324,8 @@ __device__ __forceinline__ void pix_bwd_load1(const CamInfo& cam, int px, int py
     }
 }
 
-// Loads the pair's state; its upstream gradient goes to shared memory, the red and green pairs as one
-// float4 at *g01p and the blue pair at *gp (per-thread slots, read back at every step with two loads
-// instead of being held in registers).
-__device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, float4* g01p, const CamInfo& cam, int px, int py,
-                                              float3 bg,
+// Loads the pair's state, its upstream gradient included (held in registers for the whole walk).
+__device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, const CamInfo& cam, int px, int py, float3 bg,
                                               const float* __restrict__ T_final, const int* __restrict__ n_last,
                                               const float* __restrict__ dL_dimage) {
     float2 g0, g1, g2;
@@ -336,8 +334,9 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, float4* g0
     pix_bwd_load1(cam, px, py + 4, T_final, n_last, dL_dimage, p.T.y, g0.y, g1.y, g2.y, p.last1);
     p.S = __ffma2_rn(g2, make_float2(bg.z, bg.z),
                      __ffma2_rn(g1, make_float2(bg.y, bg.y), __fmul2_rn(g0, make_float2(bg.x, bg.x))));
-    *g01p = make_float4(g0.x, g0.y, g1.x, g1.y);
-    *gp = g2;
+    p.g0 = g0;
+    p.g1 = g1;
+    p.g2 = g2;
 }
 
 // Reverse step of staged entry P0..P4 (list position pos) for both pixels of the pair; adds the
@@ -356,9 +355,9 @@ __device__ __forceinline__ void pix_bwd_load2(PixBwd2& p, float2* gp, float4* g0
 // clamp's derivative mask equals the blend mask. VALID: pos is at or before both pixels' last
 // contributor (the caller checked it for the whole round), so the position test is dropped.
 template <bool FULL, bool CLAMP, bool VALID>
-__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, const float4* g01p, int pos, float2 dx,
-                                              float2 A, float2 B, const float4 P0, const float4 P2, const float4 P3,
-                                              const float4 P4, float2* vm, float2* vf) {
+__device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, int pos, float2 dx, float2 A, float2 B, const float4 P0,
+                                              const float4 P2, const float4 P3, const float4 P4, float2* vm,
+                                              float2* vf) {
     bool val0 = VALID || pos <= p.last0, val1 = VALID || pos <= p.last1;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P2), dy, A, B);
@@ -371,8 +370,7 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, cons
     // a pixel that takes no part has om = 1 exactly, and rcp.approx(1) = 1 exactly (checked on
     // sm_103), so its T passes through unchanged without a select
     const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-    const float4 g01 = *g01p;
-    const float2 g0 = lo2(g01), g1 = hi2(g01), g2 = *gp;
+    const float2 g0 = p.g0, g1 = p.g1, g2 = p.g2;
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
     const float2 d = sub2(gc, p.S);
     const float2 dLda = __fmul2_rn(Tj, d);
@@ -404,9 +402,8 @@ __device__ __forceinline__ bool pix_bwd_step2(PixBwd2& p, const float2* gp, cons
 // Reverse step of staged entry P0..P4 that only carries the pixels' state past it (T and S, the
 // same operations as pix_bwd_step2), for a Gaussian whose gradient nobody needs.
 template <bool CLAMP, bool VALID>
-__device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, const float4* g01p, int pos, float2 dx,
-                                               float2 A, float2 B, const float4 P0, const float4 P2, const float4 P3,
-                                               const float4 P4) {
+__device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, int pos, float2 dx, float2 A, float2 B, const float4 P0,
+                                               const float4 P2, const float4 P3, const float4 P4) {
     bool val0 = VALID || pos <= p.last0, val1 = VALID || pos <= p.last1;
     const float2 dy = __fadd2_rn(p.fy, hi2(P0));
     const float2 G = splat_gauss2(lo2(P2), dy, A, B);
@@ -417,8 +414,7 @@ __device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, con
     const float2 am = make_float2(val0 ? alpha.x : 0.f, val1 ? alpha.y : 0.f);
     const float2 om = one_minus2(am);
     const float2 Tj = __fmul2_rn(p.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-    const float4 g01 = *g01p;
-    const float2 g0 = lo2(g01), g1 = hi2(g01), g2 = *gp;
+    const float2 g0 = p.g0, g1 = p.g1, g2 = p.g2;
     const float2 gc = __ffma2_rn(lo2(P4), g2, __ffma2_rn(hi2(P3), g1, __fmul2_rn(lo2(P3), g0)));
     const float2 d = sub2(gc, p.S);
     p.S = __ffma2_rn(am, d, p.S);
@@ -432,12 +428,13 @@ __device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, const float2* gp, con
 // reverse pair steps over the round's entries from the last one down, reduces each Gaussian's
 // gradient across the warp with shuffles and adds it to splat_grads[record] with vector atomics (one
 // float2 for a mean-only Gaussian: dL/du = a X + b Y, dL/dv = b X + c Y of the block sums X, Y). The
-// upstream gradients of the lanes' pixels live in shared memory (the kernel is held to 64 registers
-// for 32 resident warps per SM).
+// upstream gradients of the lanes' pixels stay in registers (72 per thread, 28 resident warps per
+// SM: faster than 64 registers with the gradients re-read from shared memory at every step, whose
+// loads made up most of the kernel's shared-memory traffic).
 // MEANS: every entry not flagged in full_grad still gets dL/dmean2D (the shift stage's
 // densification statistics need it); else those entries only carry the recurrence past them.
 template <int TILE, int BATCH, int PPL = 4, bool MEANS = true>
-__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
+__global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
@@ -445,15 +442,12 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     constexpr int BH = 4 * PPL;
     constexpr int WX = TILE / 8, WY = TILE / BH, WPT = WX * WY;
     constexpr int NP = PPL / 2;
-    constexpr int NT = 32;
     static_assert(TILE % BH == 0 && BATCH % 32 == 0, "block taller than the tile, or a partial round");
     __shared__ float4 sP[5][BATCH];
     __shared__ float4 sF[BATCH];
     __shared__ uint32_t sRec[BATCH];
     __shared__ int sPos[BATCH];
     __shared__ uint8_t sFull[BATCH];
-    __shared__ float4 sG01[NP * NT];     // upstream gradients of the lanes' pixel pairs: red and green
-    __shared__ float2 sGp[NP * NT];      // blue
     const int lane = threadIdx.x;
     const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
@@ -472,8 +466,7 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     int mylast = -1;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        pix_bwd_load2(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, cam, px, py + 8 * k, bg, T_final, n_last,
-                      dL_dimage);
+        pix_bwd_load2(pp[k], cam, px, py + 8 * k, bg, T_final, n_last, dL_dimage);
         mylast = max(mylast, max(pp[k].last0, pp[k].last1));
     }
     const int wlast = __reduce_max_sync(0xffffffffu, mylast);
@@ -539,8 +532,7 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
                 bool c = false;
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    c |= pix_bwd_step2<false, CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p, dx, A, B,
-                                                      P0, P2, P3, P4, vm, nullptr);
+                    c |= pix_bwd_step2<false, CL, VA>(pp[k], p, dx, A, B, P0, P2, P3, P4, vm, nullptr);
                 return c;
             };
             for (int t = nl - 1; t >= 0; --t) {
@@ -557,8 +549,7 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
                     for (int i = 0; i < 7; ++i) vf[i] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k < NP; ++k)
-                        contrib |= pix_bwd_step2<true, CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p,
-                                                               dx, A, B, P0, P2, P3, P4, vm, vf);
+                        contrib |= pix_bwd_step2<true, CL, VA>(pp[k], p, dx, A, B, P0, P2, P3, P4, vm, vf);
                     if (__ballot_sync(0xffffffffu, contrib)) {
                         const float X = dx.x * (vm[0].x + vm[0].y), Y = vm[1].x + vm[1].y;
                         float r[8] = {X, Y, dx.x * X, dx.x * Y, vf[2].x + vf[2].y, vf[3].x + vf[3].y,
@@ -586,8 +577,7 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
                     splat_column2(lo2(P1), hi2(P1), dx, A, B);
 #pragma unroll
                     for (int k = 0; k < NP; ++k)
-                        pix_bwd_recur2<CL, VA>(pp[k], sGp + NT * k + lane, sG01 + NT * k + lane, p, dx, A, B, P0, P2,
-                                               P3, P4);
+                        pix_bwd_recur2<CL, VA>(pp[k], p, dx, A, B, P0, P2, P3, P4);
                 } else {
                     // mean-only entries are taken four at a time when the next three are mean-only too
                     // (warp-uniform), so that one 8-value reduction serves all four
