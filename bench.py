@@ -505,12 +505,15 @@ def main():
             per.append(a.elapsed_time(b) / reps)
         return statistics.median(per)
 
+    # the tile order the stage iterations composite in (longest lists first), as dass_timestep runs it
+    order = torch.empty(sfr.tiles_total, dtype=torch.int32, device=dev)
+    D.dass_tile_order(sfr.tile_ranges, order)
     # backward first (render_fwd recomputes the same T_final/n_last, so inputs stay consistent)
     bwd_ms = timed(lambda: D.dass_render_bwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
                                              sfr.T_final, sfr.n_last, stage.dL_dimage, sfr.splat_grads,
-                                             full_grad=stage.dyn_mask, rec_stride=sfr.n))
+                                             full_grad=stage.dyn_mask, rec_stride=sfr.n, order=order))
     fwd_ms = timed(lambda: D.dass_render_fwd(sfr.splats, sfr.pair_rec, sfr.tile_ranges, cams, tile, batch,
-                                             sfr.image, sfr.T_final, sfr.n_last))
+                                             sfr.image, sfr.T_final, sfr.n_last, order=order))
     n_pairs = int(sfr.counters[0].item())
     sort_ms = timed(lambda: D.dass_bin_sort(sfr.splats, sfr.n, cams, tile, sfr.pair_rec, sfr.tile_ranges,
                                             sfr.counters, sfr.workspace), reps=5)

@@ -263,11 +263,21 @@ int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, const das
  * (sorted-pair position of the last added Gaussian, -1 if none). bg: host float[3] or NULL
  * (black). batch in {32, 64, 128, 256}: list entries each compositing warp (one 8 x 16 pixel block,
  * 8 x 8 at 8-pixel tiles) examines and stages in shared memory per round; the result does not
- * depend on it. */
+ * depend on it. tile_order: the order in which the launch's blocks take the tiles (a permutation
+ * written by dass_tile_order), or NULL for tile order; the result does not depend on it. */
 int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                     const dass_camera* cams /* host */, int n_cams, int tile, int batch,
                     const float* bg /* host, 3 */, float* image, float* T_final, int32_t* n_last,
-                    void* stream);
+                    const uint32_t* tile_order /* device or NULL */, void* stream);
+
+/* Schedule of the compositing launches (no counterpart in the paper, whose rasteriser renders one
+ * view per launch): writes tile_order (device uint32[tiles_total]), a permutation of the tiles
+ * sorted by descending list length (tile_ranges[2 t + 1] - tile_ranges[2 t], bucketed by 8 steps
+ * per power of two; empty lists last). Passed as tile_order to dass_render_fwd / dass_render_bwd,
+ * it makes the launch's blocks take the longest lists first, so that the launch does not end on a
+ * few long tiles; the results are the same with or without it (the order within a bucket is not
+ * deterministic and does not need to be). One 1024-thread block; tiles_total <= 0 is a no-op. */
+int dass_tile_order(const uint32_t* tile_ranges, int tiles_total, uint32_t* tile_order, void* stream);
 
 /* Measurement variant of dass_render_fwd (same outputs, black background) that also counts
  * the work of the compositing: work[0] = (pixel, Gaussian) pairs whose alpha the forward
@@ -289,12 +299,13 @@ int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const u
  * with full_grad[g] == 0 only receive splat_grads.mean2d (what the densification statistics
  * read), their other fields stay 0 -- e.g. the static Gaussians of the shift stage (Sec. 3.3),
  * whose parameters are not optimised; transmittance and colours are propagated identically.
- * batch as in dass_render_fwd. */
+ * batch and tile_order as in dass_render_fwd. */
 int dass_render_bwd(const dass_splat* splats, int64_t n_records, const uint32_t* pair_rec,
                     const uint32_t* tile_ranges, const dass_camera* cams /* host */, int n_cams,
                     int tile, int batch, const float* bg /* host, 3 */, const float* T_final,
                     const int32_t* n_last, const float* dL_dimage, const uint8_t* full_grad,
-                    int64_t rec_stride, dass_splat_grad* splat_grads, void* stream);
+                    int64_t rec_stride, dass_splat_grad* splat_grads,
+                    const uint32_t* tile_order /* device or NULL */, void* stream);
 
 /* Chain rule from splat gradients to parameter gradients (App. A.1 projection, SH colour,
  * sigmoid/exp activations, Eq. 1 mask), summed over cameras. rows (optional, n_rows

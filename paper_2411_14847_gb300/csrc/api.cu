@@ -287,12 +287,17 @@ bool dass::batch_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; 
 
 DASS_API int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                              const dass_camera* cams, int n_cams, int tile, int batch, const float* bg, float* image,
-                             float* T_final, int32_t* n_last, void* stream) {
+                             float* T_final, int32_t* n_last, const uint32_t* tile_order, void* stream) {
     if (!batch_ok(batch) || !tile_ranges || !image || !T_final || !n_last) return DASS_ERR_INVALID_ARG;
     static thread_local CamTable ct;
     if (!make_cam_table(cams, n_cams, tile, 0, &ct)) return DASS_ERR_INVALID_ARG;
     return render_fwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), image, T_final, n_last,
-                             as_stream(stream));
+                             as_stream(stream), nullptr, nullptr, 1, tile_order);
+}
+
+DASS_API int dass_tile_order(const uint32_t* tile_ranges, int tiles_total, uint32_t* tile_order, void* stream) {
+    if (tiles_total > 0 && (!tile_ranges || !tile_order)) return DASS_ERR_INVALID_ARG;
+    return tile_order_launch(tile_ranges, tiles_total, tile_order, as_stream(stream));
 }
 
 DASS_API int dass_render_work(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
@@ -314,7 +319,7 @@ DASS_API int dass_render_bwd(const dass_splat* splats, int64_t n_records, const 
                              const uint32_t* tile_ranges, const dass_camera* cams, int n_cams, int tile, int batch,
                              const float* bg, const float* T_final, const int32_t* n_last, const float* dL_dimage,
                              const uint8_t* full_grad, int64_t rec_stride, dass_splat_grad* splat_grads,
-                             void* stream) {
+                             const uint32_t* tile_order, void* stream) {
     if (!batch_ok(batch) || n_records < 0 || !tile_ranges || !T_final || !n_last || !dL_dimage)
         return DASS_ERR_INVALID_ARG;
     if (full_grad && rec_stride <= 0) return DASS_ERR_INVALID_ARG;
@@ -324,7 +329,7 @@ DASS_API int dass_render_bwd(const dass_splat* splats, int64_t n_records, const 
     cudaStream_t st = as_stream(stream);
     if (n_records > 0) DASS_CHECK_CUDA(cudaMemsetAsync(splat_grads, 0, sizeof(dass_splat_grad) * n_records, st));
     return render_bwd_launch(splats, pair_rec, tile_ranges, ct, batch, bg3(bg), T_final, n_last, dL_dimage,
-                             full_grad, rec_stride > 0 ? rec_stride : 1, splat_grads, st);
+                             full_grad, rec_stride > 0 ? rec_stride : 1, splat_grads, st, true, tile_order);
 }
 
 DASS_API int dass_preprocess_bwd(int64_t n, int sh_degree, const float* means, const float* log_scales,

@@ -48,17 +48,22 @@ size_t bin_sort_merge_workspace_bytes(long long moving_cap, long long cap, int t
 int bin_sort_merge_launch(const dass_splat* splats, const CamTable& ct, const StaticBins& sb, long long moving_cap,
                           long long cap, uint32_t* pair_rec, uint32_t* tile_ranges, long long* counters, void* ws,
                           size_t ws_bytes, cudaStream_t st);
+// order (optional, device, ct.tiles_total entries): a permutation of the tiles, the order in which the
+// launch's blocks take them (tile_order_launch: longest lists first); null: tile order.
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
                       unsigned long long* work = nullptr, const uint8_t* full_grad = nullptr,
-                      long long rec_stride = 1);
+                      long long rec_stride = 1, const uint32_t* order = nullptr);
 int render_prepare(int tile, int batch);
 // mean_grads false (with a full_grad mask): the Gaussians outside the mask get no gradient at all
 // (their dL/dmean2D is left as it was), the pixels' state still passes them exactly.
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st,
-                      bool mean_grads = true);
+                      bool mean_grads = true, const uint32_t* order = nullptr);
+// Tiles by descending list length (bucketed), into order[tiles]: the block order of the compositing
+// launches, so that the longest lists start first and no long list is left for the end of a launch.
+int tile_order_launch(const uint32_t* ranges, int tiles, uint32_t* order, cudaStream_t st);
 size_t loss_workspace_bytes(const CamTable& ct);
 int loss_launch(const float* image, const float* target, const CamTable& ct, float lambda, float inv_cams, float* dL,
                 double* loss, void* ws, size_t ws_bytes, cudaStream_t st, const float* target_stats = nullptr);

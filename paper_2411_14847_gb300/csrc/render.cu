@@ -112,8 +112,8 @@ __device__ __forceinline__ void pix_fwd_store(float T, float C0, float C1, float
     n_last[cam.pix_base + pix] = last;
 }
 
-// Forward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile (blockIdx.x = tile * WPT
-// + block). The warp walks the tile's list in rounds of BATCH entries: lane i reads entries i,
+// Forward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile (blockIdx.x = slot * WPT
+// + block, the tile of a slot given by order, else the slot itself). The warp walks the tile's list in rounds of BATCH entries: lane i reads entries i,
 // i + 32, ... of the round, tests whether each footprint reaches the block and stages the entries
 // that do at their compacted slots (list order) in the warp's shared memory; the warp then
 // composites the round's compacted entries. Warps never wait for each other, a warp whose pixels
@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
                                                             float* __restrict__ T_final, int* __restrict__ n_last,
                                                             unsigned long long* __restrict__ work,
                                                             const uint8_t* __restrict__ full_grad,
-                                                            long long rec_stride) {
+                                                            long long rec_stride,
+                                                            const uint32_t* __restrict__ order) {
     constexpr int BH = 4 * PPL;
     constexpr int WX = TILE / 8, WY = TILE / BH, WPT = WX * WY;
     constexpr int NP = PPL / 2;
@@ -135,7 +136,9 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
     __shared__ int sPos[BATCH];
     __shared__ uint8_t sFullC[COUNT ? BATCH : 1];
     const int lane = threadIdx.x;
-    const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
+    // the WPT blocks of the tile order[blockIdx.x / WPT] (longest lists first), or of tile blockIdx.x / WPT
+    const int tile_id = order ? (int)order[blockIdx.x / WPT] : (int)(blockIdx.x / WPT);
+    const int wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
     const int bxi = (local % cam.tiles_x) * TILE + (wb % WX) * 8, byi = (local / cam.tiles_x) * TILE + (wb / WX) * BH;
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
-    dass_splat_grad* __restrict__ gsplat) {
+    dass_splat_grad* __restrict__ gsplat, const uint32_t* __restrict__ order) {
     constexpr int BH = 4 * PPL;
     constexpr int WX = TILE / 8, WY = TILE / BH, WPT = WX * WY;
     constexpr int NP = PPL / 2;
@@ -449,7 +452,9 @@ __global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
     __shared__ int sPos[BATCH];
     __shared__ uint8_t sFull[BATCH];
     const int lane = threadIdx.x;
-    const int tile_id = blockIdx.x / WPT, wb = blockIdx.x % WPT;
+    // the WPT blocks of the tile order[blockIdx.x / WPT] (longest lists first), or of tile blockIdx.x / WPT
+    const int tile_id = order ? (int)order[blockIdx.x / WPT] : (int)(blockIdx.x / WPT);
+    const int wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
     const int bxi = (local % cam.tiles_x) * TILE + (wb % WX) * 8, byi = (local / cam.tiles_x) * TILE + (wb / WX) * BH;
@@ -653,17 +658,17 @@ __global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
 template <int TILE, int BATCH>
 int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                float* img, float* tf, int* nl, unsigned long long* work, const uint8_t* full, long long stride,
-               cudaStream_t st) {
+               const uint32_t* order, cudaStream_t st) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int PPL = TILE == 8 ? 2 : 4;
     constexpr int WPT = (TILE / 8) * (TILE / (4 * PPL));
     const long long grid = (long long)ct.tiles_total * WPT;
     if (work)
         render_fwd_warp_kernel<TILE, BATCH, true, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl, work,
-                                                                              full, stride);
+                                                                              full, stride, order);
     else
         render_fwd_warp_kernel<TILE, BATCH, false, PPL><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, img, tf, nl,
-                                                                               nullptr, nullptr, 1);
+                                                                               nullptr, nullptr, 1, order);
     count_launch();
     return check_launch("render_fwd_warp_kernel");
 }
@@ -671,17 +676,17 @@ int launch_fwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
 template <int TILE, int BATCH>
 int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, const CamTable& ct, float3 bg,
                const float* tf, const int* nl, const float* dimg, const uint8_t* full, long long stride,
-               dass_splat_grad* gs, cudaStream_t st, bool means) {
+               dass_splat_grad* gs, cudaStream_t st, bool means, const uint32_t* order) {
     if (ct.tiles_total <= 0) return DASS_OK;
     constexpr int PPL = TILE == 8 ? 2 : 4;
     constexpr int WPT = (TILE / 8) * (TILE / (4 * PPL));
     const long long grid = (long long)ct.tiles_total * WPT;
     if (means || !full)
         render_bwd_warp_kernel<TILE, BATCH, PPL, true><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
-                                                                                  full, stride, gs);
+                                                                                  full, stride, gs, order);
     else
         render_bwd_warp_kernel<TILE, BATCH, PPL, false><<<(unsigned)grid, 32, 0, st>>>(sp, pr, rg, ct, bg, tf, nl, dimg,
-                                                                                   full, stride, gs);
+                                                                                   full, stride, gs, order);
     count_launch();
     return check_launch("render_bwd_warp_kernel");
 }
@@ -707,17 +712,70 @@ int launch_bwd(const dass_splat* sp, const uint32_t* pr, const uint32_t* rg, con
 
 int render_fwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, float* image, float* T_final, int* n_last, cudaStream_t st,
-                      unsigned long long* work, const uint8_t* full_grad, long long rec_stride) {
+                      unsigned long long* work, const uint8_t* full_grad, long long rec_stride,
+                      const uint32_t* order) {
     DASS_DISPATCH(launch_fwd, splats, pair_rec, ranges, ct, bg, image, T_final, n_last, work, full_grad, rec_stride,
-                  st)
+                  order, st)
 }
 
 int render_bwd_launch(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* ranges, const CamTable& ct,
                       int batch, float3 bg, const float* T_final, const int* n_last, const float* dL_dimage,
                       const uint8_t* full_grad, long long rec_stride, dass_splat_grad* gsplat, cudaStream_t st,
-                      bool mean_grads) {
+                      bool mean_grads, const uint32_t* order) {
     DASS_DISPATCH(launch_bwd, splats, pair_rec, ranges, ct, bg, T_final, n_last, dL_dimage, full_grad, rec_stride,
-                  gsplat, st, mean_grads)
+                  gsplat, st, mean_grads, order)
+}
+
+namespace {
+
+// Order of the compositing launches' tiles, longest list first: a counting sort of the tiles by
+// list length in 8 buckets per octave (e = floor(log2 len), the 3 bits below the leading one),
+// descending, empty lists last. One CTA; the order within a bucket follows the shared-memory atomics
+// and only affects the schedule, never a result (every block's pixels and gradient sums are its own).
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __restrict__ ranges, int tiles,
+                                                          uint32_t* __restrict__ order) {
+    __shared__ int count[256];
+    __shared__ int base[256];
+    auto bucket = [&](int t) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        if (len == 0) return 255;
+        const int e = 31 - __clz((int)len);
+        const int m = e >= 3 ? (int)(len >> (e - 3)) & 7 : (int)(len << (3 - e)) & 7;
+        return 254 - min(e * 8 + m, 254);
+    };
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) count[i] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&count[bucket(t)], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {          // exclusive scan of the 256 counts, 8 per lane
+        const int l = threadIdx.x;
+        int v[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = s;
+            s += count[8 * l + k];
+        }
+        int incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += u;
+        }
+        const int excl = incl - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) base[8 * l + k] = excl + v[k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&base[bucket(t)], 1)] = (uint32_t)t;
+}
+
+}  // namespace
+
+int tile_order_launch(const uint32_t* ranges, int tiles, uint32_t* order, cudaStream_t st) {
+    if (tiles <= 0) return DASS_OK;
+    tile_order_kernel<<<1, 1024, 0, st>>>(ranges, tiles, order);
+    count_launch();
+    return check_launch("tile_order_kernel");
 }
 
 // Checks a (tile, batch) shape before a stage is captured. The compositing kernels use static shared

@@ -108,6 +108,7 @@ struct RenderBufs {
     void* merge_ws;
     size_t merge_ws_bytes;
     unsigned long long* vis; // [n] cameras whose record the densification statistics count (or null)
+    uint32_t* order;         // [tiles_total] the compositing launches' tile order, longest list first
 };
 
 // Scratch of the render part (sort and loss workspaces, cached target statistics, tracking) and,
@@ -125,6 +126,7 @@ void carve_render_scratch(Arena& a, const CamTable& ct, long long n_rec, long lo
     float* ys = a.take<float>(lam > 0.f ? 6 * ct.pixels_total : 1);
     b.ystats = lam > 0.f ? ys : nullptr;
     b.track = a.take<long long>(2);
+    b.order = a.take<uint32_t>(ct.tiles_total);
     b.inc_on = false;
     b.inc_rows = inc_rows;
     b.moving_cap = 0;
@@ -201,7 +203,9 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
     if (rc) return rc;
     track_pairs_kernel<<<1, 1, 0, st>>>(b.counters, b.track);
     count_launch();
-    rc = render_fwd_launch(b.splats, b.pair_rec, b.ranges, ct, batch, bg, b.image, b.T, b.n_last, st);
+    if ((rc = tile_order_launch(b.ranges, ct.tiles_total, b.order, st))) return rc;
+    rc = render_fwd_launch(b.splats, b.pair_rec, b.ranges, ct, batch, bg, b.image, b.T, b.n_last, st, nullptr,
+                           nullptr, 1, b.order);
     if (rc) return rc;
     DASS_CHECK_CUDA(cudaMemsetAsync(b.loss, 0, sizeof(double), st));
     rc = loss_launch(b.image, targets, ct, lam, 1.f / (float)ct.n, b.dL, b.loss, b.loss_ws, b.loss_ws_bytes, st,
@@ -209,7 +213,7 @@ int render_iteration(const Scene& g, const uint8_t* keep, const CamTable& ct, co
     if (rc) return rc;
     DASS_CHECK_CUDA(cudaMemsetAsync(b.grads, 0, sizeof(dass_splat_grad) * (size_t)n_rec, st));
     return render_bwd_launch(b.splats, b.pair_rec, b.ranges, ct, batch, bg, b.T, b.n_last, b.dL, full_grad, g.n,
-                             b.grads, st, mean_grads);
+                             b.grads, st, mean_grads, b.order);
 }
 
 // Start of a stage: tracking cleared, the targets' window statistics computed once (the targets are

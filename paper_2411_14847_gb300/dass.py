@@ -144,9 +144,10 @@ _SIGS = {
     "dass_bin_sort_merge_workspace": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, _P]),
     "dass_bin_sort_merge": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
                                       C.c_int64, _P, _P, _P, C.c_size_t, _P]),
-    "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
+    "dass_render_fwd": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dass_tile_order": (C.c_int, [_P, C.c_int, _P, _P]),
     "dass_render_bwd": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, C.c_int64,
-                                  _P, _P]),
+                                  _P, _P, _P]),
     "dass_preprocess_bwd": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P,
                                       C.c_int64, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P]),
     "dass_keep_grad": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int64,
@@ -368,11 +369,17 @@ def dass_bin_sort_merge(splats, n_rows, cams, tile, moving_rec, n_moving_rec, mo
           _ptr(tile_ranges, I32), _ptr(counters, I64), _ptr(workspace, U8), workspace.numel(), _stream(stream))
 
 
-def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, bg=None, stream=None):
+def dass_render_fwd(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_final, n_last, bg=None, order=None,
+                    stream=None):
     arr = cameras(cams)
     bgp = (C.c_float * 3)(*bg) if bg is not None else None
     _call("dass_render_fwd", _ptr(splats, F32), _ptr(pair_rec, I32), _ptr(tile_ranges, I32), arr, len(cams), tile,
-          batch, bgp, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _stream(stream))
+          batch, bgp, _ptr(image, F32), _ptr(T_final, F32), _ptr(n_last, I32), _ptr(order, I32), _stream(stream))
+
+
+def dass_tile_order(tile_ranges, order, stream=None):
+    """order: int32 CUDA tensor of tile_ranges.shape[0] entries (a permutation, longest lists first)."""
+    _call("dass_tile_order", _ptr(tile_ranges, I32), int(order.numel()), _ptr(order, I32), _stream(stream))
 
 
 def dass_kernel_launches():
@@ -389,12 +396,13 @@ def dass_render_work(splats, pair_rec, tile_ranges, cams, tile, batch, image, T_
 
 
 def dass_render_bwd(splats, pair_rec, tile_ranges, cams, tile, batch, T_final, n_last, dL_dimage, splat_grads,
-                    bg=None, full_grad=None, rec_stride=0, stream=None):
+                    bg=None, full_grad=None, rec_stride=0, order=None, stream=None):
     arr = cameras(cams)
     bgp = (C.c_float * 3)(*bg) if bg is not None else None
     _call("dass_render_bwd", _ptr(splats, F32), splat_grads.numel() // GRAD_FLOATS, _ptr(pair_rec, I32),
           _ptr(tile_ranges, I32), arr, len(cams), tile, batch, bgp, _ptr(T_final, F32), _ptr(n_last, I32),
-          _ptr(dL_dimage, F32), _ptr(full_grad, U8), rec_stride, _ptr(splat_grads, F32), _stream(stream))
+          _ptr(dL_dimage, F32), _ptr(full_grad, U8), rec_stride, _ptr(splat_grads, F32), _ptr(order, I32),
+          _stream(stream))
 
 
 def dass_preprocess_bwd(g, cams, splats, splat_grads, out, grad_flags=GRAD_ALL, rows=None, accumulate=False,

@@ -343,6 +343,50 @@ def test_alpha_clamp_images_bit_identical_across_tiles_and_batches(dass):
                 assert torch.equal(out, ref), (tile, batch)
 
 
+def test_tile_order_longest_first_and_results_unchanged(dass):
+    """dass_tile_order: a permutation of the tiles by descending list length (to within its 8
+    buckets per power of two, empty lists last); compositing in that order gives the same images,
+    T_final and n_last bit for bit, and the same gradients up to the order of the atomic sums."""
+    from paper_2411_14847_gb300 import dass as D, raster
+    scene, cams = _small_multicam(seed=23, n=4000)
+    g = raster.to_device(scene.arrays())
+    fr = _frame(dass, cams, scene.n, tile=16, batch=64)
+    fr.render(g)
+    dimg = torch.randn_like(fr.image) * 1e-3
+    fr.render_bwd(dimg)
+    torch.cuda.synchronize()
+    ref = [fr.image.clone(), fr.T_final.clone(), fr.n_last.clone(), fr.splat_grads.clone()]
+    # the order property on synthetic ranges (empty, short and 2^20-long lists, 50k tiles)
+    rng = np.random.default_rng(5)
+    ln = np.where(rng.random(50_000) < 0.1, 0, np.exp(rng.uniform(0, 12, 50_000)).astype(np.int64))
+    ln[:3] = (0, 1, 1 << 20)
+    start = np.concatenate([[0], np.cumsum(ln)[:-1]])
+    syn = torch.as_tensor(np.stack([start, start + ln], 1).astype(np.int32), device="cuda")
+    o_syn = torch.full((ln.size,), -1, dtype=torch.int32, device="cuda")
+    D.dass_tile_order(syn, o_syn)
+    for rgs, o in ((syn, o_syn), (fr.tile_ranges, None)):
+        if o is None:
+            o = torch.full((fr.tiles_total,), -1, dtype=torch.int32, device="cuda")
+            D.dass_tile_order(fr.tile_ranges, o)
+            order = o
+        torch.cuda.synchronize()
+        oh = o.cpu().numpy()
+        np.testing.assert_array_equal(np.sort(oh), np.arange(oh.size))
+        r = rgs.cpu().numpy().astype(np.int64)
+        lo = (r[:, 1] - r[:, 0])[oh]
+        later_max = np.maximum.accumulate(lo[::-1])[::-1]      # longest list at or after each position
+        pos = lo > 0
+        assert np.all(later_max[pos] <= lo[pos] * 1.125)
+        assert np.all(later_max[~pos] == 0)                     # empty lists last
+    D.dass_render_fwd(fr.splats, fr.pair_rec, fr.tile_ranges, cams, 16, 64, fr.image, fr.T_final, fr.n_last,
+                      order=order)
+    D.dass_render_bwd(fr.splats, fr.pair_rec, fr.tile_ranges, cams, 16, 64, fr.T_final, fr.n_last, dimg,
+                      fr.splat_grads, order=order)
+    torch.cuda.synchronize()
+    assert torch.equal(fr.image, ref[0]) and torch.equal(fr.T_final, ref[1]) and torch.equal(fr.n_last, ref[2])
+    assert rel_l2(fr.splat_grads.cpu().numpy(), ref[3].cpu().numpy()) < 1e-5
+
+
 def test_loss_parity(dass):
     from paper_2411_14847_gb300 import dass as D
     cams = synth.arc_cameras(2, 4.0, 53, 37)
