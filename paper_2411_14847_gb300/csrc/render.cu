@@ -113,11 +113,12 @@ __device__ __forceinline__ void pix_fwd_store(float T, float C0, float C1, float
 }
 
 // Forward compositing, one warp per CTA owning one 8 x 4*PPL block of a tile (blockIdx.x = slot * WPT
-// + block, the tile of a slot given by order, else the slot itself). The warp walks the tile's list in rounds of BATCH entries: lane i reads entries i,
-// i + 32, ... of the round, tests whether each footprint reaches the block and stages the entries
-// that do at their compacted slots (list order) in the warp's shared memory; the warp then
-// composites the round's compacted entries. Warps never wait for each other, a warp whose pixels
-// are all done exits at once, and the hardware gives its slot to the next block.
+// + block, the tile of a slot given by order, else the slot itself). The warp walks the tile's list
+// in rounds of BATCH entries: lane i reads entries i, i + 32, ... of the round, tests whether each
+// footprint reaches the block and stages the entries that do at their compacted slots (list order)
+// in the warp's shared memory; the warp then composites the round's compacted entries. Warps never
+// wait for each other, a warp whose pixels are all done exits at once, and the hardware gives its
+// slot to the next block.
 template <int TILE, int BATCH, bool COUNT, int PPL = 4>
 __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_splat* __restrict__ splats,
                                                             const uint32_t* __restrict__ pair_rec,
@@ -526,19 +527,18 @@ __global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
         auto reverse_round = [&](auto clamp_tag, auto valid_tag) {
             constexpr bool CL = decltype(clamp_tag)::value;
             constexpr bool VA = decltype(valid_tag)::value;
-            // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm); returns whether a
-            // pixel of this lane took part
+            // reverse pair steps of the mean-only entry j (dL/dmean2D moments into vm). A mean-only
+            // entry's sums are reduced and added whether or not a pixel took part (adding zeros is exact,
+            // and testing for it cost more than the rare all-zero reductions it saved)
             auto mean_steps = [&](int j, float2* vm) {
                 const int p = sPos[j];
                 const float4 P0 = sP[0][j], P1 = sP[1][j], P2 = sP[2][j], P3 = sP[3][j], P4 = sP[4][j];
                 const float2 dx = __fadd2_rn(fx2, lo2(P0));
                 float2 A, B;
                 splat_column2(lo2(P1), hi2(P1), dx, A, B);
-                bool c = false;
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
-                    c |= pix_bwd_step2<false, CL, VA>(pp[k], p, dx, A, B, P0, P2, P3, P4, vm, nullptr);
-                return c;
+                    pix_bwd_step2<false, CL, VA>(pp[k], p, dx, A, B, P0, P2, P3, P4, vm, nullptr);
             };
             for (int t = nl - 1; t >= 0; --t) {
                 bool contrib = false;
@@ -588,54 +588,49 @@ __global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
                     // (warp-uniform), so that one 8-value reduction serves all four
                     if (t >= 3 && !sFull[t - 1] && !sFull[t - 2] && !sFull[t - 3]) {
                         float r8[8];
-                        bool c4 = false;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                            c4 |= mean_steps(t - e, v);
+                            mean_steps(t - e, v);
                             r8[2 * e] = v[0].x + v[0].y;
                             r8[2 * e + 1] = v[1].x + v[1].y;
                         }
-                        if (__ballot_sync(0xffffffffu, c4)) {
-                            // lane 8 e holds X of entry t - e, lane 8 e + 4 its Y
-                            const float r = warp_reduce8(r8, lane);
-                            const float Yp = __shfl_down_sync(0xffffffffu, r, 4);
-                            if ((lane & 7) == 0) {
-                                const int e = t - (lane >> 3);
-                                const float4 F = sF[e];
-                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
-                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
-                            }
+                        // lane 8 e holds X of entry t - e, lane 8 e + 4 its Y
+                        const float r = warp_reduce8(r8, lane);
+                        const float Yp = __shfl_down_sync(0xffffffffu, r, 4);
+                        if ((lane & 7) == 0) {
+                            const int e = t - (lane >> 3);
+                            const float4 F = sF[e];
+                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
+                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
                         }
                         t -= 3;
                         continue;
                     }
                     // else two at a time when the next one is mean-only too
                     const bool two = t >= 1 && !sFull[t - 1];
-                    contrib = mean_steps(t, vm);
+                    mean_steps(t, vm);
                     float2 vm2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                    if (two) contrib |= mean_steps(t - 1, vm2);
-                    if (__ballot_sync(0xffffffffu, contrib)) {
-                        if (two) {
-                            const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
-                                                         vm2[1].x + vm2[1].y, lane);
-                            // lanes 0, 8 hold X, Y of entry t; lanes 16, 24 those of entry t - 1
-                            const float Yp = __shfl_down_sync(0xffffffffu, r, 8);
-                            if ((lane & 15) == 0) {
-                                const int e = (lane & 16) ? t - 1 : t;
-                                const float4 F = sF[e];
-                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
-                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
-                            }
-                        } else {
-                            const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
-                            // lane 0 holds X, lane 16 holds Y
-                            const float Yp = __shfl_sync(0xffffffffu, r, 16);
-                            if (lane == 0) {
-                                const float4 F = sF[t];
-                                atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[t]),
-                                          make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
-                            }
+                    if (two) mean_steps(t - 1, vm2);
+                    if (two) {
+                        const float r = warp_reduce4(vm[0].x + vm[0].y, vm[1].x + vm[1].y, vm2[0].x + vm2[0].y,
+                                                     vm2[1].x + vm2[1].y, lane);
+                        // lanes 0, 8 hold X, Y of entry t; lanes 16, 24 those of entry t - 1
+                        const float Yp = __shfl_down_sync(0xffffffffu, r, 8);
+                        if ((lane & 15) == 0) {
+                            const int e = (lane & 16) ? t - 1 : t;
+                            const float4 F = sF[e];
+                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[e]),
+                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
+                        }
+                    } else {
+                        const float r = warp_reduce2(vm[0].x + vm[0].y, vm[1].x + vm[1].y, lane);
+                        // lane 0 holds X, lane 16 holds Y
+                        const float Yp = __shfl_sync(0xffffffffu, r, 16);
+                        if (lane == 0) {
+                            const float4 F = sF[t];
+                            atomicAdd(reinterpret_cast<float2*>(gsplat + sRec[t]),
+                                      make_float2(F.x * r + F.y * Yp, F.y * r + F.z * Yp));
                         }
                     }
                     if (two) --t;
