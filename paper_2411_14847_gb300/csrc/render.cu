@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
         // the round's entries, with the clamp only where some entry of the round may reach it
         auto composite = [&](auto clamp_tag) {
             constexpr bool CL = decltype(clamp_tag)::value;
-#pragma unroll 4
+#pragma unroll 8
             for (int t = 0; t < nl; ++t) {
                 if ((t & 3) == 3 && __all_sync(0xffffffffu, all_done())) break;
                 const float4 P0 = sP[0][t], P1 = sP[1][t], P2 = sP[2][t], P3 = sP[3][t];
@@ -432,13 +432,14 @@ __device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, int pos, float2 dx, f
 // reverse pair steps over the round's entries from the last one down, reduces each Gaussian's
 // gradient across the warp with shuffles and adds it to splat_grads[record] with vector atomics (one
 // float2 for a mean-only Gaussian: dL/du = a X + b Y, dL/dv = b X + c Y of the block sums X, Y). The
-// upstream gradients of the lanes' pixels stay in registers (72 per thread, 28 resident warps per
-// SM: faster than 64 registers with the gradients re-read from shared memory at every step, whose
-// loads made up most of the kernel's shared-memory traffic).
+// upstream gradients of the lanes' pixels stay in registers instead of being re-read from shared
+// memory at every step (those loads made up most of the kernel's shared-memory traffic); at 64
+// registers (a few spills in the full-gradient path) 32 warps stay resident per SM, which measured
+// faster than 72 registers at 28 warps.
 // MEANS: every entry not flagged in full_grad still gets dL/dmean2D (the shift stage's
 // densification statistics need it); else those entries only carry the recurrence past them.
 template <int TILE, int BATCH, int PPL = 4, bool MEANS = true>
-__global__ void __launch_bounds__(32, 28) render_bwd_warp_kernel(
+__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
