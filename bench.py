@@ -469,14 +469,19 @@ def main():
         dist.barrier()
     e0.record(ts.stream)
     results = []
+    step_marks = [e0]
     for _ in range(args.steps):
         results.append(one_timestep(t, targets))
         t += 1
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(ts.stream)
+        step_marks.append(ev)
     e1.record(ts.stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
+    step_s = [round(step_marks[i].elapsed_time(step_marks[i + 1]) / 1e3, 4) for i in range(args.steps)]
     launches = D.dass_kernel_launches() - l0
     clk = clocks.stop()
     ms_max = replicas.max_over_ranks(ms, dist if world > 1 else None, device=dev)
@@ -513,15 +518,20 @@ def main():
     a.record(ts.stream)
     te = t0
     e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    marks = [a]
     for _ in range(e2e_steps):
         r = one_timestep(te, dev_tgt, targets_host=host_tgt, host_out=host_out)   # returns once G_t is on the host
         te += 1
         h2d = host_tgt.numel() * 4
         d2h = r["n"] * (4 * (3 + 3 + 4 + 1 + 3 * 16) + 1)
         e2e_n.append(r["n"])
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(ts.stream)
+        marks.append(ev)
     b.record(ts.stream)
     torch.cuda.synchronize()
     e2e_s = a.elapsed_time(b) / 1e3 / e2e_steps
+    e2e_step_s = [round(marks[i].elapsed_time(marks[i + 1]) / 1e3, 4) for i in range(e2e_steps)]
     e2e_clk = e2e_clocks.stop()
     gc.unfreeze()
 
@@ -824,7 +834,8 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": False,
+                "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "step_s": step_s,
+                "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "gaussians": args.n, "cams": args.cams,
                            "resolution": f"{args.width}x{args.height}", "iters_per_timestep": args.iters,
@@ -841,7 +852,7 @@ def main():
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "path": "dass_timestep with host targets and host G_t buffers (pinned)",
                         "start_state": "the timed steps' starting scene and timestep indices",
-                        "gaussians": e2e_n, "clocks": e2e_clk},
+                        "gaussians": e2e_n, "step_s": e2e_step_s, "clocks": e2e_clk},
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
