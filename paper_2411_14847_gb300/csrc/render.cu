@@ -435,11 +435,12 @@ __device__ __forceinline__ void pix_bwd_recur2(PixBwd2& p, int pos, float2 dx, f
 // upstream gradients of the lanes' pixels stay in registers instead of being re-read from shared
 // memory at every step (those loads made up most of the kernel's shared-memory traffic); at 64
 // registers (a few spills in the full-gradient path) 32 warps stay resident per SM, which measured
-// faster than 72 registers at 28 warps.
+// faster than 72 registers at 28 warps. Rounds of 128 or 256 entries need more registers (at 64 they
+// spill heavily: 3.3 -> 6.0 ms), so those instantiations keep 72 registers and 28 warps.
 // MEANS: every entry not flagged in full_grad still gets dL/dmean2D (the shift stage's
 // densification statistics need it); else those entries only carry the recurrence past them.
 template <int TILE, int BATCH, int PPL = 4, bool MEANS = true>
-__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(
+__global__ void __launch_bounds__(32, BATCH <= 64 ? 32 : 28) render_bwd_warp_kernel(
     const dass_splat* __restrict__ splats, const uint32_t* __restrict__ pair_rec, const uint32_t* __restrict__ ranges,
     CamTable ct, float3 bg, const float* __restrict__ T_final, const int* __restrict__ n_last,
     const float* __restrict__ dL_dimage, const uint8_t* __restrict__ full_grad, long long rec_stride,
