@@ -264,7 +264,9 @@ int dass_bin_sort_static(const dass_splat* splats, int64_t rec_stride, const das
  * (black). batch in {32, 64, 128, 256}: list entries each compositing warp (one 8 x 16 pixel block,
  * 8 x 8 at 8-pixel tiles) examines and stages in shared memory per round; the result does not
  * depend on it. tile_order: the order in which the launch's blocks take the tiles (a permutation
- * written by dass_tile_order), or NULL for tile order; the result does not depend on it. */
+ * of 0 .. tiles_total - 1, as dass_tile_order writes it), or NULL for tile order; the result does
+ * not depend on it (entries outside that range are skipped, and a tile left out of the order is
+ * not composited). */
 int dass_render_fwd(const dass_splat* splats, const uint32_t* pair_rec, const uint32_t* tile_ranges,
                     const dass_camera* cams /* host */, int n_cams, int tile, int batch,
                     const float* bg /* host, 3 */, float* image, float* T_final, int32_t* n_last,

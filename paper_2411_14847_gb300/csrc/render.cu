@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(32, 32) render_fwd_warp_kernel(const dass_spla
     const int lane = threadIdx.x;
     // the WPT blocks of the tile order[blockIdx.x / WPT] (longest lists first), or of tile blockIdx.x / WPT
     const int tile_id = order ? (int)order[blockIdx.x / WPT] : (int)(blockIdx.x / WPT);
+    if ((unsigned)tile_id >= (unsigned)ct.tiles_total) return;     // not a tile: an order that is no permutation
     const int wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
@@ -457,6 +458,7 @@ __global__ void __launch_bounds__(32, BATCH <= 64 ? 32 : 28) render_bwd_warp_ker
     const int lane = threadIdx.x;
     // the WPT blocks of the tile order[blockIdx.x / WPT] (longest lists first), or of tile blockIdx.x / WPT
     const int tile_id = order ? (int)order[blockIdx.x / WPT] : (int)(blockIdx.x / WPT);
+    if ((unsigned)tile_id >= (unsigned)ct.tiles_total) return;     // not a tile: an order that is no permutation
     const int wb = blockIdx.x % WPT;
     const CamInfo& cam = ct.c[cam_of_tile(ct, tile_id)];
     const int local = tile_id - cam.tile_base;
