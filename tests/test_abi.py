@@ -62,6 +62,8 @@ def test_host_side_argument_checks(lib):
     assert lib.dass_preprocess(-1, 0, None, None, None, None, None, None, cams, 2, 16, None, None) == -1
     assert lib.dass_preprocess(10, 4, None, None, None, None, None, None, cams, 2, 16, None, None) == -1
     assert lib.dass_render_fwd(None, None, None, cams, 2, 16, 100, None, None, None, None, None, None) == -1
+    assert lib.dass_tile_order(None, 5, None, None) == -1                            # missing buffers
+    assert lib.dass_tile_order(None, 0, None, None) == 0                             # no tiles: a no-op
     assert lib.dass_shift(-5, None, None, None, None, None, None, None) == -1
     assert lib.dass_densify_select(10, None, None, None, None, 1e-4, -1.0, 10, None, None, None, 0, None) == -1
     b = C.c_size_t()
