@@ -456,7 +456,7 @@ def main():
 
     # host buffers of the end-to-end steps (pinned), allocated before any timed region
     host_tgt = targets.cpu().pin_memory()
-    dev_tgt = torch.empty_like(targets)
+    dev_tgt, dev_tgt_next = torch.empty_like(targets), torch.empty_like(targets)
     host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ts.bufs.items()}
     host_out["is_var"] = torch.empty(ts.is_var.shape, dtype=torch.uint8).pin_memory()
     torch.cuda.synchronize()
@@ -495,9 +495,11 @@ def main():
     value = replicas.seconds_per_timestep(ms_max, args.steps, world)
 
     # ---------------- end to end through the C ABI with host buffers, right after the timed steps (same
-    # thermal state): each dass_timestep call uploads its images from pinned host memory and writes G_t
-    # back into pinned host buffers; the steps restart from the scene the timed steps started from, with
-    # the same timestep indices
+    # thermal state): images go up from pinned host memory and every dass_timestep call writes G_t back
+    # into pinned host buffers before it returns. Like a streaming caller, each call also uploads the
+    # next timestep's images into a second device buffer while its stages run (the first call uploads
+    # its own images too), and the next call trains on that buffer. The steps restart from the scene the
+    # timed steps started from, with the same timestep indices
     bufs0, isv0, n0, t0 = start_state
 
     def restore_start():
@@ -506,10 +508,37 @@ def main():
         ts.is_var.copy_(isv0)
         ts.n = n0
 
+    def copy_probe(reps=3):
+        """Copy bandwidth of the end-to-end buffers on the timestep's stream (CUDA events): the step's
+        images host -> device and the largest G_t buffer device -> host, GB/s per repetition. Taken
+        before the end-to-end window's untimed first step and after the window, so that a slow
+        window can be told apart from slow copies."""
+        k = max(ts.bufs, key=lambda k: ts.bufs[k].numel() * ts.bufs[k].element_size())
+        src_d, dst_h = ts.bufs[k], host_out[k]
+        jobs = (("h2d_gbs", lambda: dev_tgt.copy_(host_tgt, non_blocking=True), host_tgt.numel() * 4),
+                ("d2h_gbs", lambda: dst_h.copy_(src_d, non_blocking=True), src_d.numel() * src_d.element_size()))
+        res = {name: [] for name, _, _ in jobs}
+        torch.cuda.synchronize()
+        with torch.cuda.stream(ts.stream):
+            for _ in range(reps):
+                for name, fn, nbytes in jobs:
+                    ca, cb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ca.record(ts.stream)
+                    fn()
+                    cb.record(ts.stream)
+                    cb.synchronize()
+                    res[name].append(round(nbytes / (ca.elapsed_time(cb) * 1e-3) / 1e9, 1))
+        return res
+
+    def e2e_step(te, first, cur, nxt):
+        kw = {"targets_host": host_tgt} if first else {}
+        return one_timestep(te, cur, host_out=host_out, next_targets_host=host_tgt, next_targets=nxt, **kw)
+
     # one untimed step through the same path (first use of the pinned buffers), then the timed steps
     # from the start state again
+    copies_before = copy_probe()
     restore_start()
-    one_timestep(t0, dev_tgt, targets_host=host_tgt, host_out=host_out)
+    e2e_step(t0, True, dev_tgt, dev_tgt_next)
     restore_start()
     del start_state, bufs0
     torch.cuda.synchronize()
@@ -522,10 +551,12 @@ def main():
     te = t0
     e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
     marks = [a]
-    for _ in range(e2e_steps):
-        r = one_timestep(te, dev_tgt, targets_host=host_tgt, host_out=host_out)   # returns once G_t is on the host
+    cur, nxt = dev_tgt, dev_tgt_next
+    for i in range(e2e_steps):
+        r = e2e_step(te, i == 0, cur, nxt)           # returns once G_t is on the host
+        cur, nxt = nxt, cur
         te += 1
-        h2d = host_tgt.numel() * 4
+        h2d = host_tgt.numel() * 4 * (e2e_steps + 1) // e2e_steps     # one image set per step, plus the first
         d2h = r["n"] * (4 * (3 + 3 + 4 + 1 + 3 * 16) + 1)
         e2e_n.append(r["n"])
         ev = torch.cuda.Event(enable_timing=True)
@@ -536,6 +567,7 @@ def main():
     e2e_s = a.elapsed_time(b) / 1e3 / e2e_steps
     e2e_step_s = [round(marks[i].elapsed_time(marks[i + 1]) / 1e3, 4) for i in range(e2e_steps)]
     e2e_clk = e2e_clocks.stop()
+    copies_after = copy_probe()
     gc.unfreeze()
 
     # ---------------- dominant kernels, timed standalone on one shift-stage iteration's buffers of G_t
@@ -853,9 +885,11 @@ def main():
                 "paper_schedule": stages, "streaming_schedule": streaming,
                 "render_latency": {"single_view": render, "under_load": serve},
                 "e2e": {"value": round(e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "path": "dass_timestep with host targets and host G_t buffers (pinned)",
+                        "path": "dass_timestep with host targets and host G_t buffers (pinned); each call "
+                                "uploads the next timestep's images while it trains",
                         "start_state": "the timed steps' starting scene and timestep indices",
-                        "gaussians": e2e_n, "step_s": e2e_step_s, "clocks": e2e_clk},
+                        "gaussians": e2e_n, "step_s": e2e_step_s, "clocks": e2e_clk,
+                        "copy_gbs": {"before": copies_before, "after": copies_after}},
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:

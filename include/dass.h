@@ -770,6 +770,15 @@ typedef struct dass_timestep_desc {
     float* host_opacity_logit;
     float* host_sh;
     uint8_t* host_is_var;
+    /* optional upload of the NEXT timestep's images, overlapped with this timestep's stages (a
+     * streaming caller's input pipeline). With both set, next_targets_host (host, pinned for an
+     * asynchronous copy) is copied into next_targets (device, 3 * pixels floats like targets, not
+     * overlapping targets) on a stream of the call's own, ordered after the work already queued on
+     * `stream`. The call returns only once that copy has completed, on success and on error. The
+     * caller passes next_targets as the next call's targets, with targets_host NULL. Both NULL:
+     * no prefetch; only one of them set: DASS_ERR_INVALID_ARG. */
+    const float* next_targets_host;
+    float* next_targets;
 } dass_timestep_desc;
 
 /* What one timestep did (host struct filled by dass_timestep). */

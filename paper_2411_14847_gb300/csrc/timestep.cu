@@ -764,9 +764,47 @@ bool timestep_desc_ok(const dass_timestep_desc* d) {
         return false;
     if (!(d->prune_opacity > 0.f && d->prune_opacity < 1.f) || !(d->tau_pos >= 0.f) || !(d->tau_err >= 0.f))
         return false;
+    if (!d->next_targets_host != !d->next_targets || (d->next_targets && d->next_targets == d->targets)) return false;
     const long long n = *d->n;
     return n > 0 && n + d->k_max <= d->n_max;
 }
+
+// Upload of the next timestep's images on a stream of its own, overlapped with the stages running on
+// the timestep's stream; finish() (also run by the destructor, so every return path waits) blocks
+// until the copy has landed.
+class Prefetch {
+  public:
+    int start(float* dst, const float* src, size_t bytes, cudaStream_t after) {
+        DASS_CHECK_CUDA(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+        DASS_CHECK_CUDA(cudaEventCreateWithFlags(&ev_, cudaEventDisableTiming));
+        DASS_CHECK_CUDA(cudaEventRecord(ev_, after));      // after the last readers of dst queued so far
+        DASS_CHECK_CUDA(cudaStreamWaitEvent(cs_, ev_, 0));
+        DASS_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs_));
+        return DASS_OK;
+    }
+    int finish() {
+        cudaError_t e = cudaSuccess;
+        if (cs_) {
+            e = cudaStreamSynchronize(cs_);
+            cudaStreamDestroy(cs_);
+            cs_ = nullptr;
+        }
+        if (ev_) {
+            cudaEventDestroy(ev_);
+            ev_ = nullptr;
+        }
+        if (e != cudaSuccess) {
+            set_last_error("cudaStreamSynchronize(prefetch)", e);
+            return DASS_ERR_CUDA;
+        }
+        return DASS_OK;
+    }
+    ~Prefetch() { finish(); }
+
+  private:
+    cudaStream_t cs_ = nullptr;
+    cudaEvent_t ev_ = nullptr;
+};
 
 int read_scalar(const long long* dev, long long* host, cudaStream_t st) {
     DASS_CHECK_CUDA(cudaMemcpyAsync(host, dev, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -980,7 +1018,13 @@ DASS_API int dass_timestep(const dass_timestep_desc* d, dass_timestep_stats* sta
     ct0 = ct;
     for (int c = 0; c < ct0.n; ++c) ct0.c[c].rec_base = (long long)c * *d->n;
     ct0.rec_stride = *d->n;
-    const int rc = timestep_run(d, ct0, w, *stats, st);
+    Prefetch next;
+    if (d->next_targets) {
+        if (int rc = next.start(d->next_targets, d->next_targets_host, sizeof(float) * 3 * (size_t)ct.pixels_total, st))
+            return rc;
+    }
+    int rc = timestep_run(d, ct0, w, *stats, st);
     if (rc) cudaStreamSynchronize(st);   // nothing of the failed timestep stays in flight
-    return rc;
+    const int rc_next = next.finish();
+    return rc ? rc : rc_next;
 }

@@ -103,7 +103,7 @@ class dass_timestep_desc(C.Structure):
         ("lr_sh_rest", _F), ("beta1", _F), ("beta2", _F), ("eps", _F),
         ("pair_capacity", _I64), ("workspace", _V), ("workspace_bytes", C.c_size_t),
         ("host_means", _V), ("host_log_scales", _V), ("host_quats", _V), ("host_opacity_logit", _V),
-        ("host_sh", _V), ("host_is_var", _V),
+        ("host_sh", _V), ("host_is_var", _V), ("next_targets_host", _V), ("next_targets", _V),
     ]
 
 

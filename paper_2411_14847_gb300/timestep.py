@@ -574,11 +574,17 @@ class Timestep:
             setattr(d, k, v)
         return d
 
-    def run(self, t, targets, dyn_idx, offsets, z=None, targets_host=None, host_out=None, max_regrow=3):
+    def run(self, t, targets, dyn_idx, offsets, z=None, targets_host=None, host_out=None, max_regrow=3,
+            next_targets_host=None, next_targets=None):
         """Reconstruct timestep t from the images `targets` (device; with targets_host (pinned host
         tensor) the call first uploads it into `targets`). `offsets` ([n_dyn][7], device) gives the
         initial offsets and receives the learned ones. host_out (optional dict of pinned host tensors
-        like `bufs` plus is_var) receives G_t. Returns a dict of what the timestep did."""
+        like `bufs` plus is_var) receives G_t. With next_targets_host (pinned host tensor) and
+        next_targets (a second device image buffer), the next timestep's images are uploaded while
+        this one trains; the next call then takes next_targets as its `targets`. Returns a dict of
+        what the timestep did."""
+        if (next_targets_host is None) != (next_targets is None):
+            raise ValueError("next_targets_host and next_targets go together")
         n_dyn = int(dyn_idx.numel())
         dyn_idx = dyn_idx.contiguous()
         off_init = offsets.contiguous().clone()
@@ -593,6 +599,8 @@ class Timestep:
             self._n_host.value = self.n
             d.targets, d.targets_host = _vp(targets), (C.c_void_p(targets_host.data_ptr())
                                                        if targets_host is not None else None)
+            if next_targets is not None:
+                d.next_targets_host, d.next_targets = C.c_void_p(next_targets_host.data_ptr()), _vp(next_targets)
             d.t = int(t)
             d.dyn_idx, d.offsets_init, d.offsets, d.z = _vp(dyn_idx), _vp(off_init), _vp(offsets), _vp(z)
             need = D.dass_timestep_workspace(d)

@@ -176,3 +176,52 @@ def test_timestep_host_buffers(dass):
     assert rh["loss"] == pytest.approx(rd["loss"], rel=1e-5)
     for k in PARAMS:
         assert rel_l2(gh[k].numpy(), gd[k].numpy()) < 1e-4, k
+
+
+def test_timestep_prefetches_the_next_images(dass):
+    """Two timesteps where the first call also uploads the second's images (from pinned host memory
+    into a second device buffer, overlapped with its stages) and the second call trains on that
+    buffer: the uploaded images are exact, and G_t after both steps equals the device-buffer form.
+    A descriptor with only one of the two prefetch fields is refused."""
+    from paper_2411_14847_gb300 import dass as D
+    from paper_2411_14847_gb300.timestep import Timestep
+    arrays, is_var, cams, deg, tgt, dyn, off, z = _case(seed=74)
+    tgt2 = (tgt.flip(0) * 0.5 + 0.25).contiguous()
+    n = arrays["means"].shape[0]
+    res = {}
+    for mode in ("device", "prefetch"):
+        ts = Timestep(cams, n + 400, deg, tile=16, batch=128, n_shift=4, k_max=40)
+        ts.load(arrays, is_var=is_var)
+        if mode == "device":
+            r1 = ts.run(5, tgt, dyn, off.clone(), z=z)
+            r2 = ts.run(6, tgt2, dyn, off.clone(), z=z)
+        else:
+            host_a, host_b = tgt.cpu().pin_memory(), tgt2.cpu().pin_memory()
+            dev_a, dev_b = torch.zeros_like(tgt), torch.zeros_like(tgt)
+            r1 = ts.run(5, dev_a, dyn, off.clone(), z=z, targets_host=host_a, next_targets_host=host_b,
+                        next_targets=dev_b)
+            assert torch.equal(dev_a, tgt) and torch.equal(dev_b, tgt2)
+            r2 = ts.run(6, dev_b, dyn, off.clone(), z=z)
+            p2_n = ts.n
+            with pytest.raises(ValueError):
+                ts.run(7, dev_b, dyn, off.clone(), z=z, next_targets=dev_a)
+            # a descriptor valid but for its prefetch fields: one of the two, or the targets' own buffer
+            off0, off1 = off.clone(), off.clone()
+            d = ts._desc_template(int(dyn.numel()))
+            ts._n_host.value = ts.n
+            d.targets, d.t = dev_b.data_ptr(), 7
+            d.dyn_idx, d.offsets_init, d.offsets, d.z = dyn.data_ptr(), off0.data_ptr(), off1.data_ptr(), z.data_ptr()
+            d.workspace, d.workspace_bytes = ts.workspace.data_ptr(), ts.workspace.numel()
+            for nh, nd in ((None, dev_a), (host_a, None), (host_a, dev_b)):
+                d.next_targets_host = nh.data_ptr() if nh is not None else None
+                d.next_targets = nd.data_ptr() if nd is not None else None
+                with pytest.raises(D.DassError) as e:
+                    D.dass_timestep(d, stream=ts.stream)
+                assert e.value.status == D.ERR_INVALID_ARG
+            assert ts.n == p2_n
+        res[mode] = (r1, r2, {k: v.cpu() for k, v in ts.view().items()})
+    (d1, d2, gd), (p1, p2, gp) = res["device"], res["prefetch"]
+    assert (d1["n"], d2["n"], d1["spawned"], d2["spawned"]) == (p1["n"], p2["n"], p1["spawned"], p2["spawned"])
+    assert p2["loss"] == pytest.approx(d2["loss"], rel=1e-5)
+    for k in PARAMS:
+        assert rel_l2(gp[k].numpy(), gd[k].numpy()) < 1e-4, k
