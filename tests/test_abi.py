@@ -154,3 +154,37 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[s.__name__]) == C.sizeof(s), s.__name__
         for f, _ in s._fields_:
             assert int(got[f"{s.__name__}.{f}"]) == getattr(s, f).offset, (s.__name__, f)
+
+
+def test_timestep_descriptor_prefetch_checks(lib):
+    """dass_timestep refuses, on the host and before any device work, a descriptor whose prefetch
+    fields are half set or name the targets' own buffer. The same descriptor without them, or with
+    both set to a separate buffer, passes the checks and stops at the workspace size (DASS_ERR_OOM),
+    still on the host. The pointers are stand-ins that the host checks never dereference."""
+    from paper_2411_14847_gb300 import dass, synth
+    cams = dass.cameras(synth.arc_cameras(2, 4.0, 100, 50))
+    n_host = C.c_int64(100)
+    bufs = [C.create_string_buffer(64) for _ in range(12)]
+
+    def ptr(i):
+        return C.cast(bufs[i], C.c_void_p).value
+
+    d = dass.dass_timestep_desc()
+    d.n_max, d.sh_degree, d.n_cams = 200, 1, 2
+    d.means, d.log_scales, d.quats, d.opacity_logit, d.sh, d.is_var = (ptr(i) for i in range(6))
+    d.n, d.cams = C.cast(C.pointer(n_host), C.c_void_p), C.cast(cams, C.c_void_p)
+    d.targets, d.offsets, d.z, d.workspace = ptr(6), ptr(7), ptr(8), ptr(9)
+    d.workspace_bytes = 16
+    d.tile, d.batch, d.pair_capacity, d.k_max = 16, 128, 1 << 16, 10
+    d.lambda_dssim, d.quantile, d.prune_opacity = 0.2, 0.5, 0.005
+    stats = dass.dass_timestep_stats()
+
+    def call():
+        return lib.dass_timestep(C.byref(d), C.byref(stats), None)
+
+    assert call() == dass.ERR_OOM
+    for nh, nd in ((ptr(10), None), (None, ptr(11)), (ptr(10), ptr(6))):
+        d.next_targets_host, d.next_targets = nh, nd
+        assert call() == dass.ERR_INVALID_ARG, (nh, nd)
+    d.next_targets_host, d.next_targets = ptr(10), ptr(11)
+    assert call() == dass.ERR_OOM
