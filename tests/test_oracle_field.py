@@ -17,6 +17,20 @@ def _t(p):
     return {k: torch.as_tensor(v) for k, v in p.items()}
 
 
+def test_level_resolutions_closed_forms():
+    """Level sizes grow geometrically from n_min to n_max: with n_max / n_min = 2^(levels - 1) every
+    level doubles exactly; one level is n_min alone, two are the ends; the 16-level 16..2048 grid is
+    strictly increasing from 16 to 2048 with a nearly constant ratio (128^(1/15) ~ 1.38)."""
+    assert fld.level_resolutions(8, 16, 2048) == [16 << l for l in range(8)]
+    assert fld.level_resolutions(5, 8, 128) == [8, 16, 32, 64, 128]
+    assert fld.level_resolutions(1, 16, 2048) == [16]
+    assert fld.level_resolutions(2, 16, 2048) == [16, 2048]
+    res = fld.level_resolutions(16, 16, 2048)
+    assert res[0] == 16 and res[-1] == 2048 and all(a < b for a, b in zip(res, res[1:]))
+    ratios = [b / a for a, b in zip(res, res[1:])]
+    assert all(1.33 < r < 1.43 for r in ratios)
+
+
 def test_dense_level_reproduces_linear_functions():
     """On a densely indexed level, a table holding a linear function of the vertex coordinates is
     interpolated to that same function of x * N (trilinear interpolation is exact on linear

@@ -336,6 +336,26 @@ def test_ssim_matches_scipy_filter():
     assert g.sum() == pytest.approx(1.0) and np.argmax(g) == 5
 
 
+def test_window_moments_match_scipy_and_constant_images():
+    """The target's window statistics (w * y, w * y^2) that the cached-statistics loss reads: SciPy's
+    zero-padded correlation of y and of y^2 with the 11 x 11 window, and (c, c^2) for a constant image
+    c at pixels whose window lies inside the image (the window sums to one)."""
+    from scipy.ndimage import correlate
+    rng = np.random.default_rng(16)
+    img = rng.uniform(size=(3, 19, 23))
+    g = L.gaussian_window().numpy()
+    w2 = np.outer(g, g)
+    m1, m2 = L.window_moments(torch.tensor(img, dtype=DT))
+    for c in range(3):
+        np.testing.assert_allclose(m1[c].numpy(), correlate(img[c], w2, mode="constant", cval=0.0), atol=1e-13)
+        np.testing.assert_allclose(m2[c].numpy(), correlate(img[c] ** 2, w2, mode="constant", cval=0.0),
+                                   atol=1e-13)
+    c1, c2 = L.window_moments(torch.full((3, 16, 16), 0.7, dtype=DT))
+    np.testing.assert_allclose(c1[:, 5:11, 5:11].numpy(), 0.7, rtol=1e-13)
+    np.testing.assert_allclose(c2[:, 5:11, 5:11].numpy(), 0.49, rtol=1e-13)
+    assert float(c1[0, 0, 0]) == pytest.approx(0.7 * float(g[5:].sum()) ** 2, rel=1e-13)   # corner: a quarter window
+
+
 def test_fidelity_loss_l1_closed_form():
     x = torch.full((3, 4, 4), 0.25, dtype=DT)
     y = torch.full((3, 4, 4), 0.75, dtype=DT)
