@@ -776,7 +776,7 @@ typedef struct dass_timestep_desc {
      * overlapping targets) on a stream of the call's own, ordered after the work already queued on
      * `stream`. The call returns only once that copy has completed, on success and on error. The
      * caller passes next_targets as the next call's targets, with targets_host NULL. Both NULL:
-     * no prefetch; only one of them set: DASS_ERR_INVALID_ARG. */
+     * no prefetch; only one of them set, or next_targets overlapping targets: DASS_ERR_INVALID_ARG. */
     const float* next_targets_host;
     float* next_targets;
 } dass_timestep_desc;

@@ -764,7 +764,7 @@ bool timestep_desc_ok(const dass_timestep_desc* d) {
         return false;
     if (!(d->prune_opacity > 0.f && d->prune_opacity < 1.f) || !(d->tau_pos >= 0.f) || !(d->tau_err >= 0.f))
         return false;
-    if (!d->next_targets_host != !d->next_targets || (d->next_targets && d->next_targets == d->targets)) return false;
+    if (!d->next_targets_host != !d->next_targets) return false;
     const long long n = *d->n;
     return n > 0 && n + d->k_max <= d->n_max;
 }
@@ -1007,6 +1007,12 @@ DASS_API int dass_timestep(const dass_timestep_desc* d, dass_timestep_stats* sta
     if (!timestep_desc_ok(d) || !stats) return DASS_ERR_INVALID_ARG;
     static thread_local CamTable ct;
     if (!make_cam_table(d->cams, d->n_cams, d->tile, d->n_max, &ct)) return DASS_ERR_INVALID_ARG;
+    const size_t image_bytes = sizeof(float) * 3 * (size_t)ct.pixels_total;
+    if (d->next_targets) {   // the prefetched images may not land in this timestep's images
+        const char* a = reinterpret_cast<const char*>(d->targets);
+        const char* b = reinterpret_cast<const char*>(d->next_targets);
+        if (a < b + image_bytes && b < a + image_bytes) return DASS_ERR_INVALID_ARG;
+    }
     if (d->workspace_bytes < carve_timestep(d, ct, nullptr, nullptr)) return DASS_ERR_OOM;
     cudaStream_t st = as_stream(stream);
     if (st == nullptr) return DASS_ERR_INVALID_ARG;
@@ -1020,8 +1026,7 @@ DASS_API int dass_timestep(const dass_timestep_desc* d, dass_timestep_stats* sta
     ct0.rec_stride = *d->n;
     Prefetch next;
     if (d->next_targets) {
-        if (int rc = next.start(d->next_targets, d->next_targets_host, sizeof(float) * 3 * (size_t)ct.pixels_total, st))
-            return rc;
+        if (int rc = next.start(d->next_targets, d->next_targets_host, image_bytes, st)) return rc;
     }
     int rc = timestep_run(d, ct0, w, *stats, st);
     if (rc) cudaStreamSynchronize(st);   // nothing of the failed timestep stays in flight

@@ -158,7 +158,7 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 def test_timestep_descriptor_prefetch_checks(lib):
     """dass_timestep refuses, on the host and before any device work, a descriptor whose prefetch
-    fields are half set or name the targets' own buffer. The same descriptor without them, or with
+    fields are half set or whose prefetch buffer overlaps the targets. The same descriptor without them, or with
     both set to a separate buffer, passes the checks and stops at the workspace size (DASS_ERR_OOM),
     still on the host. The pointers are stand-ins that the host checks never dereference."""
     from paper_2411_14847_gb300 import dass, synth
@@ -183,8 +183,11 @@ def test_timestep_descriptor_prefetch_checks(lib):
         return lib.dass_timestep(C.byref(d), C.byref(stats), None)
 
     assert call() == dass.ERR_OOM
-    for nh, nd in ((ptr(10), None), (None, ptr(11)), (ptr(10), ptr(6))):
+    # half set; the targets' own buffer; a buffer that starts inside the targets (2 x 100 x 50 x 3 floats)
+    for nh, nd in ((ptr(10), None), (None, ptr(11)), (ptr(10), ptr(6)), (ptr(10), ptr(6) + 4 * 100 * 50 * 3 * 2 - 4)):
         d.next_targets_host, d.next_targets = nh, nd
         assert call() == dass.ERR_INVALID_ARG, (nh, nd)
+    d.next_targets_host, d.next_targets = ptr(10), ptr(6) + 4 * 100 * 50 * 3 * 2      # just past them
+    assert call() == dass.ERR_OOM
     d.next_targets_host, d.next_targets = ptr(10), ptr(11)
     assert call() == dass.ERR_OOM
