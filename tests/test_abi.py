@@ -183,11 +183,13 @@ def test_timestep_descriptor_prefetch_checks(lib):
         return lib.dass_timestep(C.byref(d), C.byref(stats), None)
 
     assert call() == dass.ERR_OOM
-    # half set; the targets' own buffer; a buffer that starts inside the targets (2 x 100 x 50 x 3 floats)
-    for nh, nd in ((ptr(10), None), (None, ptr(11)), (ptr(10), ptr(6)), (ptr(10), ptr(6) + 4 * 100 * 50 * 3 * 2 - 4)):
+    # the targets hold 2 x 100 x 50 x 3 floats from ptr(6); the prefetch buffers are addresses relative
+    # to it (only compared, never dereferenced): half set, the targets themselves, one starting inside
+    image = 4 * 100 * 50 * 3 * 2
+    for nh, nd in ((ptr(10), None), (None, ptr(6) + 4 * image), (ptr(10), ptr(6)), (ptr(10), ptr(6) + image - 4),
+                   (ptr(10), ptr(6) - image + 4)):
         d.next_targets_host, d.next_targets = nh, nd
         assert call() == dass.ERR_INVALID_ARG, (nh, nd)
-    d.next_targets_host, d.next_targets = ptr(10), ptr(6) + 4 * 100 * 50 * 3 * 2      # just past them
-    assert call() == dass.ERR_OOM
-    d.next_targets_host, d.next_targets = ptr(10), ptr(11)
-    assert call() == dass.ERR_OOM
+    for nd in (ptr(6) + image, ptr(6) + 4 * image, ptr(6) - image):    # adjacent or apart
+        d.next_targets_host, d.next_targets = ptr(10), nd
+        assert call() == dass.ERR_OOM, nd
